@@ -1,0 +1,131 @@
+"""FP64 CPU oracle for the CDI phase-field step (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never does, and nothing here imports the product.
+
+The arithmetic lives in ``cdi_oracle.c`` (plain C, nested loops, float64),
+compiled with gcc into ``oracle/_lib/libcdi_oracle.so`` by :func:`build`.
+Functions take numpy arrays shaped ``(nz, ny, nx)``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cdi_oracle.c")
+_OUT = os.path.join(_HERE, "_lib", "libcdi_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, -O2) if needed."""
+    if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
+        return _OUT
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    tmp = _OUT + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _OUT)
+    return _OUT
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i, d = ctypes.c_int, ctypes.c_double
+            lib.oracle_rhs.argtypes = [i, i, i, d, _D, _D, _D, _D, d, d, d, _D]
+            lib.oracle_step.argtypes = [i, i, i, d, _D, _D, _D, _D, d, d, d, d, _D]
+            lib.oracle_stats.argtypes = [ctypes.c_long, _D, d, d, _D,
+                                         ctypes.POINTER(ctypes.c_longlong)]
+            lib.oracle_adjoint.argtypes = [i, i, i, d, _D, _D, _D, _D, _D, d, d, d, d,
+                                           _D, _D, _D, _D]
+            for f in (lib.oracle_rhs, lib.oracle_step, lib.oracle_stats, lib.oracle_adjoint):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(phi, u, v, w):
+    phi, u, v, w = (_f64(x) for x in (phi, u, v, w))
+    if phi.ndim != 3 or any(x.shape != phi.shape for x in (u, v, w)):
+        raise ValueError("phi, u, v, w must share one (nz, ny, nx) shape")
+    return phi, u, v, w
+
+
+def rhs(phi, u, v, w, dx, eps, gamma, vel_scale=1.0):
+    """d phi/dt of Eq. 1 discretised by the five steps of Section 2.2."""
+    phi, u, v, w = _check(phi, u, v, w)
+    nz, ny, nx = phi.shape
+    out = np.empty_like(phi)
+    rc = _load().oracle_rhs(nx, ny, nz, dx, _p(phi), _p(u), _p(v), _p(w), eps, gamma,
+                            vel_scale, _p(out))
+    if rc:
+        raise ValueError("oracle_rhs: bad arguments")
+    return out
+
+
+def step(phi, u, v, w, dx, dt, eps, gamma, vel_scale=1.0):
+    """One explicit Euler step of the CDI equation (Eq. 11 generalised to 3D)."""
+    phi, u, v, w = _check(phi, u, v, w)
+    nz, ny, nx = phi.shape
+    out = np.empty_like(phi)
+    rc = _load().oracle_step(nx, ny, nz, dx, _p(phi), _p(u), _p(v), _p(w), dt, eps,
+                             gamma, vel_scale, _p(out))
+    if rc:
+        raise ValueError("oracle_step: bad arguments")
+    return out
+
+
+def run(phi, u, v, w, dx, dt, eps, gamma, nsteps, period=0.0, t0=0.0):
+    """nsteps Euler steps; velocity scaled by cos(pi t / period) when period > 0."""
+    p = _f64(phi)
+    t = t0
+    for _ in range(nsteps):
+        s = np.cos(np.pi * t / period) if period > 0 else 1.0
+        p = step(p, u, v, w, dx, dt, eps, gamma, s)
+        t += dt
+    return p
+
+
+def stats(phi, dV, tol):
+    """{mass, sum, min, max, n_strict, n_tol} of a field (plain sequential sum)."""
+    phi = _f64(phi).ravel()
+    o = np.empty(4)
+    c = np.empty(2, dtype=np.int64)
+    _load().oracle_stats(phi.size, _p(phi), dV, tol, _p(o),
+                         c.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    return dict(mass=o[0], sum=o[1], min=o[2], max=o[3], n_strict=int(c[0]), n_tol=int(c[1]))
+
+
+def adjoint(phi, u, v, w, lam_next, dx, dt, eps, gamma, vel_scale=1.0, want_vel=False):
+    """Discrete adjoint of one Euler step: returns lam (and velocity gradients)."""
+    phi, u, v, w = _check(phi, u, v, w)
+    lam_next = _f64(lam_next)
+    nz, ny, nx = phi.shape
+    lam = np.empty_like(phi)
+    g = [np.zeros_like(phi) for _ in range(3)] if want_vel else [None] * 3
+    rc = _load().oracle_adjoint(nx, ny, nz, dx, _p(phi), _p(u), _p(v), _p(w), _p(lam_next),
+                                dt, eps, gamma, vel_scale, _p(lam), _p(g[0]), _p(g[1]), _p(g[2]))
+    if rc:
+        raise ValueError("oracle_adjoint: bad arguments")
+    return (lam, *g) if want_vel else lam

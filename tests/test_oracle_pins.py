@@ -1,0 +1,395 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle (oracle/cdi_oracle.c) against something other
+than itself: the paper's coefficient form (Eq. 13, Eq. 18-22), the printed
+1D scheme (Eq. 11), the phi -> 1 - phi symmetry (Eq. 16), discrete
+conservation, the boundedness theorem (Eq. 17/24 with A <= 1/(2 D_f)), the
+below-line classification of Table 2, a constructed exact discrete
+equilibrium, Table 1's E_eps, equivariances, and (for the adjoint) finite
+differences and a brute-force Jacobian transpose.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1803_01262_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+AX = (2, 1, 0)  # array axis of x, y, z
+
+
+def coefficient_form_step(phi, u, v, w, dx, dt, eps, gamma):
+    """Eq. 18-22 (and Eq. 13 in 1D), written for 3D: phi' = sum C phi.
+
+    C_c = 1 - 2 D A - (B A / gamma) sum_d (u^d_{c+1/2} - u^d_{c-1/2})   (Eq. 19, D = 3
+          terms of the 3D stencil; degenerate axes contribute their A too)
+    C_{c-e_d} = A [1 + B (n^d_{c-e_d} (1 - phi_{c-e_d}) + u^d_{c-1/2} / gamma)]   (Eq. 21)
+    C_{c+e_d} = A [1 + B (-n^d_{c+e_d} (1 - phi_{c+e_d}) - u^d_{c+1/2} / gamma)]  (Eq. 22)
+    """
+    A = dt * gamma * eps / dx ** 2
+    B = dx / (2 * eps)
+    g = [np.roll(phi, -1, a) - np.roll(phi, 1, a) for a in AX]
+    m = np.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2)
+    safe = np.where(m > 0, m, 1.0)
+    n = [np.where(m > 0, gd / safe, 0.0) for gd in g]
+    vel = (u, v, w)
+    Cc = 1 - 6 * A - (B * A / gamma) * sum(vel[d] - np.roll(vel[d], 1, AX[d]) for d in range(3))
+    out = Cc * phi
+    for d in range(3):
+        a = AX[d]
+        pm, nm, um = np.roll(phi, 1, a), np.roll(n[d], 1, a), np.roll(vel[d], 1, a)
+        pp, npp, up = np.roll(phi, -1, a), np.roll(n[d], -1, a), vel[d]
+        out = out + A * (1 + B * (nm * (1 - pm) + um / gamma)) * pm
+        out = out + A * (1 + B * (-npp * (1 - pp) - up / gamma)) * pp
+    return out
+
+
+def eq11_1d(phi, u, dx, dt, eps, gamma):
+    """The printed 1D update, Eq. 11, with the sharpening sign read as in Eq. 13."""
+    pp, pm = np.roll(phi, -1), np.roll(phi, 1)
+    n = np.sign(pp - pm)
+    npp, nm = np.roll(n, -1), np.roll(n, 1)
+    adv = -u * (pp - pm) / (2 * dx)
+    dif = gamma * eps * (pp - 2 * phi + pm) / dx ** 2
+    shp = gamma * ((pp ** 2 - pp) * npp - (pm ** 2 - pm) * nm) / (2 * dx)
+    return phi + dt * (adv + dif + shp)
+
+
+def rand_case(shape, seed, solenoidal=True, h=0.05):
+    rng = np.random.default_rng(seed)
+    phi = I.random_phi(shape, seed)
+    if solenoidal:
+        u, v, w = I.random_velocity(shape, h, nmodes=8, kmax=3, seed=seed + 1)
+    else:
+        u, v, w = (rng.standard_normal(shape) for _ in range(3))
+    return phi, u, v, w, h
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 17), (1, 9, 11), (5, 6, 7), (4, 4, 4), (3, 1, 8)])
+@pytest.mark.parametrize("solenoidal", [True, False])
+def test_coefficient_form(shape, solenoidal):
+    """Flux form == Eq. 13 / Eq. 18-22 coefficient form (any periodic u)."""
+    phi, u, v, w, h = rand_case(shape, 11, solenoidal)
+    dt, eps, gamma = 0.3 * h * h, 1.2 * h, 0.8
+    a = oracle.step(phi, u, v, w, h, dt, eps, gamma)
+    b = coefficient_form_step(phi, u, v, w, h, dt, eps, gamma)
+    assert np.abs(a - b).max() < 2e-15
+
+
+def test_eq11_1d():
+    """ny = nz = 1 reduces exactly to the printed 1D scheme (Eq. 11)."""
+    n, h = 40, 1.0 / 40
+    x = I.centres(n, h)
+    phi = I.tanh_profile(0.25 - np.abs(x - 0.5), h)
+    rng = np.random.default_rng(3)
+    phi = np.clip(phi + 0.05 * rng.standard_normal(n), 0, 1)
+    u = 0.7
+    dt, eps, gamma = 0.2 * h, 1.1 * h, 1.3
+    ours = oracle.step(phi.reshape(1, 1, n), np.full((1, 1, n), u), np.zeros((1, 1, n)),
+                       np.zeros((1, 1, n)), h, dt, eps, gamma)[0, 0]
+    ref = eq11_1d(phi, u, h, dt, eps, gamma)
+    assert np.abs(ours - ref).max() < 1e-15
+
+
+def test_sign_reading_matters():
+    """A plausible mistake (the '+' printed in Eq. 11) is caught by Eq. 13."""
+    n, h = 32, 1.0 / 32
+    phi = I.tanh_profile(0.2 - np.abs(I.centres(n, h) - 0.5), h)
+    pp, pm = np.roll(phi, -1), np.roll(phi, 1)
+    nn = np.sign(pp - pm)
+    wrong = ((pp ** 2 - pp) * np.roll(nn, -1) - (pm ** 2 + pm) * np.roll(nn, 1))
+    right = ((pp ** 2 - pp) * np.roll(nn, -1) - (pm ** 2 - pm) * np.roll(nn, 1))
+    assert np.abs(wrong - right).max() > 0.1
+
+
+@pytest.mark.parametrize("shape", [(1, 12, 10), (6, 5, 7), (2, 3, 4)])
+def test_symmetry_eq16(shape):
+    """step(1 - phi) = 1 - step(phi) for discretely solenoidal u (Eq. 16)."""
+    phi, u, v, w, h = rand_case(shape, 5)
+    args = (u, v, w, h, 0.2 * h * h, h, 1.0)
+    a = oracle.step(1 - phi, *args)
+    b = 1 - oracle.step(phi, *args)
+    assert np.abs(a - b).max() < 1e-15
+
+
+def test_symmetry_defect_is_divergence():
+    """For non-solenoidal u the Eq. 16 defect is exactly -dt * div(u) (derived)."""
+    phi, u, v, w, h = rand_case((4, 5, 6), 8, solenoidal=False)
+    dt = 0.1 * h * h
+    a = oracle.step(1 - phi, u, v, w, h, dt, h, 1.0)
+    b = 1 - oracle.step(phi, u, v, w, h, dt, h, 1.0)
+    div = sum(vel - np.roll(vel, 1, AX[d]) for d, vel in enumerate((u, v, w))) / h
+    assert np.abs((a - b) + dt * div).max() < 1e-13
+
+
+@pytest.mark.parametrize("solenoidal", [True, False])
+def test_conservation(solenoidal):
+    """sum phi^{k+1} = sum phi^k to round-off for any periodic u (telescoping fluxes)."""
+    phi, u, v, w, h = rand_case((7, 8, 9), 2, solenoidal)
+    p = phi
+    for _ in range(10):
+        p = oracle.step(p, u, v, w, h, 0.2 * h * h, 1.5 * h, 1.0)
+    assert abs(p.sum() - phi.sum()) / phi.sum() < 1e-14
+
+
+def test_constant_field():
+    """phi = c with discretely solenoidal u stays c to round-off."""
+    shape = (6, 7, 8)
+    _, u, v, w, h = rand_case(shape, 4)
+    for c in (0.0, 0.3, 1.0):
+        p = oracle.step(np.full(shape, c), u, v, w, h, 0.2 * h * h, h, 1.0)
+        assert np.abs(p - c).max() < 1e-14
+
+
+def discrete_equilibrium_1d(n, e):
+    """Exact zero-flux profile of the scheme at u = 0, eps/dx = e (derived).
+
+    With n = +1 on a rising profile, a zero face flux means
+    e (phi_{i+1} - phi_i) = (phi_i (1 - phi_i) + phi_{i+1} (1 - phi_{i+1})) / 2,
+    a quadratic in either neighbour.  March it up and down from 0.5, then
+    mirror it so the periodic box holds a drop.
+    """
+    half = n // 2
+    up = np.empty(half)
+    c0 = half // 2
+    up[c0] = 0.5
+    for i in range(c0, half - 1):
+        p = up[i]
+        c = e * p + 0.5 * p * (1 - p)
+        up[i + 1] = -(e - 0.5) + math.sqrt((e - 0.5) ** 2 + 2 * c)
+    for i in range(c0, 0, -1):
+        x = up[i]
+        q = e * x - 0.5 * x * (1 - x)
+        up[i - 1] = (e + 0.5) - math.sqrt((e + 0.5) ** 2 - 2 * q)
+    return np.concatenate([up, up[::-1]])
+
+
+@pytest.mark.parametrize("e", [0.7, 1.0, 1.5])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_discrete_equilibrium_is_stationary(e, axis):
+    """A constructed exact discrete equilibrium is left unchanged by a step.
+
+    This fixes the sharpening sign, the centre-product-then-average
+    interpolation (Section 2.2, second step), the diffusion coefficient and
+    the dx scaling: a face-product sharpening term or a wrong sign moves it.
+    """
+    n, h = 240, 1.0 / 240
+    prof = discrete_equilibrium_1d(n, e)
+    shape = [4, 3, 5]
+    shape[AX[axis]] = n
+    sh = [1, 1, 1]
+    sh[AX[axis]] = n
+    phi = np.broadcast_to(prof.reshape(sh), shape).copy()
+    z = np.zeros(shape)
+    dt = 0.16 * h * h / (1.0 * e * h)  # A = 0.16
+    p = oracle.step(phi, z, z, z, h, dt, e * h, 1.0)
+    assert np.abs(p - phi).max() < 1e-15
+    # the analytic tanh profile is only near-stationary: it does move
+    x = I.centres(n, h)
+    tanh = I.tanh_profile(0.25 - np.abs(x - 0.5), e * h)
+    t = np.broadcast_to(tanh.reshape(sh), shape).copy()
+    assert np.abs(oracle.step(t, z, z, z, h, dt, e * h, 1.0) - t).max() > 1e-6
+
+
+def test_face_product_variant_is_not_stationary():
+    """The face-product reading of the sharpening term breaks the equilibrium."""
+    n, h, e = 240, 1.0 / 240, 1.0
+    p = discrete_equilibrium_1d(n, e)
+    pr = np.roll(p, -1)
+    pf = 0.5 * (p + pr)
+    nn = np.sign(np.roll(p, -1) - np.roll(p, 1))
+    nf = 0.5 * (nn + np.roll(nn, -1))
+    F = -e * (pr - p) + pf * (1 - pf) * nf  # gamma = dx = 1 units
+    assert np.abs(F - np.roll(F, 1)).max() > 1e-4
+
+
+def test_boundedness_theorem_random_boxes():
+    """0 <= phi <= 1 (within machine eps) under Eq. 24 and A <= 1/(2 D_f).
+
+    Many seeded small periodic boxes with random solenoidal velocity, eps/dx
+    on or above the crossover line, U = max face |component|.
+    """
+    rng = np.random.default_rng(2024)
+    tol = np.finfo(np.float64).eps
+    worst = 0
+    for b in range(120):
+        dims = rng.integers(3, 10, size=3)
+        if b % 4 == 0:
+            dims[0] = 1
+        shape = tuple(int(x) for x in dims)
+        h = 1.0 / max(shape)
+        phi = I.random_phi(shape, int(rng.integers(1 << 30)), smooth=bool(b % 2))
+        u, v, w = I.random_velocity(shape, h, 8, 3, int(rng.integers(1 << 30)))
+        U = I.face_umax(u, v, w)
+        eoh = float(rng.uniform(0.55, 2.0))
+        gmin = 1.0 / (2 * eoh - 1) if eoh > 0.5 else np.inf
+        gamma = U * gmin * float(rng.uniform(1.0, 2.0))
+        Df = sum(1 for s in shape if s > 1)
+        eps = eoh * h
+        dt = float(rng.uniform(0.5, 1.0)) * h * h / (2 * Df * gamma * eps)
+        p = phi
+        for _ in range(25):
+            p = oracle.step(p, u, v, w, h, dt, eps, gamma)
+            worst = max(worst, int(((p < -tol) | (p > 1 + tol)).sum()))
+    assert worst == 0
+
+
+def _table2_run(eoh, gu):
+    f, _ = I.drop_2d_uniform(eoh)
+    h, eps, gamma = f.h, eoh * f.h, gu
+    dt = min(h * h / (4 * gamma * eps), h / (f.u.max() + f.v.max() + 2 * gamma))
+    T = 2 * math.sqrt(2)
+    n = int(math.ceil(T / dt))
+    dt = T / n
+    p, tol, bad = f.phi, np.finfo(float).eps, 0
+    for _ in range(n):
+        p = oracle.step(p, f.u, f.v, f.w, h, dt, eps, gamma)
+        bad += int(((p < -tol) | (p > 1 + tol)).sum())
+    return bad
+
+
+@pytest.mark.parametrize("point,eoh,gu,bounded", [
+    (1, 1.5, 0.5, True), (2, 1.0, 1.0, True), (3, 5 / 6, 1.5, True), (4, 1.5, 1.5, True),
+    (5, 0.9, 0.9, True), (6, 0.8, 0.8, False), (7, 0.7, 0.7, False)])
+def test_table2_uniform_classification(point, eoh, gu, bounded):
+    """Table 2 (uniform velocity): points 1-5 bounded, 6-7 not.
+
+    The paper ran RK4; here explicit Euler with A <= 1/4.  Points 1-5 satisfy
+    Eq. 23 (component maxima), 6-7 violate it, as the paper explains.
+    """
+    assert (_table2_run(eoh, gu) == 0) == bounded
+
+
+def test_table1_e_eps():
+    """E_eps of the 2D drop initial condition reproduces Table 1 within 3%."""
+    rows = np.loadtxt(os.path.join(GOLDEN, "table1_e_eps.txt"))
+    for _, eoh, _, ref in rows:
+        f, th = I.drop_2d_uniform(eoh)
+        E = np.abs(f.phi - th).sum() * f.h ** 2 / 4.0
+        assert abs(E / ref - 1) < 0.03, (eoh, E, ref)
+
+
+def test_equivariance():
+    """Periodic shift, x<->y swap (with u<->v) and x-reflection (u -> -u)."""
+    phi, u, v, w, h = rand_case((5, 6, 6), 9)
+    args = dict(dx=h, dt=0.2 * h * h, eps=h, gamma=1.1)
+    base = oracle.step(phi, u, v, w, **args)
+    r = lambda a: np.roll(np.roll(a, 2, 2), -1, 0)
+    assert np.abs(oracle.step(r(phi), r(u), r(v), r(w), **args) - r(base)).max() == 0.0
+    s = lambda a: np.swapaxes(a, 1, 2)
+    sw = oracle.step(s(phi), s(v), s(u), s(w), **args)
+    assert np.abs(sw - s(base)).max() < 1e-15
+    fl = lambda a: a[:, :, ::-1]
+    ur = -np.roll(fl(u), -1, 2)  # face i+1/2 of the mirror is face N-2-i+1/2
+    rf = oracle.step(fl(phi), ur, fl(v), fl(w), **args)
+    assert np.abs(rf - fl(base)).max() < 1e-15
+
+
+def test_degenerate_z_is_2d():
+    """nz = 1: any w is inert and the 2D coefficient form (Eq. 18) holds."""
+    phi, u, v, w, h = rand_case((1, 8, 9), 12)
+    a = oracle.step(phi, u, v, w, h, 0.2 * h * h, h, 1.0)
+    b = oracle.step(phi, u, v, np.zeros_like(w) + 3.0, h, 0.2 * h * h, h, 1.0)
+    assert np.array_equal(a, b)
+
+
+def test_velocity_generators():
+    """Staggered curl is discretely solenoidal; analytic fields are reproduced."""
+    for f in (I.single_vortex_2d(32), I.deformation_3d(24)):
+        div = sum(vel - np.roll(vel, 1, AX[d]) for d, vel in enumerate((f.u, f.v, f.w)))
+        assert np.abs(div).max() / f.h < 1e-11
+    n = 64
+    f = I.single_vortex_2d(n)
+    xf, yc = I.centres(n, f.h, 1.0), I.centres(n, f.h, 0.5)
+    ua = -np.sin(np.pi * xf)[None, :] ** 2 * np.sin(2 * np.pi * yc)[:, None]
+    assert np.abs(f.u[0] - ua).max() < 5e-3
+    n = 32
+    f = I.deformation_3d(n)
+    xf, xc = I.centres(n, f.h, 1.0), I.centres(n, f.h, 0.5)
+    ua = (2 * np.sin(np.pi * xf)[None, None, :] ** 2 * np.sin(2 * np.pi * xc)[None, :, None]
+          * np.sin(2 * np.pi * xc)[:, None, None])
+    assert np.abs(f.u - ua).max() < 2e-2
+    u, v, w = I.random_velocity((6, 7, 8), 0.1, 16, 4, 3)
+    div = sum(vel - np.roll(vel, 1, AX[d]) for d, vel in enumerate((u, v, w)))
+    assert np.abs(div).max() < 1e-10 and abs(I.face_umax(u, v, w) - 1.0) < 1e-15
+
+
+def test_stats():
+    """Oracle reductions against plain numpy on a field with planted violations."""
+    p = I.random_phi((4, 5, 6), 1)
+    p[0, 0, 0], p[1, 2, 3], p[3, 4, 5] = -1e-20, 1 + 1e-10, -0.3
+    s = oracle.stats(p, 0.5, 1e-15)
+    assert s["n_strict"] == 3 and s["n_tol"] == 2
+    assert s["min"] == -0.3 and s["max"] == 1 + 1e-10
+    assert abs(s["sum"] - p.sum()) < 1e-12 and abs(s["mass"] - 0.5 * p.sum()) < 1e-12
+
+
+# ---------------------------------------------------------------- adjoint pins
+
+def _fd_jvp(phi, u, v, w, dphi, args, hfd=1e-6):
+    a = oracle.step(phi + hfd * dphi, u, v, w, **args)
+    b = oracle.step(phi - hfd * dphi, u, v, w, **args)
+    return (a - b) / (2 * hfd)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 12), (1, 7, 8), (4, 5, 6)])
+def test_adjoint_dot_product(shape):
+    """<J dphi, lam> (central FD) == <dphi, J^T lam> (adjoint) to 1e-7 relative."""
+    rng = np.random.default_rng(7)
+    phi, u, v, w, h = rand_case(shape, 21)
+    phi = 0.1 + 0.8 * I.random_phi(shape, 3, smooth=True)
+    args = dict(dx=h, dt=0.2 * h * h, eps=1.2 * h, gamma=1.3, vel_scale=0.8)
+    lam = rng.standard_normal(shape)
+    dphi = rng.standard_normal(shape)
+    jv = _fd_jvp(phi, u, v, w, dphi, args)
+    jt = oracle.adjoint(phi, u, v, w, lam, **args)
+    lhs, rhs = (jv * lam).sum(), (dphi * jt).sum()
+    assert abs(lhs - rhs) <= 1e-7 * (abs(lhs) + abs(rhs))
+
+
+def test_adjoint_brute_force_transpose():
+    """Adjoint columns == rows of the FD Jacobian on a tiny box (every entry)."""
+    shape = (3, 4, 5)
+    phi, u, v, w, h = rand_case(shape, 31)
+    phi = 0.05 + 0.9 * I.random_phi(shape, 4, smooth=True)
+    args = dict(dx=h, dt=0.2 * h * h, eps=h, gamma=1.0, vel_scale=1.0)
+    n = phi.size
+    J = np.empty((n, n))
+    for c in range(n):
+        e = np.zeros(n)
+        e[c] = 1.0
+        J[:, c] = _fd_jvp(phi, u, v, w, e.reshape(shape), args).ravel()
+    for r in range(0, n, 7):
+        e = np.zeros(n)
+        e[r] = 1.0
+        col = oracle.adjoint(phi, u, v, w, e.reshape(shape), **args).ravel()
+        assert np.abs(col - J[r]).max() < 1e-7
+
+
+def test_adjoint_velocity_gradient():
+    """Velocity gradient of <lam, phi'> against central FD in each component."""
+    rng = np.random.default_rng(3)
+    shape = (4, 4, 5)
+    phi, u, v, w, h = rand_case(shape, 41)
+    args = dict(dx=h, dt=0.2 * h * h, eps=h, gamma=1.0, vel_scale=0.7)
+    lam = rng.standard_normal(shape)
+    _, gu, gv, gw = oracle.adjoint(phi, u, v, w, lam, want_vel=True, **args)
+    vel = [u, v, w]
+    for d, g in enumerate((gu, gv, gw)):
+        dv = rng.standard_normal(shape)
+        vp = [x.copy() for x in vel]
+        vm = [x.copy() for x in vel]
+        vp[d] += 1e-6 * dv
+        vm[d] -= 1e-6 * dv
+        fd = ((oracle.step(phi, *vp, **args) - oracle.step(phi, *vm, **args)) / 2e-6 * lam).sum()
+        assert abs(fd - (g * dv).sum()) <= 1e-7 * abs(fd) + 1e-12
+
+
+def test_adjoint_constant_lambda():
+    """lam' = const gives lam = lam' exactly: J^T 1 = 1 follows from conservation."""
+    phi, u, v, w, h = rand_case((4, 5, 6), 51, solenoidal=False)
+    lam = oracle.adjoint(phi, u, v, w, np.full(phi.shape, 2.5), h, 0.2 * h * h, h, 1.0)
+    assert np.abs(lam - 2.5).max() == 0.0
