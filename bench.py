@@ -1,0 +1,376 @@
+"""Benchmark of the fused CDI phase-field step on GB300.
+
+Workload (one "step" = one explicit Euler CDI step of the whole box):
+  256^3 periodic unit box, sphere R = 0.15 at (0.35, 0.35, 0.35) with the
+  tanh profile, 3D deformation face velocity (discrete curl of a staggered
+  vector potential) scaled by cos(pi t / 3), eps = dx, gamma = U (on the
+  crossover line of Eq. 17), dt = 0.1 dx / U.  FP32 stencil with FP64-summed
+  mass; FP64 and the adjoint step are measured on the same box.
+
+Metric: Gcell-updates/s of the FP32 step (whole job, all ranks).  Inputs
+(phi 64 MiB + three face velocities 192 MiB) exceed the 129 MB L2, so no
+flush is done between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the plain reference
+implementation of the same discretisation) on the host cores, on a bounded
+sample of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 256
+BYTES_F32 = 20   # phi read 4 + u, v, w 12 + phi write 4 per cell-update
+BYTES_F64 = 40
+BYTES_ADJ_F32 = 24  # phi, lam', u, v, w read + lam write
+FLOPS_PER_CELL = 51  # 17 per mesh point per direction (Section 3.3.3) x 3
+METRIC = "Gcell-updates/s per phi step (FP32 CDI step, 256^3 deformation)"
+PROFILE_F32 = os.path.join(ROOT, "profiles", "fwd_f32_deformation256.txt")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N, help="box edge (default 256)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("cdi_fwd.cu", "cdi_reduce.cuh", "cdi_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1803_01262_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it is current."""
+    if not os.path.exists(PROFILE_F32):
+        return None
+    kv = {}
+    for line in open(PROFILE_F32):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_source_sha") != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index),
+                                      f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.1)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_rate(fields, dt, eps, gamma, planes, steps):
+    """Gcell-updates/s of the oracle on `planes` z-planes of the box (periodic wrap)."""
+    import oracle
+    sub = [np.ascontiguousarray(x[:planes]) for x in (fields.phi, fields.u, fields.v, fields.w)]
+    oracle.step(*sub, fields.h, dt, eps, gamma)  # warm (build, page-in)
+    t = time.perf_counter()
+    p = sub[0]
+    for i in range(steps):
+        p = oracle.step(p, *sub[1:], fields.h, dt, eps, gamma, math.cos(math.pi * i * dt / 3.0))
+    el = time.perf_counter() - t
+    return p.size * steps / el / 1e9, el
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle timed on the host (rank 0 only)."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1803_01262_gb300 import inputs as I
+    import oracle
+    oracle.build()
+    f = I.deformation_3d(args.n)
+    dt, eps, gamma = 0.1 * f.h / f.U, f.h, f.U
+    # Bounded per-step sample so K + W steps take about two minutes at ~6 Mcell/s.
+    budget_cells = 6e6 * 120.0 / max(1, args.steps + args.warmup)
+    planes = int(max(1, min(args.n, budget_cells // (args.n * args.n))))
+    sub = [np.ascontiguousarray(x[:planes]) for x in (f.phi, f.u, f.v, f.w)]
+    p = sub[0]
+    for i in range(args.warmup):
+        p = oracle.step(p, *sub[1:], f.h, dt, eps, gamma)
+    t = time.perf_counter()
+    for i in range(args.steps):
+        p = oracle.step(p, *sub[1:], f.h, dt, eps, gamma, math.cos(math.pi * i * dt / 3.0))
+    el = time.perf_counter() - t
+    cells = p.size
+    val = cells * args.steps / el / 1e9
+    sample = (f"{planes} of {args.n} z-planes ({args.n}x{args.n}x{planes} = {cells} cells, periodic "
+              f"wrap) of the {args.n}^3 deformation box per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "Gcell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / max(1, args.steps) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"cdi_step_deformation_{args.n}^3", "sample_per_step": sample},
+        "cpu_baseline": {"value": val, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    from paper_1803_01262_gb300 import build as B
+    from paper_1803_01262_gb300 import cdi
+    from paper_1803_01262_gb300 import inputs as I
+
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    f = I.deformation_3d(args.n)   # every rank advances its own box (weak scaling)
+    dt, eps, gamma = 0.1 * f.h / f.U, f.h, f.U
+    T = 3.0
+    n = args.n
+    cells = n ** 3
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def maxrank(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def setup(dtype):
+        g = cdi.Grid(n, n, n, f.h, dtype)
+        vel = [torch.from_numpy(x).to(dev, dtype) for x in (f.u, f.v, f.w)]
+        g.set_velocity(*vel)
+        a = torch.from_numpy(f.phi).to(dev, dtype)
+        b = torch.empty_like(a)
+        return g, vel, a, b
+
+    def time_steps(step, K, W):
+        """W untimed + K timed calls of step(i); per-launch CUDA events on the launching stream."""
+        s = torch.cuda.current_stream()
+        for i in range(W):
+            step(i)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        start.record(s)
+        for i in range(K):
+            ev0[i].record(s)
+            step(W + i)
+            ev1[i].record(s)
+        stop.record(s)
+        barrier()
+        total_ms = start.elapsed_time(stop)
+        kern_ms = [e0.elapsed_time(e1) for e0, e1 in zip(ev0, ev1)]
+        return total_ms, kern_ms
+
+    def fwd_stepper(g, a, b):
+        buf = [a, b]
+
+        def step(i):
+            g.step(buf[i & 1], buf[(i + 1) & 1], dt, eps, gamma, math.cos(math.pi * i * dt / T))
+        return step
+
+    def adj_stepper(g, phi_k, la, lb):
+        buf = [la, lb]
+
+        def step(i):
+            g.step_adjoint(phi_k, buf[i & 1], buf[(i + 1) & 1], dt, eps, gamma,
+                           math.cos(math.pi * i * dt / T))
+        return step
+
+    K, W = args.steps, max(3, args.warmup)
+
+    # ---- FP32 fused step (the headline) ----
+    g32, vel32, a32, b32 = setup(torch.float32)
+    with ClockSampler(local) as clk:
+        total_ms, kern_ms = time_steps(fwd_stepper(g32, a32, b32), K, W)
+    total_ms = maxrank(total_ms)
+    st = g32.stats()
+    avg_kernel_ms = sum(kern_ms) / len(kern_ms)
+    ms_per_step = total_ms / K
+    value = ws * cells * K / (total_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    achieved = BYTES_F32 * cells / (avg_kernel_ms * 1e-3) / 1e9
+    traffic = profiled_traffic()
+
+    # ---- FP64 fused step on the same box ----
+    K64 = max(10, K // 4)
+    g64, vel64, a64, b64 = setup(torch.float64)
+    t64, k64 = time_steps(fwd_stepper(g64, a64, b64), K64, W)
+    t64 = maxrank(t64)
+    v64 = ws * cells * K64 / (t64 * 1e-3) / 1e9
+    avg64 = sum(k64) / len(k64)
+    del g64, vel64, a64, b64
+
+    # ---- FP32 adjoint step ----
+    Ka = max(10, K // 4)
+    lam_a = torch.from_numpy(np.random.default_rng(0).standard_normal((n, n, n))).to(dev, torch.float32)
+    lam_b = torch.empty_like(lam_a)
+    ta, ka = time_steps(adj_stepper(g32, a32, lam_a, lam_b), Ka, W)
+    ta = maxrank(ta)
+    avg_adj = sum(ka) / len(ka)
+    del lam_a, lam_b
+
+    # ---- end to end through the C ABI with host buffers ----
+    Ke = max(3, min(K, 50))
+    pin_in = torch.from_numpy(f.phi.astype(np.float32)).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    hin, hout = pin_in.numpy(), pin_out.numpy()
+    for i in range(3):
+        g32.step_host(hin, hout, dt, eps, gamma, 1.0)
+    barrier()
+    t0 = time.perf_counter()
+    for i in range(Ke):
+        g32.step_host(hin, hout, dt, eps, gamma, math.cos(math.pi * i * dt / T))
+        hin, hout = hout, hin
+    barrier()
+    te = maxrank(time.perf_counter() - t0)
+    e2e_val = ws * cells * Ke / te / 1e9
+    del g32, vel32, a32, b32
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and ws == 1:
+            planes = max(1, int(round(4 * 6e6 * 3 / (n * n))))  # about 4 s per step-sample set
+            planes = min(planes, n)
+            rate, el = cpu_oracle_rate(f, dt, eps, gamma, planes, 4)
+            cpu = {"value": rate, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
+                   "sample": f"4 FP64 oracle steps on {planes} of {n} z-planes of the {n}^3 box "
+                             f"({n}x{n}x{planes} cells, periodic wrap), {el:.1f} s, single thread"}
+        clocks = clk.summary()
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gcell-updates/s", "n_gpus": ws, "steps": K,
+            "warmup": W, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"cdi_step_deformation_{n}^3", "grid": [n, n, n],
+                       "eps_over_dx": 1.0, "gamma_over_U": 1.0, "cfl": 0.1,
+                       "reduction": "fp64 mass/min/max/violations fused per step",
+                       "l2": "inputs 268 MB > 129 MB L2, no flush",
+                       "parallelism": f"replicas{ws}" if ws > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind, "bytes_per_cell": BYTES_F32,
+                         "kernel_ms": avg_kernel_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "Gcell-updates/s",
+                    "h2d_bytes_per_step": cells * 4, "d2h_bytes_per_step": cells * 4 + 88,
+                    "api": "cdi_step_host (pinned host phi in, phi + stats out)"},
+            "gpu_launches": K,
+            "fp64": {"value": v64, "unit": "Gcell-updates/s", "ms_per_step": t64 / K64,
+                     "kernel_ms": avg64, "steps": K64,
+                     "achieved_gbs": BYTES_F64 * cells / (avg64 * 1e-3) / 1e9,
+                     "gflops_fp64": FLOPS_PER_CELL * cells / (avg64 * 1e-3) / 1e9,
+                     "fp32_speedup": value / v64},
+            "adjoint": {"kernel_ms": avg_adj, "ms_per_step": ta / Ka, "steps": Ka,
+                        "adj_over_fwd": avg_adj / avg_kernel_ms,
+                        "achieved_gbs": BYTES_ADJ_F32 * cells / (avg_adj * 1e-3) / 1e9},
+            "stats_last_step": {"mass": st["mass"], "min": st["min"], "max": st["max"],
+                                "n_tol": st["n_tol"]},
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

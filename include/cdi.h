@@ -1,0 +1,196 @@
+/*
+ * cdi.h -- C ABI of the GB300 (sm_103a) conservative diffuse interface
+ * (CDI) phase-field library.
+ *
+ * The library advances the phase field phi of Eq. 1 of Mirjalili, Ivey &
+ * Mani, "A conservative diffuse interface method for two-phase flows with
+ * provable boundedness properties" (arXiv 1803.01262):
+ *
+ *     d phi/dt + div(u phi) = div[ gamma ( eps grad phi - phi (1-phi) grad phi/|grad phi| ) ]
+ *
+ * discretised as in Section 2.2 on a periodic, uniform, isotropic staggered
+ * grid: phi at cell centres, velocity components on faces, second-order
+ * central differences, explicit Euler in time (Eq. 11 in 1D, Eq. 18-22 in
+ * coefficient form).  Per face between cells L and R along axis d:
+ *
+ *     F = (vs * u_f) (phi_L + phi_R)/2 - gamma eps (phi_R - phi_L)/dx
+ *         + gamma (s_L + s_R)/2,     s = phi (1 - phi) n_d,
+ *     n = g/|g|, g_d = phi_{c+e_d} - phi_{c-e_d}   (n = 0 where g = 0),
+ *     phi'_c = phi_c - (dt/dx) sum_d (F_{c+1/2 e_d} - F_{c-1/2 e_d}),
+ *
+ * where vs is the caller's velocity scale (the time factor of a
+ * time-periodic field, e.g. cos(pi t/T) in Eq. 33).
+ *
+ * Conventions shared by every call:
+ *  - Arrays are dense [nz][ny][nx] (x fastest), element type float
+ *    (CDI_F32) or double (CDI_F64) as fixed at grid creation.
+ *  - u[k][j][i] is the x-velocity on the face (i+1/2, j, k) (right face of
+ *    cell i); v on (i, j+1/2, k); w on (i, j, k+1/2).  All axes periodic.
+ *  - Device pointers are owned by the caller and borrowed for the duration
+ *    of the work enqueued by the call.  They must be aligned to 16 bytes.
+ *  - The library owns only small device scratch (per-block reduction
+ *    partials, a statistics record) allocated in cdi_create_grid.
+ *  - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every kernel is enqueued on it; nothing synchronises unless
+ *    the call says so.
+ *  - A grid (with its scratch) must be used by one stream at a time.
+ *  - Every call returns CDI_OK (0) or a negative CDI_ERR_* code and records
+ *    a message readable with cdi_last_error_string() (thread-local).  No
+ *    call aborts or throws.
+ */
+#ifndef CDI_H
+#define CDI_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CDI_VERSION 1
+
+#if defined(__GNUC__)
+#define CDI_API __attribute__((visibility("default")))
+#else
+#define CDI_API
+#endif
+
+enum {
+    CDI_OK = 0,
+    CDI_ERR_ARG = -1,        /* bad pointer, size, or parameter value      */
+    CDI_ERR_DIM = -2,        /* grid extent out of range                   */
+    CDI_ERR_CUDA = -3,       /* a CUDA runtime call failed                 */
+    CDI_ERR_CONDITION = -4,  /* Eq. 17/24 or A <= 1/(2 D_f) not satisfied */
+    CDI_ERR_NAN = -5,        /* non-finite value detected in a reduction   */
+    CDI_ERR_TIMEOUT = -6,    /* a bounded device-side wait gave up         */
+    CDI_ERR_STATE = -7       /* call out of order (e.g. no velocity set)   */
+};
+
+enum { CDI_F32 = 0, CDI_F64 = 1 };
+
+/* Time schemes for cdi_max_dt (Eq. 25-28). */
+enum { CDI_EULER = 0, CDI_RK2 = 1, CDI_RK3 = 2, CDI_RK4 = 3 };
+
+/* Flags of cdi_step / cdi_run. */
+#define CDI_CHECK_CONDITION 1  /* refuse (CDI_ERR_CONDITION) unless Eq. 24 and A <= 1/(2 D_f) hold */
+
+typedef struct cdi_grid cdi_grid;
+
+/*
+ * Mass and bounds of a phase field (conservation, Section 2.2.1 and
+ * Fig. 5c; boundedness criterion of Section 3.2).
+ *   mass      = dV * sum(phi), dV = dx^D_f, D_f = number of axes with extent > 1
+ *   n_strict  = #(phi < 0 or phi > 1)
+ *   n_tol     = #(phi < -tol or phi > 1 + tol), tol = machine epsilon of the dtype
+ * The *_run fields accumulate over every fused step since the last
+ * cdi_reset_run_stats (min/max over steps, summed violation counts).
+ * Sums are accumulated in double on the device in a fixed order, so a
+ * result is reproducible run to run.
+ */
+typedef struct cdi_stats {
+    double mass;
+    double sum;
+    double min;
+    double max;
+    long long n_strict;
+    long long n_tol;
+    double min_run;
+    double max_run;
+    long long n_strict_run;
+    long long n_tol_run;
+    long long steps_run;
+} cdi_stats;
+
+/* Create a periodic nx x ny x nz grid of spacing dx (> 0) holding phi of
+ * type dtype.  ny = nz = 1 (nz = 1) gives the 1D (2D) scheme exactly.
+ * Extents must be >= 1 with nx*ny < 2^31 and nx*ny*nz < 2^36.  Allocates the
+ * reduction scratch (device memory) on the current device. */
+CDI_API int cdi_create_grid(cdi_grid **g, int nx, int ny, int nz, double dx, int dtype);
+
+/* Free a grid and its scratch (NULL is a no-op).  Does not synchronise
+ * beyond what cudaFree implies. */
+CDI_API int cdi_destroy_grid(cdi_grid *g);
+
+/* Query extents, spacing and dtype. */
+CDI_API int cdi_grid_info(const cdi_grid *g, int *nx, int *ny, int *nz, double *dx, int *dtype);
+
+/* Borrow face velocities (device, dtype of the grid).  w may be NULL only
+ * when nz == 1 (w is then inert: the z-faces coincide, Eq. 18 in 2D); v
+ * likewise when ny == 1 and nz == 1.  umax >= 0 sets U, the largest face
+ * |component| used by the condition check (Eq. 24); umax < 0 computes U on
+ * the device (synchronises the stream). */
+CDI_API int cdi_set_velocity(cdi_grid *g, const void *u, const void *v, const void *w,
+                     double umax, void *stream);
+
+/* U as set or computed by cdi_set_velocity. */
+CDI_API int cdi_get_umax(const cdi_grid *g, double *U);
+
+/* One explicit Euler step phi_out = phi_in + dt * RHS(phi_in) (Eq. 11 / 18),
+ * with face velocity vel_scale * (u, v, w).  phi_in and phi_out are device
+ * arrays of nx*ny*nz elements and must not overlap.  The fused reduction
+ * (cdi_stats of phi_out) is written to the grid's device record; read it
+ * with cdi_step_stats.  With CDI_CHECK_CONDITION the call first checks
+ * eps/dx >= (g + 1)/(2 g), g = gamma/(|vel_scale| U) (Eq. 24), and
+ * A = dt gamma eps/dx^2 <= 1/(2 D_f) (Eq. 25) and returns
+ * CDI_ERR_CONDITION without launching if either fails. */
+CDI_API int cdi_step(cdi_grid *g, const void *phi_in, void *phi_out, double dt, double eps,
+             double gamma, double vel_scale, int flags, void *stream);
+
+/* nsteps Euler steps starting at time t0, ping-ponging between buf_a (holds
+ * phi at t0 on entry) and buf_b; vel_scale = cos(pi t / period) at each
+ * step's start time t (period <= 0: vel_scale = 1).  The launch loop runs
+ * in native code.  On return *final_in_b tells which buffer holds the
+ * result.  Stats of the last step are in the device record. */
+CDI_API int cdi_run(cdi_grid *g, void *buf_a, void *buf_b, int nsteps, double t0, double dt,
+            double eps, double gamma, double period, int flags, int *final_in_b,
+            void *stream);
+
+/* Copy the device statistics record of the last fused step to *out;
+ * synchronises the stream.  Returns CDI_ERR_NAN if the sum is not finite. */
+CDI_API int cdi_step_stats(cdi_grid *g, cdi_stats *out, void *stream);
+
+/* Reset the run accumulators (*_run, steps_run) of the device record. */
+CDI_API int cdi_reset_run_stats(cdi_grid *g, void *stream);
+
+/* Reduce an arbitrary phi (device) into *out (host); synchronises. */
+CDI_API int cdi_mass_and_bounds(cdi_grid *g, const void *phi, cdi_stats *out, void *stream);
+
+/* Host-buffer step: copies phi_in (host, ideally pinned) to the device,
+ * performs cdi_step with the velocity set by cdi_set_velocity, copies
+ * phi_out and the statistics back to host memory and synchronises.  Uses
+ * two device staging buffers owned by the grid (allocated on first use). */
+CDI_API int cdi_step_host(cdi_grid *g, const void *phi_in_host, void *phi_out_host, double dt,
+                  double eps, double gamma, double vel_scale, int flags,
+                  cdi_stats *stats_out, void *stream);
+
+/*
+ * Discrete adjoint of one Euler step (reverse mode through the five steps
+ * of Section 2.2).  With J = d phi^{k+1}/d phi^k at phi_k:
+ *     lam_k = J^T lam_next
+ * and, if gu/gv/gw are non-NULL, (d phi^{k+1}/d u_f)^T lam_next is ADDED to
+ * them (accumulated over steps by the caller).  phi_k is the forward input
+ * of the step (recomputed by the caller from a checkpoint).  lam_k must not
+ * overlap lam_next or phi_k.  Same dt/eps/gamma/vel_scale as the forward.
+ */
+CDI_API int cdi_step_adjoint(cdi_grid *g, const void *phi_k, const void *lam_next, void *lam_k,
+                     void *gu, void *gv, void *gw, double dt, double eps, double gamma,
+                     double vel_scale, void *stream);
+
+/* Boundedness condition (Eq. 17/24 with U the face maximum) and the Euler
+ * diffusive limit A <= 1/(2 D_f) (Eq. 25).  Returns 1 if both hold, 0 if
+ * not, CDI_ERR_ARG on bad input.  gamma_over_U = +inf is allowed. */
+CDI_API int cdi_check_condition(double eps_over_dx, double gamma_over_U, double A, int Df);
+
+/* Largest stable, bounded time step for a scheme above the crossover line:
+ * Euler and RK2 dx^2/(2 D_f gamma eps) (Eq. 25, 26), RK3 2.51 dx^2/(4 D_f
+ * gamma eps) (Eq. 27), RK4 2.79 dx^2/(4 D_f gamma eps) (Eq. 28). */
+CDI_API int cdi_max_dt(double dx, double eps, double gamma, int Df, int scheme, double *dt);
+
+/* Message of the last failed call on this thread ("" if none). */
+CDI_API const char *cdi_last_error_string(void);
+
+/* CDI_VERSION of the loaded library. */
+CDI_API int cdi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CDI_H */

@@ -1,0 +1,231 @@
+"""Thin Python binding of the CDI C ABI (include/cdi.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``_lib/libcdi.so``.  Device arrays are torch CUDA tensors shaped
+``(nz, ny, nx)``, contiguous, of the grid's dtype; streams are torch streams
+(default: the current stream).  There is no fallback: if the library is
+missing or fails to load, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libcdi.so")
+
+CDI_OK, CDI_ERR_ARG, CDI_ERR_DIM, CDI_ERR_CUDA = 0, -1, -2, -3
+CDI_ERR_CONDITION, CDI_ERR_NAN, CDI_ERR_TIMEOUT, CDI_ERR_STATE = -4, -5, -6, -7
+CDI_F32, CDI_F64 = 0, 1
+CDI_EULER, CDI_RK2, CDI_RK3, CDI_RK4 = 0, 1, 2, 3
+CDI_CHECK_CONDITION = 1
+
+_ERRNAMES = {-1: "CDI_ERR_ARG", -2: "CDI_ERR_DIM", -3: "CDI_ERR_CUDA", -4: "CDI_ERR_CONDITION",
+             -5: "CDI_ERR_NAN", -6: "CDI_ERR_TIMEOUT", -7: "CDI_ERR_STATE"}
+
+
+class CDIError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("sum", ctypes.c_double), ("min", ctypes.c_double),
+                ("max", ctypes.c_double), ("n_strict", ctypes.c_longlong),
+                ("n_tol", ctypes.c_longlong), ("min_run", ctypes.c_double),
+                ("max_run", ctypes.c_double), ("n_strict_run", ctypes.c_longlong),
+                ("n_tol_run", ctypes.c_longlong), ("steps_run", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_V = ctypes.c_void_p
+_I = ctypes.c_int
+_Dbl = ctypes.c_double
+_P = ctypes.POINTER
+
+# name -> argtypes (all return int unless listed in _RESTYPE)
+SIGNATURES = {
+    "cdi_version": [],
+    "cdi_last_error_string": [],
+    "cdi_create_grid": [_P(_V), _I, _I, _I, _Dbl, _I],
+    "cdi_destroy_grid": [_V],
+    "cdi_grid_info": [_V, _P(_I), _P(_I), _P(_I), _P(_Dbl), _P(_I)],
+    "cdi_set_velocity": [_V, _V, _V, _V, _Dbl, _V],
+    "cdi_get_umax": [_V, _P(_Dbl)],
+    "cdi_step": [_V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _I, _V],
+    "cdi_run": [_V, _V, _V, _I, _Dbl, _Dbl, _Dbl, _Dbl, _Dbl, _I, _P(_I), _V],
+    "cdi_step_stats": [_V, _P(Stats), _V],
+    "cdi_reset_run_stats": [_V, _V],
+    "cdi_mass_and_bounds": [_V, _V, _P(Stats), _V],
+    "cdi_step_host": [_V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _I, _P(Stats), _V],
+    "cdi_step_adjoint": [_V, _V, _V, _V, _V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _V],
+    "cdi_check_condition": [_Dbl, _Dbl, _Dbl, _I],
+    "cdi_max_dt": [_Dbl, _Dbl, _Dbl, _I, _I, _P(_Dbl)],
+}
+_RESTYPE = {"cdi_last_error_string": ctypes.c_char_p}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libcdi.so (built by ``paper_1803_01262_gb300.build``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise CDIError(CDI_ERR_STATE, f"CUDA library not built: {LIB_PATH} is missing "
+                                              "(run paper_1803_01262_gb300.build.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = _RESTYPE.get(name, ctypes.c_int)
+            _lib = L
+    return _lib
+
+
+def _err():
+    return lib().cdi_last_error_string().decode(errors="replace")
+
+
+def _ck(rc):
+    if rc < 0:
+        raise CDIError(rc, _err())
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(dtype):
+    if dtype == torch.float32:
+        return CDI_F32
+    if dtype == torch.float64:
+        return CDI_F64
+    raise ValueError("dtype must be torch.float32 or torch.float64")
+
+
+def check_condition(eps_over_dx, gamma_over_U, A, Df):
+    """Eq. 17/24 and A <= 1/(2 D_f): True if both hold."""
+    return bool(_ck(lib().cdi_check_condition(eps_over_dx, gamma_over_U, A, Df)))
+
+
+def max_dt(dx, eps, gamma, Df, scheme=CDI_EULER):
+    """Largest bounded step of Eq. 25-28 for the given scheme."""
+    out = ctypes.c_double()
+    _ck(lib().cdi_max_dt(dx, eps, gamma, Df, scheme, ctypes.byref(out)))
+    return out.value
+
+
+class Grid:
+    """A periodic nx x ny x nz grid of spacing dx on the current CUDA device."""
+
+    def __init__(self, nx, ny, nz, dx, dtype=torch.float32):
+        self.shape = (nz, ny, nx)
+        self.dx = float(dx)
+        self.dtype = dtype
+        self._h = ctypes.c_void_p()
+        _ck(lib().cdi_create_grid(ctypes.byref(self._h), nx, ny, nz, self.dx, _dtype_code(dtype)))
+        self._vel = None
+
+    @property
+    def Df(self):
+        return sum(1 for s in self.shape if s > 1)
+
+    def close(self):
+        if self._h:
+            lib().cdi_destroy_grid(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _arr(self, t, name):
+        if t is None:
+            return None
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.dtype or tuple(t.shape) != self.shape or not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous {self.dtype} of shape {self.shape}")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def set_velocity(self, u, v, w=None, umax=None, stream=None):
+        """Borrow face velocities; U computed on the device unless umax is given."""
+        _ck(lib().cdi_set_velocity(self._h, self._arr(u, "u"), self._arr(v, "v"),
+                                   self._arr(w, "w"), -1.0 if umax is None else float(umax),
+                                   _stream(stream)))
+        self._vel = (u, v, w)  # keep the borrowed storage alive
+
+    @property
+    def U(self):
+        out = ctypes.c_double()
+        _ck(lib().cdi_get_umax(self._h, ctypes.byref(out)))
+        return out.value
+
+    def step(self, phi_in, phi_out, dt, eps, gamma, vel_scale=1.0, check=False, stream=None):
+        """phi_out = one Euler CDI step of phi_in (fused statistics in the record)."""
+        _ck(lib().cdi_step(self._h, self._arr(phi_in, "phi_in"), self._arr(phi_out, "phi_out"),
+                           dt, eps, gamma, vel_scale, CDI_CHECK_CONDITION if check else 0,
+                           _stream(stream)))
+        return phi_out
+
+    def run(self, a, b, nsteps, dt, eps, gamma, period=0.0, t0=0.0, check=False, stream=None):
+        """nsteps steps ping-ponging a <-> b (native loop); returns the result tensor."""
+        fb = ctypes.c_int()
+        _ck(lib().cdi_run(self._h, self._arr(a, "a"), self._arr(b, "b"), nsteps, t0, dt, eps,
+                          gamma, period, CDI_CHECK_CONDITION if check else 0, ctypes.byref(fb),
+                          _stream(stream)))
+        return b if fb.value else a
+
+    def stats(self, stream=None):
+        """Statistics of the last fused step (synchronises)."""
+        s = Stats()
+        _ck(lib().cdi_step_stats(self._h, ctypes.byref(s), _stream(stream)))
+        return s.as_dict()
+
+    def reset_run_stats(self, stream=None):
+        _ck(lib().cdi_reset_run_stats(self._h, _stream(stream)))
+
+    def mass_and_bounds(self, phi, stream=None):
+        s = Stats()
+        _ck(lib().cdi_mass_and_bounds(self._h, self._arr(phi, "phi"), ctypes.byref(s),
+                                      _stream(stream)))
+        return s.as_dict()
+
+    def step_host(self, phi_in, phi_out, dt, eps, gamma, vel_scale=1.0, check=False,
+                  stream=None):
+        """Host-buffer step (numpy arrays, ideally pinned); returns the statistics."""
+        for a in (phi_in, phi_out):
+            if not isinstance(a, np.ndarray) or a.shape != self.shape or not a.flags.c_contiguous:
+                raise ValueError("host arrays must be C-contiguous numpy arrays of the grid shape")
+        s = Stats()
+        _ck(lib().cdi_step_host(self._h, ctypes.c_void_p(phi_in.ctypes.data),
+                                ctypes.c_void_p(phi_out.ctypes.data), dt, eps, gamma, vel_scale,
+                                CDI_CHECK_CONDITION if check else 0, ctypes.byref(s),
+                                _stream(stream)))
+        return s.as_dict()
+
+    def step_adjoint(self, phi_k, lam_next, lam_k, dt, eps, gamma, vel_scale=1.0, grads=None,
+                     stream=None):
+        """lam_k = J^T lam_next; if grads=(gu, gv, gw) the velocity gradient is added to them."""
+        g = grads if grads is not None else (None, None, None)
+        _ck(lib().cdi_step_adjoint(self._h, self._arr(phi_k, "phi_k"),
+                                   self._arr(lam_next, "lam_next"), self._arr(lam_k, "lam_k"),
+                                   self._arr(g[0], "gu"), self._arr(g[1], "gv"),
+                                   self._arr(g[2], "gw"), dt, eps, gamma, vel_scale,
+                                   _stream(stream)))
+        return lam_k

@@ -1,0 +1,230 @@
+// Discrete adjoint of one explicit CDI step (reverse mode through the five
+// steps of Section 2.2), lam_k = (d phi^{k+1}/d phi^k)^T lam_{k+1}, for sm_103a.
+//
+// In gather form, for cell c with faces f = c +- 1/2 e_d:
+//   Fbar_f      = (dt/dx) (lam'_R - lam'_L)
+//   sbar_d(c)   = (gamma dt / 2dx) (lam'_{c+e_d} - lam'_{c-e_d})
+//   nbar(c)     = sbar(c) phi_c (1 - phi_c)
+//   gbar(c)     = (nbar - n (n . nbar)) / |g|         (0 where g = 0)
+//   phibar_c    = sum_d [ Fbar_{c+1/2}(vs u_{c+1/2}/2 + gamma eps/dx)
+//                       + Fbar_{c-1/2}(vs u_{c-1/2}/2 - gamma eps/dx) ]
+//               + (1 - 2 phi_c) (sbar(c) . n_c)
+//               + sum_d ( gbar_d(c - e_d) - gbar_d(c + e_d) )
+//   lam_c       = lam'_c + phibar_c
+//   ubar_{c+1/2} += Fbar_{c+1/2} vs (phi_c + phi_{c+e_d}) / 2     (optional)
+// The structure mirrors the forward kernel: phi and lam' planes staged with a
+// halo of 2 in 4-slot shared rings, gbar_x / gbar_y on a one-cell ring in a
+// 2-slot shared buffer, gbar_z and the z-face term carried in registers.
+#include "cdi_internal.cuh"
+
+namespace cdi {
+
+__device__ __forceinline__ float rsqrt_a(float q) { return rsqrtf(q); }
+__device__ __forceinline__ double rsqrt_a(double q) { return rsqrt(q); }
+
+template <typename T, int BX, int BY>
+struct AdjSmem {
+    static constexpr int PX = BX + 4, PY = BY + 4;
+    static constexpr size_t bytes =
+        sizeof(T) * (2 * 4 * PY * PX + 2 * BY * (BX + 2) + 2 * (BY + 2) * BX);
+};
+
+template <typename T, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+adj_kernel(const AdjArgs<T> a)
+{
+    constexpr int PX = BX + 4, PY = BY + 4, PLANE = PX * PY;
+    constexpr int NT = BX * BY;
+    constexpr int NLOAD = (PLANE + NT - 1) / NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T(*sp)[PY][PX] = reinterpret_cast<T(*)[PY][PX]>(smem_raw);          // phi ring [4]
+    T(*sl)[PY][PX] = sp + 4;                                            // lam' ring [4]
+    T(*gxs)[BY][BX + 2] = reinterpret_cast<T(*)[BY][BX + 2]>(sl + 4);   // gbar_x [2]
+    T(*gys)[BY + 2][BX] = reinterpret_cast<T(*)[BY + 2][BX]>(gxs + 2);  // gbar_y [2]
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    const long long plane = (long long)nx * ny;
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, nz);
+
+    int loff[NLOAD];
+#pragma unroll
+    for (int r = 0; r < NLOAD; ++r) {
+        const int e = tid + r * NT;
+        const int ey = e / PX, ex = e - ey * PX;
+        loff[r] = (e < PLANE) ? wrapi(y0 + ey - 2, ny) * nx + wrapi(x0 + ex - 2, nx) : 0;
+    }
+    const int gx = wrapi(x0 + tx, nx), gy = wrapi(y0 + ty, ny);
+    const bool own = (x0 + tx < nx) && (y0 + ty < ny);
+    const int oc = gy * nx + gx;
+    const int oxm = gy * nx + wrapi(gx - 1, nx);
+    const int oym = wrapi(gy - 1, ny) * nx + gx;
+
+    int rkind = 0, rx = 0, ry = 0;
+    if (tid < 2 * BX) {
+        rkind = 1;
+        rx = tid % BX;
+        ry = tid < BX ? -1 : BY;
+    } else if (tid < 2 * BX + 2 * BY) {
+        rkind = 2;
+        const int r = tid - 2 * BX;
+        ry = r % BY;
+        rx = r < BY ? -1 : BX;
+    }
+
+    const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_upd = a.c.c_upd, c_sb = a.c_shp_adj;
+    const T c_vel = a.c_vel;
+    const bool want_vel = a.gu != nullptr;
+
+    auto load_plane = [&](int z) {
+        const long long zo = (long long)wrapi(z, nz) * plane;
+        T *dp = &sp[z & 3][0][0];
+        T *dl = &sl[z & 3][0][0];
+#pragma unroll
+        for (int r = 0; r < NLOAD; ++r) {
+            const int e = tid + r * NT;
+            if (e < PLANE) {
+                dp[e] = __ldg(a.phi + zo + loff[r]);
+                dl[e] = __ldg(a.lam + zo + loff[r]);
+            }
+        }
+    };
+    // gbar (3-vector) and the local term (1 - 2 phi)(sbar . n) at cell (lx, ly) of plane z.
+    auto gbar = [&](int z, int lx, int ly, T &b0, T &b1, T &b2, T &tloc) {
+        const int X = lx + 2, Y = ly + 2;
+        const int m = z & 3, mm = (z - 1) & 3, mp = (z + 1) & 3;
+        const T p = sp[m][Y][X];
+        const T g0 = sp[m][Y][X + 1] - sp[m][Y][X - 1];
+        const T g1 = sp[m][Y + 1][X] - sp[m][Y - 1][X];
+        const T g2 = sp[mp][Y][X] - sp[mm][Y][X];
+        const T q = g0 * g0 + g1 * g1 + g2 * g2;
+        const T inv = q > T(0) ? rsqrt_a(q) : T(0);
+        const T n0 = g0 * inv, n1 = g1 * inv, n2 = g2 * inv;
+        const T sb0 = c_sb * (sl[m][Y][X + 1] - sl[m][Y][X - 1]);
+        const T sb1 = c_sb * (sl[m][Y + 1][X] - sl[m][Y - 1][X]);
+        const T sb2 = c_sb * (sl[mp][Y][X] - sl[mm][Y][X]);
+        const T sdn = sb0 * n0 + sb1 * n1 + sb2 * n2;
+        tloc = (T(1) - T(2) * p) * sdn;
+        // nbar = sbar p (1 - p);  gbar = (nbar - n (n . nbar)) / |g|
+        const T w = p * (T(1) - p) * inv;
+        b0 = w * (sb0 - n0 * sdn);
+        b1 = w * (sb1 - n1 * sdn);
+        b2 = w * (sb2 - n2 * sdn);
+    };
+    auto gbar_plane = [&](int z, T &gzc, T &tc) {
+        T b0, b1;
+        gbar(z, tx, ty, b0, b1, gzc, tc);
+        gxs[z & 1][ty][tx + 1] = b0;
+        gys[z & 1][ty + 1][tx] = b1;
+        if (rkind) {
+            T r0, r1, r2, rt;
+            gbar(z, rx, ry, r0, r1, r2, rt);
+            if (rkind == 1) gys[z & 1][ry + 1][rx] = r1;
+            else gxs[z & 1][ry][rx + 1] = r0;
+        }
+    };
+
+    load_plane(z0 - 2);
+    load_plane(z0 - 1);
+    load_plane(z0);
+    load_plane(z0 + 1);
+    __syncthreads();
+    T gz_m, gz_c, t_c;
+    {
+        T d0, d1, dt_;
+        gbar(z0 - 1, tx, ty, d0, d1, gz_m, dt_);
+    }
+    gbar_plane(z0, gz_c, t_c);
+    T Tzm;
+    {
+        const T wlo = __ldg(a.w + (long long)wrapi(z0 - 1, nz) * plane + oc);
+        const T Fb = c_upd * (sl[z0 & 3][ty + 2][tx + 2] - sl[(z0 - 1) & 3][ty + 2][tx + 2]);
+        Tzm = Fb * (c_adv * wlo - c_dif);
+    }
+    __syncthreads();
+
+    for (int k = z0; k < z1; ++k) {
+        load_plane(k + 2);
+        const long long zb = (long long)k * plane;
+        const T uc = __ldg(a.u + zb + oc), um = __ldg(a.u + zb + oxm);
+        const T vc = __ldg(a.v + zb + oc), vm = __ldg(a.v + zb + oym);
+        const T wc = __ldg(a.w + zb + oc);
+        __syncthreads();
+        T gz_p, t_p;
+        gbar_plane(k + 1, gz_p, t_p);
+        __syncthreads();
+        const int m = k & 3, b = k & 1, mp = (k + 1) & 3;
+        const T lc = sl[m][ty + 2][tx + 2];
+        const T Fxp = c_upd * (sl[m][ty + 2][tx + 3] - lc);
+        const T Fxm = c_upd * (lc - sl[m][ty + 2][tx + 1]);
+        const T Fyp = c_upd * (sl[m][ty + 3][tx + 2] - lc);
+        const T Fym = c_upd * (lc - sl[m][ty + 1][tx + 2]);
+        const T Fzp = c_upd * (sl[mp][ty + 2][tx + 2] - lc);
+        T pb = Fxp * (c_adv * uc + c_dif) + Fxm * (c_adv * um - c_dif);
+        pb += Fyp * (c_adv * vc + c_dif) + Fym * (c_adv * vm - c_dif);
+        pb += Fzp * (c_adv * wc + c_dif) + Tzm;
+        pb += t_c;
+        pb += (gxs[b][ty][tx] - gxs[b][ty][tx + 2]) + (gys[b][ty][tx] - gys[b][ty + 2][tx]) +
+              (gz_m - gz_p);
+        if (own) {
+            a.out[zb + oc] = lc + pb;
+            if (want_vel) {
+                const T pc = sp[m][ty + 2][tx + 2];
+                a.gu[zb + oc] += Fxp * c_vel * (pc + sp[m][ty + 2][tx + 3]);
+                a.gv[zb + oc] += Fyp * c_vel * (pc + sp[m][ty + 3][tx + 2]);
+                a.gw[zb + oc] += Fzp * c_vel * (pc + sp[mp][ty + 2][tx + 2]);
+            }
+        }
+        Tzm = Fzp * (c_adv * wc - c_dif);
+        gz_m = gz_c;
+        gz_c = gz_p;
+        t_c = t_p;
+    }
+}
+
+struct TileDimA { int bx, by; };
+static const TileDimA kATiles[] = {{32, 8}, {32, 16}, {32, 4}};
+static const int kNumATiles = sizeof(kATiles) / sizeof(kATiles[0]);
+
+int adj_num_tiles() { return kNumATiles; }
+
+int adj_blocks(int tile, int zchunk, int nx, int ny, int nz)
+{
+    const TileDimA t = kATiles[tile];
+    return ((nx + t.bx - 1) / t.bx) * ((ny + t.by - 1) / t.by) * ((nz + zchunk - 1) / zchunk);
+}
+
+template <typename T, int BX, int BY>
+static cudaError_t launch_adj_t(const AdjArgs<T> &a, cudaStream_t s)
+{
+    const size_t smem = AdjSmem<T, BX, BY>::bytes;
+    static bool attr_set = false;  // per instantiation; idempotent if raced
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(adj_kernel<T, BX, BY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + a.zchunk - 1) / a.zchunk);
+    dim3 block(BX, BY);
+    adj_kernel<T, BX, BY><<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adj(const AdjArgs<T> &a, int tile, cudaStream_t s)
+{
+    switch (tile) {
+    case 0: return launch_adj_t<T, 32, 8>(a, s);
+    case 1: return launch_adj_t<T, 32, 16>(a, s);
+    case 2: return launch_adj_t<T, 32, 4>(a, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_adj<float>(const AdjArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_adj<double>(const AdjArgs<double> &, int, cudaStream_t);
+
+}  // namespace cdi

@@ -1,0 +1,480 @@
+// C ABI of the CDI library (declared in include/cdi.h): argument checking,
+// scratch ownership, launch-configuration choice and the native launch loop.
+#include <cuda_runtime.h>
+#include <float.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "cdi.h"
+#include "cdi_internal.cuh"
+
+using cdi::LaunchCfg;
+using cdi::RedScratch;
+using cdi::StatsRec;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(CDI_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+constexpr int kZMin = 8;          // smallest z chunk any launch uses
+constexpr int kStatsBlocks = 1216; // 8 blocks of 256 threads per SM on 152 SMs
+
+}  // namespace
+
+struct cdi_grid {
+    int nx, ny, nz;
+    double dx;
+    int dtype;
+    int Df;
+    long long n;
+    const void *u, *v, *w;
+    double U;
+    int vel_set;
+    // reduction scratch (owned)
+    cdi::Partial *partials;
+    unsigned int *counter;
+    StatsRec *rec;    // fused-step record
+    StatsRec *rec2;   // stand-alone reductions
+    int capacity;
+    // launch configuration of the forward and adjoint kernels
+    LaunchCfg fwd, adj;
+    // staging for cdi_step_host (owned, allocated on first use)
+    void *stage_in, *stage_out;
+    int sm_count;
+};
+
+static size_t esize(const cdi_grid *g) { return g->dtype == CDI_F64 ? 8 : 4; }
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+static int check_grid(const cdi_grid *g)
+{
+    if (!g) return fail(CDI_ERR_ARG, "grid is NULL");
+    return CDI_OK;
+}
+
+static RedScratch scratch(const cdi_grid *g, StatsRec *rec, int update_run)
+{
+    RedScratch r;
+    r.partials = g->partials;
+    r.counter = g->counter;
+    r.rec = rec;
+    r.capacity = g->capacity;
+    r.dV = pow(g->dx, (double)g->Df);
+    r.update_run = update_run;
+    return r;
+}
+
+static void reset_run_host(StatsRec *r)
+{
+    memset(r, 0, sizeof(*r));
+    r->mn = INFINITY;
+    r->mx = -INFINITY;
+    r->mn_run = INFINITY;
+    r->mx_run = -INFINITY;
+}
+
+// Default launch configuration: 32 x 16 tiles (32 x 4 for narrow grids) and a
+// z chunk giving about eight resident blocks per SM.
+static LaunchCfg default_cfg(const cdi_grid *g)
+{
+    LaunchCfg c;
+    c.tile = (g->nx >= 32 && g->ny >= 16) ? 1 : 3;
+    int bx, by;
+    cdi::fwd_tile_dims(c.tile, &bx, &by);
+    long long tiles = (long long)((g->nx + bx - 1) / bx) * ((g->ny + by - 1) / by);
+    long long want = (long long)g->sm_count * 8;
+    long long zc = (g->nz * tiles + want - 1) / want;
+    if (zc < kZMin) zc = kZMin;
+    if (zc > g->nz) zc = g->nz;
+    c.zchunk = (int)zc;
+    return c;
+}
+
+// The public functions keep C linkage from their declarations in cdi.h.
+
+int cdi_version(void) { return CDI_VERSION; }
+
+const char *cdi_last_error_string(void) { return g_err; }
+
+int cdi_create_grid(cdi_grid **out, int nx, int ny, int nz, double dx, int dtype)
+{
+    if (!out) return fail(CDI_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(CDI_ERR_DIM, "extents must be >= 1 (got %d %d %d)", nx, ny, nz);
+    if ((long long)nx * ny >= (1LL << 31)) return fail(CDI_ERR_DIM, "nx*ny must be < 2^31");
+    if ((long long)nx * ny * nz >= (1LL << 36)) return fail(CDI_ERR_DIM, "nx*ny*nz must be < 2^36");
+    if (!(dx > 0.0) || !isfinite(dx)) return fail(CDI_ERR_ARG, "dx must be finite and > 0");
+    if (dtype != CDI_F32 && dtype != CDI_F64) return fail(CDI_ERR_ARG, "dtype must be CDI_F32 or CDI_F64");
+    cdi_grid *g = new cdi_grid();
+    memset(g, 0, sizeof(*g));
+    g->nx = nx; g->ny = ny; g->nz = nz; g->dx = dx; g->dtype = dtype;
+    g->Df = (nx > 1) + (ny > 1) + (nz > 1);
+    g->n = (long long)nx * ny * nz;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaGetDevice"); }
+    e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+    int cap = kStatsBlocks;
+    for (int t = 0; t < cdi::fwd_num_tiles(); ++t) {
+        int b = cdi::fwd_blocks(t, kZMin, nx, ny, nz);
+        if (b > cap) cap = b;
+    }
+    for (int t = 0; t < cdi::adj_num_tiles(); ++t) {
+        int b = cdi::adj_blocks(t, kZMin, nx, ny, nz);
+        if (b > cap) cap = b;
+    }
+    g->capacity = cap;
+    if ((e = cudaMalloc(&g->partials, sizeof(cdi::Partial) * (size_t)cap)) != cudaSuccess ||
+        (e = cudaMalloc(&g->counter, sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMalloc(&g->rec, sizeof(StatsRec))) != cudaSuccess ||
+        (e = cudaMalloc(&g->rec2, sizeof(StatsRec))) != cudaSuccess) {
+        cdi_destroy_grid(g);
+        return cuda_fail(e, "cudaMalloc(scratch)");
+    }
+    StatsRec h;
+    reset_run_host(&h);
+    if ((e = cudaMemset(g->counter, 0, sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMemcpy(g->rec, &h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(g->rec2, &h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess) {
+        cdi_destroy_grid(g);
+        return cuda_fail(e, "scratch init");
+    }
+    g->fwd = default_cfg(g);
+    g->adj.tile = (nx >= 32 && ny >= 16) ? 1 : 2;
+    g->adj.zchunk = g->fwd.zchunk;
+    *out = g;
+    return CDI_OK;
+}
+
+int cdi_destroy_grid(cdi_grid *g)
+{
+    if (!g) return CDI_OK;
+    cudaFree(g->partials);
+    cudaFree(g->counter);
+    cudaFree(g->rec);
+    cudaFree(g->rec2);
+    cudaFree(g->stage_in);
+    cudaFree(g->stage_out);
+    delete g;
+    return CDI_OK;
+}
+
+int cdi_grid_info(const cdi_grid *g, int *nx, int *ny, int *nz, double *dx, int *dtype)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (nx) *nx = g->nx;
+    if (ny) *ny = g->ny;
+    if (nz) *nz = g->nz;
+    if (dx) *dx = g->dx;
+    if (dtype) *dtype = g->dtype;
+    return CDI_OK;
+}
+
+int cdi_set_velocity(cdi_grid *g, const void *u, const void *v, const void *w, double umax,
+                     void *stream)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (!u) return fail(CDI_ERR_ARG, "u is NULL");
+    if (!v && !(g->ny == 1 && g->nz == 1)) return fail(CDI_ERR_ARG, "v may be NULL only when ny == nz == 1");
+    if (!w && g->nz != 1) return fail(CDI_ERR_ARG, "w may be NULL only when nz == 1");
+    if (!aligned16(u) || (v && !aligned16(v)) || (w && !aligned16(w)))
+        return fail(CDI_ERR_ARG, "velocity arrays must be 16-byte aligned");
+    if (!isfinite(umax) && umax > 0) return fail(CDI_ERR_ARG, "umax must be finite");
+    g->u = u;
+    g->v = v;
+    g->w = w;
+    g->vel_set = 1;
+    if (umax >= 0.0) {
+        g->U = umax;
+        return CDI_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int nb = kStatsBlocks;
+    RedScratch r = scratch(g, g->rec2, 0);
+    cudaError_t e = g->dtype == CDI_F64
+        ? cdi::launch_absmax<double>((const double *)u, (const double *)v, (const double *)w, g->n, r, nb, s)
+        : cdi::launch_absmax<float>((const float *)u, (const float *)v, (const float *)w, g->n, r, nb, s);
+    if (e != cudaSuccess) return cuda_fail(e, "absmax launch");
+    StatsRec h;
+    if ((e = cudaMemcpyAsync(&h, g->rec2, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "absmax readback");
+    if (!isfinite(h.mx)) return fail(CDI_ERR_NAN, "velocity contains non-finite values");
+    g->U = h.mx;
+    return CDI_OK;
+}
+
+int cdi_get_umax(const cdi_grid *g, double *U)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (!U) return fail(CDI_ERR_ARG, "U is NULL");
+    if (!g->vel_set) return fail(CDI_ERR_STATE, "no velocity set");
+    *U = g->U;
+    return CDI_OK;
+}
+
+int cdi_check_condition(double eps_over_dx, double gamma_over_U, double A, int Df)
+{
+    if (!(eps_over_dx > 0) || !(gamma_over_U > 0) || !(A >= 0) || Df < 0 || Df > 3)
+        return fail(CDI_ERR_ARG, "bad condition arguments");
+    // Eq. 17 / 24: eps/dx >= (g + 1) / (2 g), g = gamma / U; g -> inf gives 1/2.
+    const double rhs = isinf(gamma_over_U) ? 0.5 : (gamma_over_U + 1.0) / (2.0 * gamma_over_U);
+    const double rel = 1e-12;  // configurations placed exactly on the line
+    const bool line_ok = eps_over_dx >= rhs * (1.0 - rel);
+    // Eq. 25: A = dt gamma eps / dx^2 <= 1 / (2 D_f).
+    const int d = Df > 0 ? Df : 1;
+    const bool a_ok = A <= (1.0 / (2.0 * d)) * (1.0 + rel);
+    return (line_ok && a_ok) ? 1 : 0;
+}
+
+int cdi_max_dt(double dx, double eps, double gamma, int Df, int scheme, double *dt)
+{
+    if (!dt) return fail(CDI_ERR_ARG, "dt is NULL");
+    if (!(dx > 0) || !(eps > 0) || !(gamma > 0) || Df < 1 || Df > 3)
+        return fail(CDI_ERR_ARG, "bad arguments to cdi_max_dt");
+    const double base = dx * dx / (gamma * eps * Df);
+    switch (scheme) {
+    case CDI_EULER:
+    case CDI_RK2: *dt = base / 2.0; break;          // Eq. 25, 26
+    case CDI_RK3: *dt = 2.51 * base / 4.0; break;   // Eq. 27
+    case CDI_RK4: *dt = 2.79 * base / 4.0; break;   // Eq. 28
+    default: return fail(CDI_ERR_ARG, "unknown scheme %d", scheme);
+    }
+    return CDI_OK;
+}
+
+static int check_step_args(const cdi_grid *g, const void *a, void *b, double dt, double eps,
+                           double gamma, double vel_scale)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (!g->vel_set) return fail(CDI_ERR_STATE, "cdi_set_velocity has not been called");
+    if (!a || !b) return fail(CDI_ERR_ARG, "phi pointer is NULL");
+    if (!aligned16(a) || !aligned16(b)) return fail(CDI_ERR_ARG, "phi arrays must be 16-byte aligned");
+    const size_t bytes = (size_t)g->n * esize(g);
+    const char *pa = (const char *)a, *pb = (const char *)b;
+    if (pa < pb + bytes && pb < pa + bytes) return fail(CDI_ERR_ARG, "phi_in and phi_out overlap");
+    if (!(dt >= 0) || !isfinite(dt)) return fail(CDI_ERR_ARG, "dt must be finite and >= 0");
+    if (!(eps > 0) || !isfinite(eps)) return fail(CDI_ERR_ARG, "eps must be finite and > 0");
+    if (!(gamma >= 0) || !isfinite(gamma)) return fail(CDI_ERR_ARG, "gamma must be finite and >= 0");
+    if (!isfinite(vel_scale)) return fail(CDI_ERR_ARG, "vel_scale must be finite");
+    return CDI_OK;
+}
+
+static int check_condition_flag(const cdi_grid *g, double dt, double eps, double gamma,
+                                double vel_scale)
+{
+    const double Ueff = fabs(vel_scale) * g->U;
+    const double gU = Ueff > 0 ? gamma / Ueff : INFINITY;
+    const double A = dt * gamma * eps / (g->dx * g->dx);
+    if (!(gamma > 0)) return fail(CDI_ERR_CONDITION, "gamma must be > 0 for the boundedness condition");
+    int ok = cdi_check_condition(eps / g->dx, gU, A, g->Df);
+    if (ok < 0) return ok;
+    if (!ok)
+        return fail(CDI_ERR_CONDITION,
+                    "boundedness condition fails: eps/dx=%.6g gamma/U=%.6g A=%.6g Df=%d "
+                    "(need eps/dx >= (g+1)/(2g) and A <= 1/(2 Df))",
+                    eps / g->dx, gU, A, g->Df);
+    return CDI_OK;
+}
+
+template <typename T>
+static cdi::StepCoef<T> coefs(const cdi_grid *g, double dt, double eps, double gamma, double vs)
+{
+    cdi::StepCoef<T> c;
+    c.c_adv = (T)(0.5 * vs);
+    c.c_dif = (T)(gamma * eps / g->dx);
+    c.c_shp = (T)(0.5 * gamma);
+    c.c_upd = (T)(dt / g->dx);
+    c.tol = sizeof(T) == 8 ? (T)DBL_EPSILON : (T)FLT_EPSILON;
+    return c;
+}
+
+template <typename T>
+static int step_t(cdi_grid *g, const void *in, void *out, double dt, double eps, double gamma,
+                  double vs, cudaStream_t s)
+{
+    cdi::FwdArgs<T> a;
+    a.phi = (const T *)in;
+    a.out = (T *)out;
+    a.u = (const T *)g->u;
+    a.v = (const T *)(g->v ? g->v : g->u);  // ny == nz == 1: v is inert
+    a.w = (const T *)(g->w ? g->w : g->u);  // nz == 1: w is inert
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
+    a.zchunk = g->fwd.zchunk;
+    a.c = coefs<T>(g, dt, eps, gamma, vs);
+    a.red = scratch(g, g->rec, 1);
+    if (cdi::fwd_blocks(g->fwd.tile, a.zchunk, g->nx, g->ny, g->nz) > g->capacity)
+        return fail(CDI_ERR_STATE, "launch configuration exceeds the reduction scratch");
+    cudaError_t e = cdi::launch_fwd<T>(a, g->fwd.tile, s);
+    if (e != cudaSuccess) return cuda_fail(e, "forward step launch");
+    return CDI_OK;
+}
+
+int cdi_step(cdi_grid *g, const void *phi_in, void *phi_out, double dt, double eps, double gamma,
+             double vel_scale, int flags, void *stream)
+{
+    if (int rc = check_step_args(g, phi_in, phi_out, dt, eps, gamma, vel_scale)) return rc;
+    if (flags & CDI_CHECK_CONDITION)
+        if (int rc = check_condition_flag(g, dt, eps, gamma, vel_scale)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    return g->dtype == CDI_F64 ? step_t<double>(g, phi_in, phi_out, dt, eps, gamma, vel_scale, s)
+                               : step_t<float>(g, phi_in, phi_out, dt, eps, gamma, vel_scale, s);
+}
+
+int cdi_run(cdi_grid *g, void *buf_a, void *buf_b, int nsteps, double t0, double dt, double eps,
+            double gamma, double period, int flags, int *final_in_b, void *stream)
+{
+    if (nsteps < 0) return fail(CDI_ERR_ARG, "nsteps must be >= 0");
+    if (int rc = check_step_args(g, buf_a, buf_b, dt, eps, gamma, 1.0)) return rc;
+    if (flags & CDI_CHECK_CONDITION)
+        if (int rc = check_condition_flag(g, dt, eps, gamma, 1.0)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    void *src = buf_a, *dst = buf_b;
+    for (int i = 0; i < nsteps; ++i) {
+        const double t = t0 + i * dt;
+        const double vs = period > 0 ? cos(M_PI * t / period) : 1.0;
+        int rc = g->dtype == CDI_F64 ? step_t<double>(g, src, dst, dt, eps, gamma, vs, s)
+                                     : step_t<float>(g, src, dst, dt, eps, gamma, vs, s);
+        if (rc) return rc;
+        void *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    if (final_in_b) *final_in_b = (src == buf_b);
+    return CDI_OK;
+}
+
+static int read_rec(const StatsRec *dev, cdi_stats *out, cudaStream_t s)
+{
+    StatsRec h;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&h, dev, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "statistics readback");
+    static_assert(sizeof(StatsRec) == sizeof(cdi_stats), "record layout");
+    memcpy(out, &h, sizeof(h));
+    if (!isfinite(h.sum)) return fail(CDI_ERR_NAN, "non-finite phi (sum = %g)", h.sum);
+    return CDI_OK;
+}
+
+int cdi_step_stats(cdi_grid *g, cdi_stats *out, void *stream)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (!out) return fail(CDI_ERR_ARG, "out is NULL");
+    return read_rec(g->rec, out, (cudaStream_t)stream);
+}
+
+int cdi_reset_run_stats(cdi_grid *g, void *stream)
+{
+    if (int rc = check_grid(g)) return rc;
+    StatsRec h;
+    reset_run_host(&h);
+    cudaStream_t s = (cudaStream_t)stream;
+    // The host record must outlive the async copy: synchronise before returning.
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(g->rec, &h, sizeof(h), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "reset run statistics");
+    return CDI_OK;
+}
+
+int cdi_mass_and_bounds(cdi_grid *g, const void *phi, cdi_stats *out, void *stream)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (!phi || !out) return fail(CDI_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    RedScratch r = scratch(g, g->rec2, 0);
+    int nb = kStatsBlocks;
+    if ((long long)nb * 256 > g->n) nb = (int)((g->n + 255) / 256);
+    cudaError_t e = g->dtype == CDI_F64
+        ? cdi::launch_stats<double>((const double *)phi, g->n, DBL_EPSILON, r, nb, s)
+        : cdi::launch_stats<float>((const float *)phi, g->n, FLT_EPSILON, r, nb, s);
+    if (e != cudaSuccess) return cuda_fail(e, "stats launch");
+    return read_rec(g->rec2, out, s);
+}
+
+int cdi_step_host(cdi_grid *g, const void *phi_in_host, void *phi_out_host, double dt, double eps,
+                  double gamma, double vel_scale, int flags, cdi_stats *stats_out, void *stream)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (!phi_in_host || !phi_out_host) return fail(CDI_ERR_ARG, "host pointer is NULL");
+    const size_t bytes = (size_t)g->n * esize(g);
+    cudaError_t e;
+    if (!g->stage_in) {
+        if ((e = cudaMalloc(&g->stage_in, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(stage)");
+        if ((e = cudaMalloc(&g->stage_out, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(stage)");
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((e = cudaMemcpyAsync(g->stage_in, phi_in_host, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "host-to-device copy");
+    if (int rc = cdi_step(g, g->stage_in, g->stage_out, dt, eps, gamma, vel_scale, flags, stream)) return rc;
+    if ((e = cudaMemcpyAsync(phi_out_host, g->stage_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+        return cuda_fail(e, "device-to-host copy");
+    if (stats_out) return read_rec(g->rec, stats_out, s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "synchronise");
+    return CDI_OK;
+}
+
+template <typename T>
+static int adjoint_t(cdi_grid *g, const void *phi, const void *lam, void *out, void *gu, void *gv,
+                     void *gw, double dt, double eps, double gamma, double vs, cudaStream_t s)
+{
+    cdi::AdjArgs<T> a;
+    a.phi = (const T *)phi;
+    a.lam = (const T *)lam;
+    a.out = (T *)out;
+    a.u = (const T *)g->u;
+    a.v = (const T *)(g->v ? g->v : g->u);
+    a.w = (const T *)(g->w ? g->w : g->u);
+    a.gu = (T *)gu;
+    a.gv = (T *)gv;
+    a.gw = (T *)gw;
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
+    a.zchunk = g->adj.zchunk;
+    a.c = coefs<T>(g, dt, eps, gamma, vs);
+    a.c_shp_adj = (T)(gamma * dt / (2.0 * g->dx));
+    a.c_vel = (T)(0.5 * vs);
+    if (cdi::adj_blocks(g->adj.tile, a.zchunk, g->nx, g->ny, g->nz) > g->capacity)
+        return fail(CDI_ERR_STATE, "adjoint launch configuration out of range");
+    cudaError_t e = cdi::launch_adj<T>(a, g->adj.tile, s);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint step launch");
+    return CDI_OK;
+}
+
+int cdi_step_adjoint(cdi_grid *g, const void *phi_k, const void *lam_next, void *lam_k, void *gu,
+                     void *gv, void *gw, double dt, double eps, double gamma, double vel_scale,
+                     void *stream)
+{
+    if (int rc = check_step_args(g, phi_k, lam_k, dt, eps, gamma, vel_scale)) return rc;
+    if (!lam_next || !aligned16(lam_next)) return fail(CDI_ERR_ARG, "lam_next NULL or misaligned");
+    const size_t bytes = (size_t)g->n * esize(g);
+    const char *pa = (const char *)lam_next, *pb = (const char *)lam_k;
+    if (pa < pb + bytes && pb < pa + bytes) return fail(CDI_ERR_ARG, "lam_k overlaps lam_next");
+    const int ng = (gu != nullptr) + (gv != nullptr) + (gw != nullptr);
+    if (ng != 0 && ng != 3) return fail(CDI_ERR_ARG, "gu, gv, gw must be all NULL or all set");
+    if (ng == 3 && (!aligned16(gu) || !aligned16(gv) || !aligned16(gw)))
+        return fail(CDI_ERR_ARG, "velocity gradients must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    return g->dtype == CDI_F64
+        ? adjoint_t<double>(g, phi_k, lam_next, lam_k, gu, gv, gw, dt, eps, gamma, vel_scale, s)
+        : adjoint_t<float>(g, phi_k, lam_next, lam_k, gu, gv, gw, dt, eps, gamma, vel_scale, s);
+}
+

@@ -1,0 +1,109 @@
+// Internal declarations shared by the CDI CUDA translation units.
+// Not part of the public ABI (include/cdi.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cdi {
+
+// Per-block partial of the fused reductions (mass, min, max, violation counts).
+struct Partial {
+    double sum;
+    double mn;
+    double mx;
+    long long ns;  // #(phi < 0 or phi > 1)
+    long long nt;  // #(phi < -tol or phi > 1 + tol)
+};
+
+// Device-side statistics record; same layout as the public cdi_stats.
+struct StatsRec {
+    double mass, sum, mn, mx;
+    long long ns, nt;
+    double mn_run, mx_run;
+    long long ns_run, nt_run, steps_run;
+};
+
+// Library-owned reduction scratch of one grid.
+struct RedScratch {
+    Partial *partials;      // one slot per block of the largest launch
+    unsigned int *counter;  // blocks finished in the current launch (self-resetting)
+    StatsRec *rec;          // result record
+    int capacity;           // number of partial slots
+    double dV;              // cell measure dx^D_f
+    int update_run;         // 1: fold this result into the *_run accumulators
+};
+
+// Coefficients of one step, precomputed on the host in double and cast.
+template <typename T>
+struct StepCoef {
+    T c_adv;  // vel_scale / 2      (advective flux u_f (phi_L + phi_R)/2)
+    T c_dif;  // gamma * eps / dx   (diffusive flux)
+    T c_shp;  // gamma / 2          (sharpening flux, face average of s)
+    T c_upd;  // dt / dx            (flux divergence)
+    T tol;    // machine epsilon of T (tolerant bound count)
+};
+
+template <typename T>
+struct FwdArgs {
+    const T *__restrict__ phi;
+    T *__restrict__ out;
+    const T *__restrict__ u;
+    const T *__restrict__ v;
+    const T *__restrict__ w;
+    int nx, ny, nz;
+    int zchunk;
+    StepCoef<T> c;
+    RedScratch red;
+};
+
+template <typename T>
+struct AdjArgs {
+    const T *__restrict__ phi;
+    const T *__restrict__ lam;   // lambda^{k+1}
+    T *__restrict__ out;         // lambda^k
+    const T *__restrict__ u;
+    const T *__restrict__ v;
+    const T *__restrict__ w;
+    T *gu, *gv, *gw;             // nullable, accumulated
+    int nx, ny, nz;
+    int zchunk;
+    StepCoef<T> c;
+    T c_shp_adj;                 // gamma dt / (2 dx)
+    T c_vel;                     // vel_scale / 2 (velocity gradient factor)
+};
+
+// Launch configurations of the fused forward step (tile BX x BY, z chunk).
+struct LaunchCfg {
+    int tile;    // index into the tile table (see cdi_fwd.cu)
+    int zchunk;  // planes per block along z
+};
+
+int fwd_num_tiles();
+void fwd_tile_dims(int tile, int *bx, int *by);
+int fwd_blocks(int tile, int zchunk, int nx, int ny, int nz);
+
+template <typename T>
+cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_stats(const T *phi, long long n, T tol, RedScratch red, int nblocks,
+                         cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_absmax(const T *u, const T *v, const T *w, long long n, RedScratch red,
+                          int nblocks, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_adj(const AdjArgs<T> &a, int tile, cudaStream_t s);
+
+int adj_num_tiles();
+int adj_blocks(int tile, int zchunk, int nx, int ny, int nz);
+
+__host__ __device__ inline int wrapi(int a, int n)
+{
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+}  // namespace cdi

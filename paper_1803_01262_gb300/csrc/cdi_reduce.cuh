@@ -1,0 +1,182 @@
+// Fused reductions of the CDI step: discrete mass (double sum), min, max and
+// two violation counts, reduced per block and finished by the last block to
+// arrive (fixed combination order, so results are reproducible run to run).
+#pragma once
+
+#include <math.h>
+#include "cdi_internal.cuh"
+
+namespace cdi {
+
+__device__ __forceinline__ Partial pidentity()
+{
+    Partial p;
+    p.sum = 0.0;
+    p.mn = INFINITY;
+    p.mx = -INFINITY;
+    p.ns = 0;
+    p.nt = 0;
+    return p;
+}
+
+__device__ __forceinline__ Partial pcombine(Partial a, const Partial &b)
+{
+    a.sum += b.sum;
+    a.mn = fmin(a.mn, b.mn);
+    a.mx = fmax(a.mx, b.mx);
+    a.ns += b.ns;
+    a.nt += b.nt;
+    return a;
+}
+
+__device__ __forceinline__ Partial warp_reduce(Partial p)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Partial q;
+        q.sum = __shfl_down_sync(0xffffffffu, p.sum, o);
+        q.mn = __shfl_down_sync(0xffffffffu, p.mn, o);
+        q.mx = __shfl_down_sync(0xffffffffu, p.mx, o);
+        q.ns = __shfl_down_sync(0xffffffffu, p.ns, o);
+        q.nt = __shfl_down_sync(0xffffffffu, p.nt, o);
+        p = pcombine(p, q);
+    }
+    return p;
+}
+
+// Per-thread accumulator.  FP32 keeps a compensated (Kahan) float sum so the
+// per-thread partial is accurate before it is promoted to double; FP64 sums
+// directly.  min/max are exact; NaN is ignored by min/max and not counted.
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<float> {
+    float s, c, mn, mx;
+    int ns, nt;
+    __device__ __forceinline__ void init()
+    {
+        s = 0.f; c = 0.f; mn = INFINITY; mx = -INFINITY; ns = 0; nt = 0;
+    }
+    __device__ __forceinline__ void add(float p, float tol)
+    {
+        float y = p - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+        mn = fminf(mn, p);
+        mx = fmaxf(mx, p);
+        ns += (p < 0.f) | (p > 1.f);
+        nt += (p < -tol) | (p > 1.f + tol);
+    }
+    __device__ __forceinline__ Partial partial() const
+    {
+        Partial r;
+        r.sum = (double)s - (double)c;
+        r.mn = (double)mn;
+        r.mx = (double)mx;
+        r.ns = ns;
+        r.nt = nt;
+        return r;
+    }
+};
+
+template <>
+struct Acc<double> {
+    double s, mn, mx;
+    int ns, nt;
+    __device__ __forceinline__ void init()
+    {
+        s = 0.0; mn = INFINITY; mx = -INFINITY; ns = 0; nt = 0;
+    }
+    __device__ __forceinline__ void add(double p, double tol)
+    {
+        s += p;
+        mn = fmin(mn, p);
+        mx = fmax(mx, p);
+        ns += (p < 0.0) | (p > 1.0);
+        nt += (p < -tol) | (p > 1.0 + tol);
+    }
+    __device__ __forceinline__ Partial partial() const
+    {
+        Partial r;
+        r.sum = s;
+        r.mn = mn;
+        r.mx = mx;
+        r.ns = ns;
+        r.nt = nt;
+        return r;
+    }
+};
+
+__device__ __forceinline__ Partial load_partial_cg(const Partial *p)
+{
+    Partial r;
+    r.sum = __ldcg(&p->sum);
+    r.mn = __ldcg(&p->mn);
+    r.mx = __ldcg(&p->mx);
+    r.ns = __ldcg(&p->ns);
+    r.nt = __ldcg(&p->nt);
+    return r;
+}
+
+// Block-reduce p (every thread of the block must call this), store the block
+// partial, and let the last block to finish combine all partials in index
+// order into red.rec.  The block size must be a multiple of 32.
+__device__ __forceinline__ void reduce_and_finish(Partial p, const RedScratch &red)
+{
+    __shared__ Partial wsum[32];
+    __shared__ int is_last;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+
+    p = warp_reduce(p);
+    if (lane == 0) wsum[wid] = p;
+    __syncthreads();
+    if (wid == 0) {
+        Partial q = lane < nw ? wsum[lane] : pidentity();
+        q = warp_reduce(q);
+        if (lane == 0) {
+            red.partials[bid] = q;
+            __threadfence();
+            unsigned prev = atomicAdd(red.counter, 1u);
+            is_last = (prev == (unsigned)(nb - 1));
+        }
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    Partial acc = pidentity();
+    for (int i = tid; i < nb; i += nthr) acc = pcombine(acc, load_partial_cg(red.partials + i));
+    acc = warp_reduce(acc);
+    __syncthreads();
+    if (lane == 0) wsum[wid] = acc;
+    __syncthreads();
+    if (wid == 0) {
+        Partial q = lane < nw ? wsum[lane] : pidentity();
+        q = warp_reduce(q);
+        if (lane == 0) {
+            StatsRec *r = red.rec;
+            r->mass = red.dV * q.sum;
+            r->sum = q.sum;
+            r->mn = q.mn;
+            r->mx = q.mx;
+            r->ns = q.ns;
+            r->nt = q.nt;
+            if (red.update_run) {
+                r->mn_run = fmin(r->mn_run, q.mn);
+                r->mx_run = fmax(r->mx_run, q.mx);
+                r->ns_run += q.ns;
+                r->nt_run += q.nt;
+                r->steps_run += 1;
+            }
+            __threadfence();
+            *red.counter = 0u;
+        }
+    }
+}
+
+}  // namespace cdi

@@ -1,0 +1,88 @@
+"""GPU parity of the discrete-adjoint step against the FP64 oracle adjoint."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1803_01262_gb300 import cdi
+from paper_1803_01262_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a, dtype):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def case(shape, seed, smooth):
+    h = 1.0 / max(shape)
+    phi = 0.02 + 0.96 * I.random_phi(shape, seed, smooth=smooth)
+    u, v, w = I.random_velocity(shape, h, 8, 3, seed + 1)
+    lam = np.random.default_rng(seed + 2).standard_normal(shape)
+    return phi, u, v, w, lam, h
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape", [(1, 1, 29), (1, 23, 17), (5, 6, 7), (17, 21, 66), (2, 3, 40)])
+@pytest.mark.parametrize("with_vel", [False, True])
+def test_adjoint_parity(dtype, shape, with_vel):
+    smooth = dtype == torch.float32
+    phi, u, v, w, lam, h = case(shape, 7 + sum(shape), smooth)
+    t = np.float64 if dtype == torch.float64 else np.float32
+    phi, u, v, w, lam = (np.asarray(x, t).astype(np.float64) for x in (phi, u, v, w, lam))
+    dt, eps, gamma, vs = 0.15 * h * h / (1.3 * 1.1 * h), 1.1 * h, 1.3, 0.7
+    nz, ny, nx = shape
+    g = cdi.Grid(nx, ny, nz, h, dtype)
+    vel = [dev(x, dtype) for x in (u, v, w)]
+    g.set_velocity(*vel)
+    out = torch.empty(shape, dtype=dtype, device="cuda")
+    grads = None
+    if with_vel:
+        g0 = np.random.default_rng(1).standard_normal((3,) + shape)
+        grads = [dev(x, dtype) for x in g0]
+    g.step_adjoint(dev(phi, dtype), dev(lam, dtype), out, dt, eps, gamma, vs, grads=grads)
+    ref = oracle.adjoint(phi, u, v, w, lam, h, dt, eps, gamma, vs, want_vel=with_vel)
+    if with_vel:
+        ref, rgu, rgv, rgw = ref
+    scale = max(1.0, np.abs(ref).max())
+    tol = 1e-12 if dtype == torch.float64 else 2e-6
+    assert np.abs(out.double().cpu().numpy() - ref).max() <= tol * scale
+    if with_vel:
+        for gd, rg, base in zip(grads, (rgu, rgv, rgw), g0):
+            base = np.asarray(base, t).astype(np.float64)
+            s2 = max(1.0, np.abs(rg).max())
+            assert np.abs(gd.double().cpu().numpy() - (base + rg)).max() <= tol * s2 * 4
+
+
+def test_adjoint_constant_lambda_gpu():
+    """lam' = const gives lam = lam' exactly (J^T 1 = 1 from conservation)."""
+    shape = (6, 10, 40)
+    phi, u, v, w, lam, h = case(shape, 3, False)
+    g = cdi.Grid(40, 10, 6, h, torch.float64)
+    vel = [dev(x, torch.float64) for x in (u, v, w)]
+    g.set_velocity(*vel)
+    out = torch.empty(shape, dtype=torch.float64, device="cuda")
+    l1 = torch.full(shape, 2.5, dtype=torch.float64, device="cuda")
+    g.step_adjoint(dev(phi, torch.float64), l1, out, 0.1 * h * h, h, 1.0, 1.0)
+    assert torch.all(out == 2.5)
+
+
+def test_adjoint_dot_product_gpu():
+    """<J dphi, lam> with J dphi from GPU forward FD == <dphi, J^T lam> from the GPU adjoint."""
+    shape = (12, 16, 40)
+    phi, u, v, w, lam, h = case(shape, 11, True)
+    dt, eps, gamma = 0.1 * h * h / (1.2 * h), 1.2 * h, 1.0
+    g = cdi.Grid(40, 16, 12, h, torch.float64)
+    vel = [dev(x, torch.float64) for x in (u, v, w)]
+    g.set_velocity(*vel)
+    dphi = np.random.default_rng(5).standard_normal(shape)
+    hh = 1e-6
+    a = torch.empty(shape, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    g.step(dev(phi + hh * dphi, torch.float64), a, dt, eps, gamma)
+    g.step(dev(phi - hh * dphi, torch.float64), b, dt, eps, gamma)
+    jv = ((a - b) / (2 * hh)).cpu().numpy()
+    out = torch.empty_like(a)
+    g.step_adjoint(dev(phi, torch.float64), dev(lam, torch.float64), out, dt, eps, gamma)
+    lhs, rhs = (jv * lam).sum(), (dphi * out.cpu().numpy()).sum()
+    assert abs(lhs - rhs) <= 1e-7 * (abs(lhs) + abs(rhs))
