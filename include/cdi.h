@@ -130,7 +130,10 @@ CDI_API int cdi_get_umax(const cdi_grid *g, double *U);
  * with cdi_step_stats.  With CDI_CHECK_CONDITION the call first checks
  * eps/dx >= (g + 1)/(2 g), g = gamma/(|vel_scale| U) (Eq. 24), and
  * A = dt gamma eps/dx^2 <= 1/(2 D_f) (Eq. 25) and returns
- * CDI_ERR_CONDITION without launching if either fails. */
+ * CDI_ERR_CONDITION without launching if either fails.  The check allows a
+ * relative slack of 1e-12 (CDI_F64) or 4 FLT_EPSILON (CDI_F32, where U is
+ * measured on the float-rounded velocity) so that configurations placed
+ * exactly on the crossover line pass. */
 CDI_API int cdi_step(cdi_grid *g, const void *phi_in, void *phi_out, double dt, double eps,
              double gamma, double vel_scale, int flags, void *stream);
 
@@ -176,7 +179,8 @@ CDI_API int cdi_step_adjoint(cdi_grid *g, const void *phi_k, const void *lam_nex
 
 /* Boundedness condition (Eq. 17/24 with U the face maximum) and the Euler
  * diffusive limit A <= 1/(2 D_f) (Eq. 25).  Returns 1 if both hold, 0 if
- * not, CDI_ERR_ARG on bad input.  gamma_over_U = +inf is allowed. */
+ * not, CDI_ERR_ARG on bad input.  gamma_over_U = +inf is allowed.  A
+ * relative slack of 1e-12 admits values placed exactly on the line. */
 CDI_API int cdi_check_condition(double eps_over_dx, double gamma_over_U, double A, int Df);
 
 /* Largest stable, bounded time step for a scheme above the crossover line:

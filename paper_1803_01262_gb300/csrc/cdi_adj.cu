@@ -92,6 +92,9 @@ adj_kernel(const AdjArgs<T> a)
         }
     };
     // gbar (3-vector) and the local term (1 - 2 phi)(sbar . n) at cell (lx, ly) of plane z.
+    // The projection (I - n n^T) sbar is formed as n x (sbar x n), which is
+    // exactly zero when sbar and n lie along one axis (the 1D case) and avoids
+    // the cancellation of sbar - n (n . sbar) when |n| is off 1 by rounding.
     auto gbar = [&](int z, int lx, int ly, T &b0, T &b1, T &b2, T &tloc) {
         const int X = lx + 2, Y = ly + 2;
         const int m = z & 3, mm = (z - 1) & 3, mp = (z + 1) & 3;
@@ -101,17 +104,23 @@ adj_kernel(const AdjArgs<T> a)
         const T g2 = sp[mp][Y][X] - sp[mm][Y][X];
         const T q = g0 * g0 + g1 * g1 + g2 * g2;
         const T inv = q > T(0) ? rsqrt_a(q) : T(0);
-        const T n0 = g0 * inv, n1 = g1 * inv, n2 = g2 * inv;
         const T sb0 = c_sb * (sl[m][Y][X + 1] - sl[m][Y][X - 1]);
         const T sb1 = c_sb * (sl[m][Y + 1][X] - sl[m][Y - 1][X]);
         const T sb2 = c_sb * (sl[mp][Y][X] - sl[mm][Y][X]);
-        const T sdn = sb0 * n0 + sb1 * n1 + sb2 * n2;
-        tloc = (T(1) - T(2) * p) * sdn;
-        // nbar = sbar p (1 - p);  gbar = (nbar - n (n . nbar)) / |g|
-        const T w = p * (T(1) - p) * inv;
-        b0 = w * (sb0 - n0 * sdn);
-        b1 = w * (sb1 - n1 * sdn);
-        b2 = w * (sb2 - n2 * sdn);
+        const T n0 = g0 * inv, n1 = g1 * inv, n2 = g2 * inv;
+        tloc = (T(1) - T(2) * p) * (sb0 * n0 + sb1 * n1 + sb2 * n2);
+        // c = sbar x n ; d = n x c = sbar - n (n . sbar) for a unit n
+        const T c0 = sb1 * n2 - sb2 * n1;
+        const T c1 = sb2 * n0 - sb0 * n2;
+        const T c2 = sb0 * n1 - sb1 * n0;
+        const T d0 = n1 * c2 - n2 * c1;
+        const T d1 = n2 * c0 - n0 * c2;
+        const T d2 = n0 * c1 - n1 * c0;
+        // nbar = sbar p (1 - p);  gbar = (nbar - n (n . nbar)) / |g| = p (1 - p) d / |g|
+        const T wgt = p * (T(1) - p) * inv;
+        b0 = wgt * d0;
+        b1 = wgt * d1;
+        b2 = wgt * d2;
     };
     auto gbar_plane = [&](int z, T &gzc, T &tc) {
         T b0, b1;

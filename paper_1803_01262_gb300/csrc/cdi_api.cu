@@ -32,8 +32,9 @@ int cuda_fail(cudaError_t e, const char *what)
     return fail(CDI_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-constexpr int kZMin = 8;          // smallest z chunk any launch uses
+constexpr int kZMin = 8;          // smallest z chunk any adjoint launch uses
 constexpr int kStatsBlocks = 1216; // 8 blocks of 256 threads per SM on 152 SMs
+constexpr int kMaxBlocksPerSM = 32;
 
 }  // namespace
 
@@ -90,20 +91,38 @@ static void reset_run_host(StatsRec *r)
     r->mx_run = -INFINITY;
 }
 
-// Default launch configuration: 32 x 16 tiles (32 x 4 for narrow grids) and a
-// z chunk giving about eight resident blocks per SM.
-static LaunchCfg default_cfg(const cdi_grid *g)
+// Forward launch: tile shape and one balanced wave of resident blocks
+// (never more blocks than tile-planes).
+static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, LaunchCfg *c)
+{
+    int resident = 0;
+    cudaError_t e = g->dtype == CDI_F64 ? cdi::fwd_occupancy<double>(tile, &resident)
+                                        : cdi::fwd_occupancy<float>(tile, &resident);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+    if (resident < 1) return fail(CDI_ERR_CUDA, "forward kernel does not fit on an SM");
+    if (blocks_per_sm > 0 && blocks_per_sm < resident) resident = blocks_per_sm;
+    long long nb = (long long)resident * g->sm_count;
+    const long long units = cdi::fwd_units(tile, g->nx, g->ny, g->nz);
+    if (nb > units) nb = units;
+    c->tile = tile;
+    c->zchunk = 0;
+    c->nblocks = (int)nb;
+    return CDI_OK;
+}
+
+// Adjoint launch: z chunk giving about eight blocks per SM.
+static LaunchCfg adj_default(const cdi_grid *g)
 {
     LaunchCfg c;
-    c.tile = (g->nx >= 32 && g->ny >= 16) ? 1 : 3;
-    int bx, by;
-    cdi::fwd_tile_dims(c.tile, &bx, &by);
+    c.tile = (g->nx >= 32 && g->ny >= 16) ? 1 : 2;
+    const int bx = 32, by = c.tile == 1 ? 16 : 4;
     long long tiles = (long long)((g->nx + bx - 1) / bx) * ((g->ny + by - 1) / by);
     long long want = (long long)g->sm_count * 8;
     long long zc = (g->nz * tiles + want - 1) / want;
     if (zc < kZMin) zc = kZMin;
     if (zc > g->nz) zc = g->nz;
     c.zchunk = (int)zc;
+    c.nblocks = 0;
     return c;
 }
 
@@ -133,10 +152,7 @@ int cdi_create_grid(cdi_grid **out, int nx, int ny, int nz, double dx, int dtype
     e = cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaDeviceGetAttribute"); }
     int cap = kStatsBlocks;
-    for (int t = 0; t < cdi::fwd_num_tiles(); ++t) {
-        int b = cdi::fwd_blocks(t, kZMin, nx, ny, nz);
-        if (b > cap) cap = b;
-    }
+    if (g->sm_count * kMaxBlocksPerSM > cap) cap = g->sm_count * kMaxBlocksPerSM;
     for (int t = 0; t < cdi::adj_num_tiles(); ++t) {
         int b = cdi::adj_blocks(t, kZMin, nx, ny, nz);
         if (b > cap) cap = b;
@@ -157,9 +173,11 @@ int cdi_create_grid(cdi_grid **out, int nx, int ny, int nz, double dx, int dtype
         cdi_destroy_grid(g);
         return cuda_fail(e, "scratch init");
     }
-    g->fwd = default_cfg(g);
-    g->adj.tile = (nx >= 32 && ny >= 16) ? 1 : 2;
-    g->adj.zchunk = g->fwd.zchunk;
+    if (int rc = fwd_cfg(g, (nx >= 32 && ny >= 16) ? 1 : 3, 0, &g->fwd)) {
+        cdi_destroy_grid(g);
+        return rc;
+    }
+    g->adj = adj_default(g);
     *out = g;
     return CDI_OK;
 }
@@ -231,18 +249,22 @@ int cdi_get_umax(const cdi_grid *g, double *U)
     return CDI_OK;
 }
 
-int cdi_check_condition(double eps_over_dx, double gamma_over_U, double A, int Df)
+// Eq. 17 / 24: eps/dx >= (g + 1) / (2 g), g = gamma / U (g -> inf gives 1/2), and
+// Eq. 25: A = dt gamma eps / dx^2 <= 1 / (2 D_f); both with relative slack rel.
+static int condition_holds(double eps_over_dx, double gamma_over_U, double A, int Df, double rel)
 {
     if (!(eps_over_dx > 0) || !(gamma_over_U > 0) || !(A >= 0) || Df < 0 || Df > 3)
         return fail(CDI_ERR_ARG, "bad condition arguments");
-    // Eq. 17 / 24: eps/dx >= (g + 1) / (2 g), g = gamma / U; g -> inf gives 1/2.
     const double rhs = isinf(gamma_over_U) ? 0.5 : (gamma_over_U + 1.0) / (2.0 * gamma_over_U);
-    const double rel = 1e-12;  // configurations placed exactly on the line
     const bool line_ok = eps_over_dx >= rhs * (1.0 - rel);
-    // Eq. 25: A = dt gamma eps / dx^2 <= 1 / (2 D_f).
     const int d = Df > 0 ? Df : 1;
     const bool a_ok = A <= (1.0 / (2.0 * d)) * (1.0 + rel);
     return (line_ok && a_ok) ? 1 : 0;
+}
+
+int cdi_check_condition(double eps_over_dx, double gamma_over_U, double A, int Df)
+{
+    return condition_holds(eps_over_dx, gamma_over_U, A, Df, 1e-12);
 }
 
 int cdi_max_dt(double dx, double eps, double gamma, int Df, int scheme, double *dt)
@@ -285,7 +307,11 @@ static int check_condition_flag(const cdi_grid *g, double dt, double eps, double
     const double gU = Ueff > 0 ? gamma / Ueff : INFINITY;
     const double A = dt * gamma * eps / (g->dx * g->dx);
     if (!(gamma > 0)) return fail(CDI_ERR_CONDITION, "gamma must be > 0 for the boundedness condition");
-    int ok = cdi_check_condition(eps / g->dx, gU, A, g->Df);
+    // U is measured on the stored (possibly FP32-rounded) velocity, so a
+    // configuration placed on the line with a double gamma may sit a rounding
+    // error below it: allow a slack of four units of the storage precision.
+    const double rel = g->dtype == CDI_F32 ? 4.0 * FLT_EPSILON : 1e-12;
+    int ok = condition_holds(eps / g->dx, gU, A, g->Df, rel);
     if (ok < 0) return ok;
     if (!ok)
         return fail(CDI_ERR_CONDITION,
@@ -318,12 +344,11 @@ static int step_t(cdi_grid *g, const void *in, void *out, double dt, double eps,
     a.v = (const T *)(g->v ? g->v : g->u);  // ny == nz == 1: v is inert
     a.w = (const T *)(g->w ? g->w : g->u);  // nz == 1: w is inert
     a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
-    a.zchunk = g->fwd.zchunk;
     a.c = coefs<T>(g, dt, eps, gamma, vs);
     a.red = scratch(g, g->rec, 1);
-    if (cdi::fwd_blocks(g->fwd.tile, a.zchunk, g->nx, g->ny, g->nz) > g->capacity)
+    if (g->fwd.nblocks > g->capacity)
         return fail(CDI_ERR_STATE, "launch configuration exceeds the reduction scratch");
-    cudaError_t e = cdi::launch_fwd<T>(a, g->fwd.tile, s);
+    cudaError_t e = cdi::launch_fwd<T>(a, g->fwd.tile, g->fwd.nblocks, s);
     if (e != cudaSuccess) return cuda_fail(e, "forward step launch");
     return CDI_OK;
 }

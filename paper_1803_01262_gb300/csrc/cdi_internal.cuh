@@ -52,7 +52,6 @@ struct FwdArgs {
     const T *__restrict__ v;
     const T *__restrict__ w;
     int nx, ny, nz;
-    int zchunk;
     StepCoef<T> c;
     RedScratch red;
 };
@@ -73,18 +72,23 @@ struct AdjArgs {
     T c_vel;                     // vel_scale / 2 (velocity gradient factor)
 };
 
-// Launch configurations of the fused forward step (tile BX x BY, z chunk).
+// Launch configuration of a kernel: tile shape, z chunk (adjoint), block count.
 struct LaunchCfg {
-    int tile;    // index into the tile table (see cdi_fwd.cu)
-    int zchunk;  // planes per block along z
+    int tile;     // index into the kernel's tile table
+    int zchunk;   // planes per block along z (adjoint kernel)
+    int nblocks;  // blocks per launch (forward kernel: balanced single wave)
 };
 
 int fwd_num_tiles();
 void fwd_tile_dims(int tile, int *bx, int *by);
-int fwd_blocks(int tile, int zchunk, int nx, int ny, int nz);
+long long fwd_units(int tile, int nx, int ny, int nz);
+
+// Blocks of fwd_kernel<T> with this tile that fit on one SM (sets the smem attribute).
+template <typename T>
+cudaError_t fwd_occupancy(int tile, int *resident);
 
 template <typename T>
-cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, cudaStream_t s);
+cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_stats(const T *phi, long long n, T tol, RedScratch red, int nblocks,

@@ -247,6 +247,8 @@ def random_velocity(shape, h, nmodes=32, kmax=4, seed=0, umax=1.0):
         Ay = None
     u, v, w = staggered_curl(Ax, Ay, Az, h)
     U = face_umax(u, v, w)
+    if U == 0.0:  # e.g. a 1x1x1 box: the discrete curl vanishes identically
+        return u, v, w
     s = umax / U
     return u * s, v * s, w * s
 
