@@ -188,6 +188,30 @@ CDI_API int cdi_check_condition(double eps_over_dx, double gamma_over_U, double 
  * gamma eps) (Eq. 27), RK4 2.79 dx^2/(4 D_f gamma eps) (Eq. 28). */
 CDI_API int cdi_max_dt(double dx, double eps, double gamma, int Df, int scheme, double *dt);
 
+/* Kernels with a tunable launch configuration. */
+enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
+
+/* Choose the launch configuration of a kernel of this grid (not part of the
+ * paper: a performance control).  Forward tiles: 0..3 one cell per thread
+ * (32x8, 32x16, 64x8, 32x4 cells), 4 and 5 sixteen-byte vectors per thread
+ * (16x16 and 16x8 threads; need nx % (16/sizeof(element)) == 0); tile < 0
+ * restores the default.  blocks_per_sm <= 0 fills the GPU; nchunks <= 0
+ * picks the number of z chunks per tile column from a cost model.  Adjoint
+ * tiles: 0..2 (32x8, 32x16, 32x4 cells), nchunks sets its z chunking.  Every
+ * configuration computes the same result up to the order of the reduction
+ * partials. */
+CDI_API int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchunks);
+
+/* Current launch configuration (any pointer may be NULL). */
+CDI_API int cdi_get_launch(const cdi_grid *g, int which, int *tile, int *nblocks, int *nchunks);
+
+/* Time every forward launch configuration on phi_a/phi_b (device, contents
+ * overwritten) with CUDA events on the stream (one warm-up + reps launches
+ * each), keep the fastest, and return its mean time in *best_ms (may be
+ * NULL).  Synchronises the stream. */
+CDI_API int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps,
+                         double gamma, int reps, double *best_ms, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 CDI_API const char *cdi_last_error_string(void);
 

@@ -23,6 +23,9 @@ CDI_ERR_CONDITION, CDI_ERR_NAN, CDI_ERR_TIMEOUT, CDI_ERR_STATE = -4, -5, -6, -7
 CDI_F32, CDI_F64 = 0, 1
 CDI_EULER, CDI_RK2, CDI_RK3, CDI_RK4 = 0, 1, 2, 3
 CDI_CHECK_CONDITION = 1
+CDI_KERNEL_FORWARD, CDI_KERNEL_ADJOINT = 0, 1
+FWD_TILES = 6
+ADJ_TILES = 3
 
 _ERRNAMES = {-1: "CDI_ERR_ARG", -2: "CDI_ERR_DIM", -3: "CDI_ERR_CUDA", -4: "CDI_ERR_CONDITION",
              -5: "CDI_ERR_NAN", -6: "CDI_ERR_TIMEOUT", -7: "CDI_ERR_STATE"}
@@ -68,6 +71,9 @@ SIGNATURES = {
     "cdi_step_adjoint": [_V, _V, _V, _V, _V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _V],
     "cdi_check_condition": [_Dbl, _Dbl, _Dbl, _I],
     "cdi_max_dt": [_Dbl, _Dbl, _Dbl, _I, _I, _P(_Dbl)],
+    "cdi_set_launch": [_V, _I, _I, _I, _I],
+    "cdi_get_launch": [_V, _I, _P(_I), _P(_I), _P(_I)],
+    "cdi_autotune": [_V, _V, _V, _Dbl, _Dbl, _Dbl, _I, _P(_Dbl), _V],
 }
 _RESTYPE = {"cdi_last_error_string": ctypes.c_char_p}
 
@@ -218,6 +224,22 @@ class Grid:
                                 CDI_CHECK_CONDITION if check else 0, ctypes.byref(s),
                                 _stream(stream)))
         return s.as_dict()
+
+    def set_launch(self, which=CDI_KERNEL_FORWARD, tile=-1, blocks_per_sm=0, nchunks=0):
+        """Force a launch configuration (tile < 0: the default)."""
+        _ck(lib().cdi_set_launch(self._h, which, tile, blocks_per_sm, nchunks))
+
+    def get_launch(self, which=CDI_KERNEL_FORWARD):
+        t, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _ck(lib().cdi_get_launch(self._h, which, ctypes.byref(t), ctypes.byref(b), ctypes.byref(c)))
+        return dict(tile=t.value, nblocks=b.value, nchunks=c.value)
+
+    def autotune(self, a, b, dt, eps, gamma, reps=5, stream=None):
+        """Time all forward configurations on scratch buffers a, b; keep the fastest."""
+        ms = ctypes.c_double()
+        _ck(lib().cdi_autotune(self._h, self._arr(a, "a"), self._arr(b, "b"), dt, eps, gamma, reps,
+                               ctypes.byref(ms), _stream(stream)))
+        return ms.value
 
     def step_adjoint(self, phi_k, lam_next, lam_k, dt, eps, gamma, vel_scale=1.0, grads=None,
                      stream=None):

@@ -91,23 +91,59 @@ static void reset_run_host(StatsRec *r)
     r->mx_run = -INFINITY;
 }
 
-// Forward launch: tile shape and one balanced wave of resident blocks
-// (never more blocks than tile-planes).
-static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, LaunchCfg *c)
+// Forward launch: a tile shape, as many blocks as fit on the GPU at once, and
+// the number of z chunks per tile column.  Blocks take (chunk, tile) units
+// round-robin; with nchunks <= 0 the count minimises
+//   max(rounds * (planes per unit + 3), units * (planes per unit + 1) / blocks),
+// a per-block critical path (3 planes of prologue per unit) against the
+// average load (1 plane of re-read per unit).
+static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, LaunchCfg *c)
 {
+    if (tile < 0 || tile >= cdi::fwd_num_tiles())
+        return fail(CDI_ERR_ARG, "forward tile %d out of range", tile);
+    const int es = (int)esize(g);
+    if (cdi::fwd_tile_is_vec(tile) && g->nx % (16 / es) != 0)
+        return fail(CDI_ERR_ARG, "vector tile needs nx %% %d == 0", 16 / es);
     int resident = 0;
     cudaError_t e = g->dtype == CDI_F64 ? cdi::fwd_occupancy<double>(tile, &resident)
                                         : cdi::fwd_occupancy<float>(tile, &resident);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (resident < 1) return fail(CDI_ERR_CUDA, "forward kernel does not fit on an SM");
     if (blocks_per_sm > 0 && blocks_per_sm < resident) resident = blocks_per_sm;
-    long long nb = (long long)resident * g->sm_count;
-    const long long units = cdi::fwd_units(tile, g->nx, g->ny, g->nz);
-    if (nb > units) nb = units;
+    const long long G = (long long)resident * g->sm_count;
+    const long long tiles = cdi::fwd_tiles_xy(tile, es, g->nx, g->ny);
+    const int nz = g->nz;
+    if (nchunks <= 0) {
+        double best = 1e300;
+        for (int nc = 1; nc <= nz; ++nc) {
+            const int zc = (nz + nc - 1) / nc;
+            if (nc > 1 && zc == (nz + nc - 2) / (nc - 1)) continue;  // same split as nc - 1
+            const long long units = tiles * ((nz + zc - 1) / zc);
+            const double rounds = (double)((units + G - 1) / G);
+            const double cost = fmax(rounds * (zc + 3.0), (double)units * (zc + 1.0) / (double)G);
+            if (cost < best * (1.0 - 1e-9)) {
+                best = cost;
+                nchunks = nc;
+            }
+        }
+    }
+    if (nchunks > nz) nchunks = nz;
+    const int zc = (nz + nchunks - 1) / nchunks;
+    const long long units = tiles * ((nz + zc - 1) / zc);
+    long long nb = G < units ? G : units;
+    if (nb > g->capacity) nb = g->capacity;
     c->tile = tile;
     c->zchunk = 0;
     c->nblocks = (int)nb;
+    c->nchunks = nchunks;
     return CDI_OK;
+}
+
+static int default_fwd_tile(const cdi_grid *g)
+{
+    const int vx = 16 / (int)esize(g);
+    if (g->nx % vx == 0 && g->nx >= 48) return g->ny >= 12 ? 4 : 5;
+    return (g->nx >= 32 && g->ny >= 16) ? 1 : 3;
 }
 
 // Adjoint launch: z chunk giving about eight blocks per SM.
@@ -123,6 +159,7 @@ static LaunchCfg adj_default(const cdi_grid *g)
     if (zc > g->nz) zc = g->nz;
     c.zchunk = (int)zc;
     c.nblocks = 0;
+    c.nchunks = 0;
     return c;
 }
 
@@ -173,7 +210,7 @@ int cdi_create_grid(cdi_grid **out, int nx, int ny, int nz, double dx, int dtype
         cdi_destroy_grid(g);
         return cuda_fail(e, "scratch init");
     }
-    if (int rc = fwd_cfg(g, (nx >= 32 && ny >= 16) ? 1 : 3, 0, &g->fwd)) {
+    if (int rc = fwd_cfg(g, default_fwd_tile(g), 0, 0, &g->fwd)) {
         cdi_destroy_grid(g);
         return rc;
     }
@@ -348,7 +385,7 @@ static int step_t(cdi_grid *g, const void *in, void *out, double dt, double eps,
     a.red = scratch(g, g->rec, 1);
     if (g->fwd.nblocks > g->capacity)
         return fail(CDI_ERR_STATE, "launch configuration exceeds the reduction scratch");
-    cudaError_t e = cdi::launch_fwd<T>(a, g->fwd.tile, g->fwd.nblocks, s);
+    cudaError_t e = cdi::launch_fwd<T>(a, g->fwd.tile, g->fwd.nblocks, g->fwd.nchunks, s);
     if (e != cudaSuccess) return cuda_fail(e, "forward step launch");
     return CDI_OK;
 }
@@ -503,3 +540,96 @@ int cdi_step_adjoint(cdi_grid *g, const void *phi_k, const void *lam_next, void 
         : adjoint_t<float>(g, phi_k, lam_next, lam_k, gu, gv, gw, dt, eps, gamma, vel_scale, s);
 }
 
+
+int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchunks)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (which == CDI_KERNEL_FORWARD) {
+        if (tile < 0) tile = default_fwd_tile(g);
+        LaunchCfg c;
+        if (int rc = fwd_cfg(g, tile, blocks_per_sm, nchunks, &c)) return rc;
+        g->fwd = c;
+        return CDI_OK;
+    }
+    if (which == CDI_KERNEL_ADJOINT) {
+        if (tile < 0) {
+            g->adj = adj_default(g);
+            return CDI_OK;
+        }
+        if (tile >= cdi::adj_num_tiles()) return fail(CDI_ERR_ARG, "adjoint tile %d out of range", tile);
+        LaunchCfg c = adj_default(g);
+        c.tile = tile;
+        if (nchunks > 0) c.zchunk = (g->nz + nchunks - 1) / nchunks;
+        if (cdi::adj_blocks(c.tile, c.zchunk, g->nx, g->ny, g->nz) > g->capacity)
+            return fail(CDI_ERR_ARG, "adjoint configuration needs more blocks than the scratch holds");
+        g->adj = c;
+        return CDI_OK;
+    }
+    return fail(CDI_ERR_ARG, "unknown kernel %d", which);
+}
+
+int cdi_get_launch(const cdi_grid *g, int which, int *tile, int *nblocks, int *nchunks)
+{
+    if (int rc = check_grid(g)) return rc;
+    const LaunchCfg *c = which == CDI_KERNEL_FORWARD ? &g->fwd : which == CDI_KERNEL_ADJOINT ? &g->adj : nullptr;
+    if (!c) return fail(CDI_ERR_ARG, "unknown kernel %d", which);
+    if (tile) *tile = c->tile;
+    if (nblocks) *nblocks = c->nblocks;
+    if (nchunks) *nchunks = which == CDI_KERNEL_FORWARD ? c->nchunks : (g->nz + c->zchunk - 1) / c->zchunk;
+    return CDI_OK;
+}
+
+int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps, double gamma, int reps,
+                 double *best_ms, void *stream)
+{
+    if (int rc = check_step_args(g, phi_a, phi_b, dt, eps, gamma, 1.0)) return rc;
+    if (reps < 1) return fail(CDI_ERR_ARG, "reps must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    const LaunchCfg saved = g->fwd;
+    LaunchCfg best = saved;
+    float best_t = 1e30f;
+    int rc = CDI_OK;
+    const int chunk_opts[] = {0, 1, 2, 4, 8, 16};
+    for (int tile = 0; tile < cdi::fwd_num_tiles() && rc == CDI_OK; ++tile) {
+        if (cdi::fwd_tile_is_vec(tile) && g->nx % (16 / (int)esize(g)) != 0) continue;
+        for (int oi = 0; oi < (int)(sizeof(chunk_opts) / sizeof(int)); ++oi) {
+            if (chunk_opts[oi] > g->nz) continue;
+            LaunchCfg c;
+            if (fwd_cfg(g, tile, 0, chunk_opts[oi], &c) != CDI_OK) continue;
+            g->fwd = c;
+            void *src = phi_a, *dst = phi_b;
+            // warm-up launch, then reps timed launches (ping-pong)
+            for (int i = 0; i <= reps && rc == CDI_OK; ++i) {
+                if (i == 1 && (e = cudaEventRecord(e0, s)) != cudaSuccess) rc = cuda_fail(e, "event");
+                if (rc == CDI_OK)
+                    rc = g->dtype == CDI_F64 ? step_t<double>(g, src, dst, dt, eps, gamma, 1.0, s)
+                                             : step_t<float>(g, src, dst, dt, eps, gamma, 1.0, s);
+                void *t = src; src = dst; dst = t;
+            }
+            if (rc != CDI_OK) break;
+            if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                rc = cuda_fail(e, "event");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (ms < best_t) {
+                best_t = ms;
+                best = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    g->fwd = rc == CDI_OK ? best : saved;
+    if (rc == CDI_OK && best_ms) *best_ms = best_t;
+    return rc;
+}

@@ -2,27 +2,28 @@
 // Eq. 18-22 in coefficient form) for sm_103a, plus the stand-alone
 // reductions.  No tensor cores: the step is a memory-bound stencil.
 //
-// Kernel structure (one block = a BX x BY column of cells marching along z):
-//   * phi planes are staged with a halo of 2 in x and y by cp.async into an
-//     8-slot shared-memory ring, PF_DIST planes ahead of use, so every phi
-//     value is read from global memory about once per block and the loads
-//     overlap the arithmetic; face velocities are prefetched into registers
-//     one plane ahead;
-//   * blocks split the (tile, plane) index space into equal contiguous
-//     ranges (one launch = one wave of resident blocks, balanced to a plane);
-//   * at plane k+1 the block computes the cell-centre normals
-//     n = g/|g| (g = central differences, n = 0 where g = 0) and the
-//     sharpening vector s = phi (1 - phi) n for its cells and for a one-cell
-//     ring (the x-ring only needs s_x, the y-ring only s_y); s_x and s_y go to
-//     a 2-slot shared buffer, s_z stays in a register;
-//   * at plane k every thread evaluates the six face fluxes of its cell,
-//       F = c_adv u_f (phi_L + phi_R) - c_dif (phi_R - phi_L) + c_shp (s_L + s_R),
-//     (the z face below is carried in a register from the previous plane),
-//     writes phi' = phi - c_upd sum_d (F_+ - F_-) and folds phi' into the
-//     per-thread mass / min / max / violation accumulators;
-//   * the block partials are finished by the last block (cdi_reduce.cuh).
-// All indices wrap periodically; tiles may overhang the grid (ragged edges),
-// overhanging threads compute on wrapped data but never write.
+// Per face between cells L and R along axis d:
+//   F = c_adv u_f (phi_L + phi_R) - c_dif (phi_R - phi_L) + c_shp (s_L + s_R),
+//   s = phi (1 - phi) g/|g|,  g_d = phi_{c+e_d} - phi_{c-e_d}  (s = 0 where g = 0),
+//   phi'_c = phi_c - c_upd sum_d (F_{c+1/2} - F_{c-1/2}).
+//
+// Two kernels share one structure (a block owns an x-y tile and marches along
+// z over a chunk of planes):
+//   fwd_vec_kernel  -- each thread owns a 16-byte vector of x-cells (4 float
+//                      or 2 double); phi and the three face-velocity planes
+//                      are staged by 16-byte cp.async two planes ahead of use;
+//                      two extra warps compute the sharpening ring (one cell
+//                      beyond the tile in x and in y) so the normal phase stays
+//                      balanced.  Needs nx % (16/sizeof(T)) == 0.
+//   fwd_kernel      -- one cell per thread, element-wise cp.async for phi,
+//                      register-prefetched velocities; any extents.
+// Work units are (z chunk, tile) pairs taken round-robin in chunk-major
+// order, so blocks resident together work on neighbouring tiles at the same
+// planes and the halo rows they share are served from L2.
+// Every block folds its outputs into mass / min / max / violation partials,
+// finished by the last block (cdi_reduce.cuh).
+// All indices wrap periodically; tiles may overhang the grid (ragged edges):
+// overhanging cells are computed on wrapped data but never written.
 #include "cdi_internal.cuh"
 #include "cdi_reduce.cuh"
 #include "cdi_async.cuh"
@@ -32,9 +33,351 @@ namespace cdi {
 __device__ __forceinline__ float rsqrt_t(float q) { return rsqrtf(q); }
 __device__ __forceinline__ double rsqrt_t(double q) { return rsqrt(q); }
 
-// Pipeline depth: phi plane k+2+PF_DIST is in flight while plane k is updated.
-constexpr int PF_DIST = 2;
-constexpr int NSLOT = 8;  // power of two >= PF_DIST + 3 live planes
+template <typename T>
+__device__ __forceinline__ T flux(T cadv_u, T cdif, T cshp, T pl, T pr, T sl, T sr)
+{
+    return cadv_u * (pl + pr) - cdif * (pr - pl) + cshp * (sl + sr);
+}
+
+// 16-byte vector of T.
+template <typename T> struct V16;
+template <> struct V16<float> {
+    static constexpr int N = 4;
+    __device__ __forceinline__ static void ld(float *d, const float *s)
+    {
+        const float4 v = *reinterpret_cast<const float4 *>(s);
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
+    __device__ __forceinline__ static void st(float *d, const float *s)
+    {
+        *reinterpret_cast<float4 *>(d) = make_float4(s[0], s[1], s[2], s[3]);
+    }
+};
+template <> struct V16<double> {
+    static constexpr int N = 2;
+    __device__ __forceinline__ static void ld(double *d, const double *s)
+    {
+        const double2 v = *reinterpret_cast<const double2 *>(s);
+        d[0] = v.x; d[1] = v.y;
+    }
+    __device__ __forceinline__ static void st(double *d, const double *s)
+    {
+        *reinterpret_cast<double2 *>(d) = make_double2(s[0], s[1]);
+    }
+};
+
+// Work unit u -> (tile origin, z range).
+struct Unit {
+    int x0, y0, z0, z1;
+};
+__device__ __forceinline__ Unit unit_of(int u, int ntiles, int tiles_x, int bw, int bh, int zc, int nz)
+{
+    Unit r;
+    const int chunk = u / ntiles, tile = u - chunk * ntiles;
+    r.x0 = (tile % tiles_x) * bw;
+    r.y0 = (tile / tiles_x) * bh;
+    r.z0 = chunk * zc;
+    r.z1 = min(nz, r.z0 + zc);
+    return r;
+}
+
+// ===========================================================================
+// Vector kernel
+
+template <typename T, int TX, int TY>
+struct VecCfg {
+    static constexpr int VX = 16 / sizeof(T);
+    static constexpr int W = TX * VX, H = TY;
+    static constexpr int NOWN = TX * TY;
+    static constexpr int NT = NOWN + 64;     // + one y-ring warp + one x-ring warp
+    static constexpr int PP = W + 2 * VX;    // phi row pitch: x0-VX .. x0+W+VX-1
+    static constexpr int PR = H + 4;         // phi rows: y0-2 .. y0+H+1
+    static constexpr int PHI = PR * PP;
+    static constexpr int UP = W + VX;        // u row pitch: x0-VX .. x0+W-1
+    static constexpr int USZ = H * UP;
+    static constexpr int VSZ = (H + 1) * W;  // v rows: y0-1 .. y0+H-1
+    static constexpr int WSZ = H * W;
+    static constexpr int VEL = USZ + VSZ + WSZ;
+    static constexpr int SXP = W + 2 * VX;   // s_x pitch: x0-1 at VX-1, x0+W at VX+W
+    static constexpr int SXS = H * SXP;
+    static constexpr int SYS = (H + 2) * W;  // s_y rows: y0-1 .. y0+H
+    static constexpr int NSP = 5, NSV = 3;   // ring slots (phi, velocity)
+    static constexpr int CPHI = PHI / VX, CU = USZ / VX, CV = VSZ / VX, CW = WSZ / VX;
+    static constexpr int RPHI = (CPHI + NT - 1) / NT;
+    static constexpr int RU = (CU + NT - 1) / NT, RV = (CV + NT - 1) / NT, RW = (CW + NT - 1) / NT;
+    static constexpr size_t bytes = sizeof(T) * (size_t)(NSP * PHI + NSV * VEL + 2 * SXS + 2 * SYS);
+    static_assert(2 * TX <= 32 && 2 * TY <= 32, "ring warps hold 2*TX groups and 2*TY cells");
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(VecCfg<T, TX, TY>::NT, 2)
+fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
+{
+    using C = VecCfg<T, TX, TY>;
+    using VV = V16<T>;
+    constexpr int VX = C::VX, W = C::W, H = C::H, PP = C::PP, UP = C::UP, SXP = C::SXP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sphi = reinterpret_cast<T *>(smem_raw);      // [NSP][PHI]
+    T *const svel = sphi + C::NSP * C::PHI;                // [NSV][VEL] = u | v | w
+    T *const ssx = svel + C::NSV * C::VEL;                 // [2][SXS]
+    T *const ssy = ssx + 2 * C::SXS;                       // [2][SYS]
+
+    const int tid = threadIdx.x;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long plane = (long long)nx * ny;
+    const int tiles_x = (nx + W - 1) / W;
+    const int ntiles = tiles_x * ((ny + H - 1) / H);
+    const int zc = (nz + nchunks - 1) / nchunks;
+    const int units = ntiles * ((nz + zc - 1) / zc);
+    const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_shp = a.c.c_shp, c_upd = a.c.c_upd;
+
+    // Role: own vector of cells (tx, ty), a y-ring group, or an x-ring cell.
+    const bool is_own = tid < C::NOWN;
+    const int tx = tid % TX, ty = tid / TX;
+    const int rr = tid - C::NOWN;  // 0..63 for ring threads
+    const bool is_yring = !is_own && rr < 32 && rr < 2 * TX;
+    const bool is_xring = !is_own && rr >= 32 && rr - 32 < 2 * TY;
+    const int ry_row = (rr < TX) ? -1 : H, ry_col = rr % TX;  // y-ring group
+    const int rx_row = (rr - 32) % TY;                         // x-ring cell
+    const int rx_col = ((rr - 32) < TY) ? -1 : W;
+
+    // Normals and sharpening of the VX cells of group (gc, ly) of plane Pm
+    // (Pmm, Pmp: the planes below and above).
+    auto sharp_group = [&](const T *Pm, const T *Pmm, const T *Pmp, int gc, int ly, T *s0, T *s1,
+                           T *s2) {
+        const int off = (ly + 2) * PP + VX + gc * VX;
+        T c[VX], yn[VX], yp[VX], zn[VX], zp[VX];
+        VV::ld(c, Pm + off);
+        VV::ld(yn, Pm + off - PP);
+        VV::ld(yp, Pm + off + PP);
+        VV::ld(zn, Pmm + off);
+        VV::ld(zp, Pmp + off);
+        const T L = Pm[off - 1], R = Pm[off + VX];
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+            const T g0 = (i + 1 < VX ? c[i + 1] : R) - (i > 0 ? c[i - 1] : L);
+            const T g1 = yp[i] - yn[i];
+            const T g2 = zp[i] - zn[i];
+            const T q = g0 * g0 + g1 * g1 + g2 * g2;
+            const T inv = q > T(0) ? rsqrt_t(q) : T(0);
+            const T wgt = c[i] * (T(1) - c[i]) * inv;
+            s0[i] = wgt * g0;
+            s1[i] = wgt * g1;
+            s2[i] = wgt * g2;
+        }
+    };
+    auto sharp_cell = [&](const T *Pm, const T *Pmm, const T *Pmp, int lx, int ly) {
+        const int off = (ly + 2) * PP + VX + lx;
+        const T p = Pm[off];
+        const T g0 = Pm[off + 1] - Pm[off - 1];
+        const T g1 = Pm[off + PP] - Pm[off - PP];
+        const T g2 = Pmp[off] - Pmm[off];
+        const T q = g0 * g0 + g1 * g1 + g2 * g2;
+        const T inv = q > T(0) ? rsqrt_t(q) : T(0);
+        return p * (T(1) - p) * inv * g0;  // s_x only
+    };
+
+    Acc<T> acc;
+    acc.init();
+
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const Unit un = unit_of(u, ntiles, tiles_x, W, H, zc, nz);
+        const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
+
+        // Global in-plane offsets of this thread's 16-byte copy chunks.
+        int gphi[C::RPHI], gu[C::RU], gv[C::RV], gw[C::RW];
+#pragma unroll
+        for (int r = 0; r < C::RPHI; ++r) {
+            const int e = tid + r * C::NT, row = e / (PP / VX), col = e - row * (PP / VX);
+            gphi[r] = wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+        }
+#pragma unroll
+        for (int r = 0; r < C::RU; ++r) {
+            const int e = tid + r * C::NT, row = e / (UP / VX), col = e - row * (UP / VX);
+            gu[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+        }
+#pragma unroll
+        for (int r = 0; r < C::RV; ++r) {
+            const int e = tid + r * C::NT, row = e / (W / VX), col = e - row * (W / VX);
+            gv[r] = wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+        }
+#pragma unroll
+        for (int r = 0; r < C::RW; ++r) {
+            const int e = tid + r * C::NT, row = e / (W / VX), col = e - row * (W / VX);
+            gw[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+        }
+        auto issue_phi = [&](int z, int slot) {
+            const T *src = a.phi + (long long)wrapi(z, nz) * plane;
+            T *dst = sphi + slot * C::PHI;
+#pragma unroll
+            for (int r = 0; r < C::RPHI; ++r) {
+                const int e = tid + r * C::NT;
+                if (e < C::CPHI) cp_async<16>(dst + e * VX, src + gphi[r]);
+            }
+        };
+        auto issue_vel = [&](int z, int slot) {
+            const long long zo = (long long)z * plane;
+            T *dst = svel + slot * C::VEL;
+#pragma unroll
+            for (int r = 0; r < C::RU; ++r) {
+                const int e = tid + r * C::NT;
+                if (e < C::CU) cp_async<16>(dst + e * VX, a.u + zo + gu[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < C::RV; ++r) {
+                const int e = tid + r * C::NT;
+                if (e < C::CV) cp_async<16>(dst + C::USZ + e * VX, a.v + zo + gv[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < C::RW; ++r) {
+                const int e = tid + r * C::NT;
+                if (e < C::CW) cp_async<16>(dst + C::USZ + C::VSZ + e * VX, a.w + zo + gw[r]);
+            }
+        };
+
+        // phi slot of plane z: (z - z0 + 2) mod 5; velocity slot: (z - z0) mod 3.
+        __syncthreads();  // the previous unit's readers are done with every slot
+        for (int d = 0; d < 5; ++d) issue_phi(z0 - 2 + d, d);  // planes z0-2 .. z0+2
+        issue_vel(z0, 0);
+        cp_async_commit();
+        if (z0 + 3 <= z1 + 1) issue_phi(z0 + 3, 0);            // slot (5 mod 5)
+        if (z0 + 1 < z1) issue_vel(z0 + 1, 1);
+        cp_async_commit();
+
+        const int own_x = x0 + tx * VX, own_y = y0 + ty;
+        const bool writes = is_own && own_x < nx && own_y < ny;
+        const long long own_off = (long long)wrapi(own_y, ny) * nx + wrapi(own_x, nx);
+
+        T wlo[VX];  // w on the face below plane z0 (own cells)
+        if (is_own) {
+            const T *src = a.w + (long long)wrapi(z0 - 1, nz) * plane + own_off;
+#pragma unroll
+            for (int i = 0; i < VX; ++i) wlo[i] = __ldg(src + i);
+        }
+        cp_async_wait<1>();
+        __syncthreads();
+
+        // Prologue: s_z at plane z0-1 (own), s at plane z0 (own + ring), flux at z0-1/2.
+        T szc[VX], Fzm[VX];
+        {
+            const T *P0 = sphi + 2 * C::PHI, *Pm1 = sphi + 1 * C::PHI, *Pm2 = sphi;
+            const T *P1 = sphi + 3 * C::PHI;
+            if (is_own) {
+                T a0[VX], a1[VX], szm[VX], s0[VX], s1[VX];
+                sharp_group(Pm1, Pm2, P0, tx, ty, a0, a1, szm);
+                sharp_group(P0, Pm1, P1, tx, ty, s0, s1, szc);
+                VV::st(ssx + (z0 & 1) * C::SXS + ty * SXP + VX + tx * VX, s0);
+                VV::st(ssy + (z0 & 1) * C::SYS + (ty + 1) * W + tx * VX, s1);
+                T pm[VX], pc[VX];
+                VV::ld(pm, Pm1 + (ty + 2) * PP + VX + tx * VX);
+                VV::ld(pc, P0 + (ty + 2) * PP + VX + tx * VX);
+#pragma unroll
+                for (int i = 0; i < VX; ++i)
+                    Fzm[i] = flux(c_adv * wlo[i], c_dif, c_shp, pm[i], pc[i], szm[i], szc[i]);
+            } else if (is_yring) {
+                T s0[VX], s1[VX], s2[VX];
+                sharp_group(P0, Pm1, P1, ry_col, ry_row, s0, s1, s2);
+                VV::st(ssy + (z0 & 1) * C::SYS + (ry_row + 1) * W + ry_col * VX, s1);
+            } else if (is_xring) {
+                ssx[(z0 & 1) * C::SXS + rx_row * SXP + VX + rx_col] = sharp_cell(P0, Pm1, P1, rx_col, rx_row);
+            }
+        }
+
+        int pk = 2;  // phi slot of plane k
+        int vk = 0;  // velocity slot of plane k
+        for (int k = z0; k < z1; ++k) {
+            const int pk1 = pk == 4 ? 0 : pk + 1;
+            const int pk2 = pk1 == 4 ? 0 : pk1 + 1;
+            const int pkm = pk == 0 ? 4 : pk - 1;   // also the slot of plane k+4
+            const int vk2 = vk == 0 ? 2 : vk - 1;   // slot of plane k+2
+            // S1: phi plane k+2 and the velocities of plane k have landed, and
+            // every thread has left iteration k-1.
+            cp_async_wait<1>();
+            __syncthreads();
+            if (k + 4 <= z1 + 1) issue_phi(k + 4, pkm);
+            if (k + 2 < z1) issue_vel(k + 2, vk2);
+            cp_async_commit();
+
+            // B: sharpening at plane k+1.
+            const T *Pk = sphi + pk * C::PHI, *Pk1 = sphi + pk1 * C::PHI, *Pk2 = sphi + pk2 * C::PHI;
+            const int b1 = (k + 1) & 1;
+            T szn[VX];
+            if (is_own) {
+                T s0[VX], s1[VX];
+                sharp_group(Pk1, Pk, Pk2, tx, ty, s0, s1, szn);
+                VV::st(ssx + b1 * C::SXS + ty * SXP + VX + tx * VX, s0);
+                VV::st(ssy + b1 * C::SYS + (ty + 1) * W + tx * VX, s1);
+            } else if (is_yring) {
+                T s0[VX], s1[VX], s2[VX];
+                sharp_group(Pk1, Pk, Pk2, ry_col, ry_row, s0, s1, s2);
+                VV::st(ssy + b1 * C::SYS + (ry_row + 1) * W + ry_col * VX, s1);
+            } else if (is_xring) {
+                ssx[b1 * C::SXS + rx_row * SXP + VX + rx_col] = sharp_cell(Pk1, Pk, Pk2, rx_col, rx_row);
+            }
+            __syncthreads();
+
+            // C: fluxes and update at plane k.
+            if (is_own) {
+                const int b = k & 1;
+                const int po = (ty + 2) * PP + VX + tx * VX;
+                T c[VX], yn[VX], yp[VX], zp[VX];
+                VV::ld(c, Pk + po);
+                VV::ld(yn, Pk + po - PP);
+                VV::ld(yp, Pk + po + PP);
+                VV::ld(zp, Pk1 + po);
+                const T L = Pk[po - 1], R = Pk[po + VX];
+                const T *sxr = ssx + b * C::SXS + ty * SXP + VX + tx * VX;
+                const T *syr = ssy + b * C::SYS + (ty + 1) * W + tx * VX;
+                T sxc[VX], syc[VX], syn[VX], syp[VX];
+                VV::ld(sxc, sxr);
+                VV::ld(syc, syr);
+                VV::ld(syn, syr - W);
+                VV::ld(syp, syr + W);
+                const T sxL = sxr[-1], sxR = sxr[VX];
+                const T *vel = svel + vk * C::VEL;
+                const T *ur = vel + ty * UP + VX + tx * VX;
+                const T *vr = vel + C::USZ + (ty + 1) * W + tx * VX;
+                const T *wr = vel + C::USZ + C::VSZ + ty * W + tx * VX;
+                T uc[VX], vc[VX], vn[VX], wc[VX];
+                VV::ld(uc, ur);
+                VV::ld(vc, vr);
+                VV::ld(vn, vr - W);
+                VV::ld(wc, wr);
+                const T uL = ur[-1];
+                T Fx[VX + 1];
+                Fx[0] = flux(c_adv * uL, c_dif, c_shp, L, c[0], sxL, sxc[0]);
+#pragma unroll
+                for (int i = 1; i < VX; ++i)
+                    Fx[i] = flux(c_adv * uc[i - 1], c_dif, c_shp, c[i - 1], c[i], sxc[i - 1], sxc[i]);
+                Fx[VX] = flux(c_adv * uc[VX - 1], c_dif, c_shp, c[VX - 1], R, sxc[VX - 1], sxR);
+                T o[VX];
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                    const T Fyp = flux(c_adv * vc[i], c_dif, c_shp, c[i], yp[i], syc[i], syp[i]);
+                    const T Fym = flux(c_adv * vn[i], c_dif, c_shp, yn[i], c[i], syn[i], syc[i]);
+                    const T Fzp = flux(c_adv * wc[i], c_dif, c_shp, c[i], zp[i], szc[i], szn[i]);
+                    o[i] = c[i] - c_upd * ((Fx[i + 1] - Fx[i]) + (Fyp - Fym) + (Fzp - Fzm[i]));
+                    Fzm[i] = Fzp;
+                    szc[i] = szn[i];
+                }
+                if (writes) {
+                    VV::st(a.out + (long long)k * plane + own_off, o);
+                    acc.template add_group<VX>(o, a.c.tol);
+                }
+            }
+            pk = pk1;
+            vk = vk == 2 ? 0 : vk + 1;
+        }
+        cp_async_wait<0>();
+    }
+    reduce_and_finish(acc.partial(), a.red);
+}
+
+// ===========================================================================
+// Scalar kernel (any extents)
+
+constexpr int PF_DIST = 2;  // phi plane k+2+PF_DIST is in flight while plane k is updated
+constexpr int NSLOT = 8;    // power of two >= PF_DIST + 3 live planes
 
 template <typename T, int BX, int BY>
 struct FwdSmem {
@@ -45,7 +388,7 @@ struct FwdSmem {
 
 template <typename T, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY)
-fwd_kernel(const FwdArgs<T> a)
+fwd_kernel(const FwdArgs<T> a, const int nchunks)
 {
     constexpr int PX = BX + 4, PY = BY + 4, PLANE = PX * PY;
     constexpr int NT = BX * BY;
@@ -59,6 +402,9 @@ fwd_kernel(const FwdArgs<T> a)
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long plane = (long long)nx * ny;
     const int tiles_x = (nx + BX - 1) / BX;
+    const int ntiles = tiles_x * ((ny + BY - 1) / BY);
+    const int zc = (nz + nchunks - 1) / nchunks;
+    const int units = ntiles * ((nz + zc - 1) / zc);
 
     // Ring cells: threads [0, 2BX) the y-ring, [2BX, 2BX + 2BY) the x-ring.
     int rkind = 0, rx = 0, ry = 0;
@@ -74,7 +420,6 @@ fwd_kernel(const FwdArgs<T> a)
     }
     const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_shp = a.c.c_shp, c_upd = a.c.c_upd;
 
-    // Sharpening vector s = phi (1 - phi) g/|g| at local cell (lx, ly) of plane z.
     auto sharp = [&](int z, int lx, int ly, T &s0, T &s1, T &s2) {
         const int X = lx + 2, Y = ly + 2;
         const int m = z & (NSLOT - 1), mm = (z - 1) & (NSLOT - 1), mp = (z + 1) & (NSLOT - 1);
@@ -105,20 +450,9 @@ fwd_kernel(const FwdArgs<T> a)
     Acc<T> acc;
     acc.init();
 
-    // Balanced work split: the (tile, plane) index space, plane fastest, is cut
-    // into equal contiguous ranges, one per block; a range may cover the end of
-    // one tile column and the start of the next (each piece is a "segment").
-    const long long total = (long long)tiles_x * ((ny + BY - 1) / BY) * nz;
-    const long long per = (total + gridDim.x - 1) / gridDim.x;
-    long long s = (long long)blockIdx.x * per;
-    const long long s_end = min(total, s + per);
-
-    while (s < s_end) {
-        const int tile = (int)(s / nz);
-        const int z0 = (int)(s - (long long)tile * nz);
-        const int z1 = (int)min((long long)nz, z0 + (s_end - s));
-        s += z1 - z0;
-        const int x0 = (tile % tiles_x) * BX, y0 = (tile / tiles_x) * BY;
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const Unit un = unit_of(u, ntiles, tiles_x, BX, BY, zc, nz);
+        const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
 
         int loff[NLOAD];
 #pragma unroll
@@ -143,8 +477,7 @@ fwd_kernel(const FwdArgs<T> a)
             }
         };
 
-        // Prologue: planes z0-2 .. z0+1 (one group), then PF_DIST more groups.
-        __syncthreads();  // previous segment's readers are done with the ring
+        __syncthreads();  // the previous unit's readers are done with the ring
         issue_plane(z0 - 2);
         issue_plane(z0 - 1);
         issue_plane(z0);
@@ -175,28 +508,24 @@ fwd_kernel(const FwdArgs<T> a)
         {
             const T pm = sp[(z0 - 1) & (NSLOT - 1)][ty + 2][tx + 2];
             const T pc = sp[z0 & (NSLOT - 1)][ty + 2][tx + 2];
-            Fzm = c_adv * wlo * (pm + pc) - c_dif * (pc - pm) + c_shp * (szm + szc);
+            Fzm = flux(c_adv * wlo, c_dif, c_shp, pm, pc, szm, szc);
         }
 
         for (int k = z0; k < z1; ++k) {
-            // S1: plane k+2 has landed (and every thread left iteration k-1).
             cp_async_wait<PF_DIST - 1>();
             __syncthreads();
             if (k + 2 + PF_DIST <= z1 + 1) issue_plane(k + 2 + PF_DIST);
             cp_async_commit();
-            // Next plane's face velocities, consumed one iteration later.
-            T un = T(0), umn = T(0), vn = T(0), vmn = T(0), wn = T(0);
+            T un_ = T(0), umn = T(0), vn = T(0), vmn = T(0), wn = T(0);
             if (k + 1 < z1) {
                 const long long zb = (long long)(k + 1) * plane;
-                un = __ldg(a.u + zb + oc); umn = __ldg(a.u + zb + oxm);
+                un_ = __ldg(a.u + zb + oc); umn = __ldg(a.u + zb + oxm);
                 vn = __ldg(a.v + zb + oc); vmn = __ldg(a.v + zb + oym);
                 wn = __ldg(a.w + zb + oc);
             }
-            // B: sharpening at plane k+1.
             T szn;
             sharp_plane(k + 1, szn);
             __syncthreads();
-            // C: fluxes and update at plane k.
             const int m = k & (NSLOT - 1), b = k & 1;
             const T pc = sp[m][ty + 2][tx + 2];
             const T pxm = sp[m][ty + 2][tx + 1], pxp = sp[m][ty + 2][tx + 3];
@@ -204,11 +533,11 @@ fwd_kernel(const FwdArgs<T> a)
             const T pzp = sp[(k + 1) & (NSLOT - 1)][ty + 2][tx + 2];
             const T sxc = sx[b][ty][tx + 1], sxm = sx[b][ty][tx], sxp = sx[b][ty][tx + 2];
             const T syc = sy[b][ty + 1][tx], sym = sy[b][ty][tx], syp = sy[b][ty + 2][tx];
-            const T Fxp = c_adv * uc * (pc + pxp) - c_dif * (pxp - pc) + c_shp * (sxc + sxp);
-            const T Fxm = c_adv * um * (pxm + pc) - c_dif * (pc - pxm) + c_shp * (sxm + sxc);
-            const T Fyp = c_adv * vc * (pc + pyp) - c_dif * (pyp - pc) + c_shp * (syc + syp);
-            const T Fym = c_adv * vm * (pym + pc) - c_dif * (pc - pym) + c_shp * (sym + syc);
-            const T Fzp = c_adv * wc * (pc + pzp) - c_dif * (pzp - pc) + c_shp * (szc + szn);
+            const T Fxp = flux(c_adv * uc, c_dif, c_shp, pc, pxp, sxc, sxp);
+            const T Fxm = flux(c_adv * um, c_dif, c_shp, pxm, pc, sxm, sxc);
+            const T Fyp = flux(c_adv * vc, c_dif, c_shp, pc, pyp, syc, syp);
+            const T Fym = flux(c_adv * vm, c_dif, c_shp, pym, pc, sym, syc);
+            const T Fzp = flux(c_adv * wc, c_dif, c_shp, pc, pzp, szc, szn);
             const T o = pc - c_upd * ((Fxp - Fxm) + (Fyp - Fym) + (Fzp - Fzm));
             if (own) {
                 a.out[(long long)k * plane + oc] = o;
@@ -216,80 +545,87 @@ fwd_kernel(const FwdArgs<T> a)
             }
             Fzm = Fzp;
             szc = szn;
-            uc = un; um = umn; vc = vn; vm = vmn; wc = wn;
+            uc = un_; um = umn; vc = vn; vm = vmn; wc = wn;
         }
         cp_async_wait<0>();
     }
     reduce_and_finish(acc.partial(), a.red);
 }
 
-// ---------------------------------------------------------------------------
-// Tile table and launch
+// ===========================================================================
+// Kernel table and launch
+//
+// Forward tiles: 0..3 scalar BX x BY = 32x8, 32x16, 64x8, 32x4;
+//                4, 5 vector TX x TY = 16x16, 16x8 (x width 16 * 16/sizeof(T)).
 
-struct TileDim { int bx, by; };
-static const TileDim kTiles[] = {{32, 8}, {32, 16}, {64, 8}, {32, 4}};
-static const int kNumTiles = sizeof(kTiles) / sizeof(kTiles[0]);
+int fwd_num_tiles() { return 6; }
 
-int fwd_num_tiles() { return kNumTiles; }
+bool fwd_tile_is_vec(int tile) { return tile >= 4; }
 
-void fwd_tile_dims(int tile, int *bx, int *by)
+void fwd_tile_dims(int tile, int esize, int *bw, int *bh)
 {
-    *bx = kTiles[tile].bx;
-    *by = kTiles[tile].by;
+    static const int sdim[4][2] = {{32, 8}, {32, 16}, {64, 8}, {32, 4}};
+    if (tile < 4) {
+        *bw = sdim[tile][0];
+        *bh = sdim[tile][1];
+    } else {
+        *bw = 16 * (16 / esize);
+        *bh = tile == 4 ? 16 : 8;
+    }
 }
 
-// Work units (tile-planes) of a grid for a tile shape.
-long long fwd_units(int tile, int nx, int ny, int nz)
+long long fwd_tiles_xy(int tile, int esize, int nx, int ny)
 {
-    const TileDim t = kTiles[tile];
-    return (long long)((nx + t.bx - 1) / t.bx) * ((ny + t.by - 1) / t.by) * nz;
+    int bw, bh;
+    fwd_tile_dims(tile, esize, &bw, &bh);
+    return (long long)((nx + bw - 1) / bw) * ((ny + bh - 1) / bh);
 }
 
-template <typename T, int BX, int BY>
-static cudaError_t fwd_prepare(int *resident)
+template <typename K>
+static cudaError_t occ(K kernel, int threads, size_t smem, int *resident)
 {
-    const size_t smem = FwdSmem<T, BX, BY>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(fwd_kernel<T, BX, BY>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, fwd_kernel<T, BX, BY>, BX * BY, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, kernel, threads, smem);
 }
 
 template <typename T>
 cudaError_t fwd_occupancy(int tile, int *resident)
 {
     switch (tile) {
-    case 0: return fwd_prepare<T, 32, 8>(resident);
-    case 1: return fwd_prepare<T, 32, 16>(resident);
-    case 2: return fwd_prepare<T, 64, 8>(resident);
-    case 3: return fwd_prepare<T, 32, 4>(resident);
+    case 0: return occ(fwd_kernel<T, 32, 8>, 256, FwdSmem<T, 32, 8>::bytes, resident);
+    case 1: return occ(fwd_kernel<T, 32, 16>, 512, FwdSmem<T, 32, 16>::bytes, resident);
+    case 2: return occ(fwd_kernel<T, 64, 8>, 512, FwdSmem<T, 64, 8>::bytes, resident);
+    case 3: return occ(fwd_kernel<T, 32, 4>, 128, FwdSmem<T, 32, 4>::bytes, resident);
+    case 4: return occ(fwd_vec_kernel<T, 16, 16>, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, resident);
+    case 5: return occ(fwd_vec_kernel<T, 16, 8>, VecCfg<T, 16, 8>::NT, VecCfg<T, 16, 8>::bytes, resident);
     default: return cudaErrorInvalidValue;
     }
 }
 template cudaError_t fwd_occupancy<float>(int, int *);
 template cudaError_t fwd_occupancy<double>(int, int *);
 
-template <typename T, int BX, int BY>
-static cudaError_t launch_fwd_t(const FwdArgs<T> &a, int nblocks, cudaStream_t s)
+template <typename T>
+cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, cudaStream_t s)
 {
-    fwd_kernel<T, BX, BY><<<nblocks, dim3(BX, BY), FwdSmem<T, BX, BY>::bytes, s>>>(a);
+    switch (tile) {
+    case 0: fwd_kernel<T, 32, 8><<<nblocks, dim3(32, 8), FwdSmem<T, 32, 8>::bytes, s>>>(a, nchunks); break;
+    case 1: fwd_kernel<T, 32, 16><<<nblocks, dim3(32, 16), FwdSmem<T, 32, 16>::bytes, s>>>(a, nchunks); break;
+    case 2: fwd_kernel<T, 64, 8><<<nblocks, dim3(64, 8), FwdSmem<T, 64, 8>::bytes, s>>>(a, nchunks); break;
+    case 3: fwd_kernel<T, 32, 4><<<nblocks, dim3(32, 4), FwdSmem<T, 32, 4>::bytes, s>>>(a, nchunks); break;
+    case 4:
+        fwd_vec_kernel<T, 16, 16><<<nblocks, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, s>>>(a, nchunks);
+        break;
+    case 5:
+        fwd_vec_kernel<T, 16, 8><<<nblocks, VecCfg<T, 16, 8>::NT, VecCfg<T, 16, 8>::bytes, s>>>(a, nchunks);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, cudaStream_t s)
-{
-    switch (tile) {
-    case 0: return launch_fwd_t<T, 32, 8>(a, nblocks, s);
-    case 1: return launch_fwd_t<T, 32, 16>(a, nblocks, s);
-    case 2: return launch_fwd_t<T, 64, 8>(a, nblocks, s);
-    case 3: return launch_fwd_t<T, 32, 4>(a, nblocks, s);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template cudaError_t launch_fwd<float>(const FwdArgs<float> &, int, int, cudaStream_t);
-template cudaError_t launch_fwd<double>(const FwdArgs<double> &, int, int, cudaStream_t);
+template cudaError_t launch_fwd<float>(const FwdArgs<float> &, int, int, int, cudaStream_t);
+template cudaError_t launch_fwd<double>(const FwdArgs<double> &, int, int, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Stand-alone reductions: statistics of any field, and max |component| of

@@ -76,19 +76,21 @@ struct AdjArgs {
 struct LaunchCfg {
     int tile;     // index into the kernel's tile table
     int zchunk;   // planes per block along z (adjoint kernel)
-    int nblocks;  // blocks per launch (forward kernel: balanced single wave)
+    int nblocks;  // blocks per launch (forward: resident blocks, units round-robin)
+    int nchunks;  // z chunks per tile column (forward)
 };
 
 int fwd_num_tiles();
-void fwd_tile_dims(int tile, int *bx, int *by);
-long long fwd_units(int tile, int nx, int ny, int nz);
+bool fwd_tile_is_vec(int tile);
+void fwd_tile_dims(int tile, int esize, int *bw, int *bh);
+long long fwd_tiles_xy(int tile, int esize, int nx, int ny);
 
-// Blocks of fwd_kernel<T> with this tile that fit on one SM (sets the smem attribute).
+// Blocks of the forward kernel with this tile that fit on one SM (sets the smem attribute).
 template <typename T>
 cudaError_t fwd_occupancy(int tile, int *resident);
 
 template <typename T>
-cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, cudaStream_t s);
+cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_stats(const T *phi, long long n, T tol, RedScratch red, int nblocks,

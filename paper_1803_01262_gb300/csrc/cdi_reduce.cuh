@@ -69,6 +69,31 @@ struct Acc<float> {
         ns += (p < 0.f) | (p > 1.f);
         nt += (p < -tol) | (p > 1.f + tol);
     }
+    // N values at once: compensated sum per value, min/max of the group, and
+    // the exact violation counts only when the group leaves [0, 1].
+    template <int N>
+    __device__ __forceinline__ void add_group(const float *o, float tol)
+    {
+        float gmn = o[0], gmx = o[0];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const float y = o[i] - c;
+            const float t = s + y;
+            c = (t - s) - y;
+            s = t;
+            gmn = fminf(gmn, o[i]);
+            gmx = fmaxf(gmx, o[i]);
+        }
+        mn = fminf(mn, gmn);
+        mx = fmaxf(mx, gmx);
+        if (gmn < 0.f || gmx > 1.f) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                ns += (o[i] < 0.f) | (o[i] > 1.f);
+                nt += (o[i] < -tol) | (o[i] > 1.f + tol);
+            }
+        }
+    }
     __device__ __forceinline__ Partial partial() const
     {
         Partial r;
@@ -96,6 +121,26 @@ struct Acc<double> {
         mx = fmax(mx, p);
         ns += (p < 0.0) | (p > 1.0);
         nt += (p < -tol) | (p > 1.0 + tol);
+    }
+    template <int N>
+    __device__ __forceinline__ void add_group(const double *o, double tol)
+    {
+        double gmn = o[0], gmx = o[0];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            s += o[i];
+            gmn = fmin(gmn, o[i]);
+            gmx = fmax(gmx, o[i]);
+        }
+        mn = fmin(mn, gmn);
+        mx = fmax(mx, gmx);
+        if (gmn < 0.0 || gmx > 1.0) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                ns += (o[i] < 0.0) | (o[i] > 1.0);
+                nt += (o[i] < -tol) | (o[i] > 1.0 + tol);
+            }
+        }
     }
     __device__ __forceinline__ Partial partial() const
     {

@@ -216,3 +216,43 @@ def test_reproducible_reduction():
         g.step(a, b, 0.1 * f.h / f.U, f.h, f.U)
         sums.append(g.stats()["sum"])
     assert sums[0] == sums[1] == sums[2]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("tile", range(cdi.FWD_TILES))
+@pytest.mark.parametrize("shape,nchunks", [((9, 21, 68), 0), ((11, 18, 136), 3), ((1, 40, 128), 1),
+                                           ((5, 7, 4), 2), ((20, 33, 72), 7)])
+def test_every_launch_configuration(dtype, tile, shape, nchunks):
+    """Each kernel variant and z chunking gives the oracle's step (ragged tiles included)."""
+    f = random_fields(shape, 31 + shape[2], True, smooth=(tile % 2 == 0))
+    eps, gamma = 1.1 * f.h, 0.9
+    dt = 0.12 * f.h * f.h / (gamma * eps)
+    g, vel = make_grid(f, dtype)
+    g.set_launch(cdi.CDI_KERNEL_FORWARD, tile, 0, nchunks)
+    a = dev(f.phi, dtype)
+    b = torch.empty_like(a)
+    g.step(a, b, dt, eps, gamma, 0.8)
+    st = g.stats()
+    phi, u, v, w = rounded(f, dtype)
+    ref = oracle.step(phi, u, v, w, f.h, dt, eps, gamma, 0.8)
+    ours = b.double().cpu().numpy()
+    assert np.abs(ours - ref).max() <= TOL[dtype]
+    assert st["min"] == ours.min() and st["max"] == ours.max()
+    assert abs(st["sum"] - ours.sum()) <= 1e-9 * abs(ours.sum())
+
+
+def test_autotune_keeps_result():
+    f = I.deformation_3d(64)
+    g, vel = make_grid(f, torch.float32)
+    a = dev(f.phi, torch.float32)
+    b = torch.empty_like(a)
+    dt = 0.1 * f.h / f.U
+    g.step(a, b, dt, f.h, f.U)
+    ref = b.clone()
+    s1, s2 = torch.empty_like(a), torch.empty_like(a)
+    ms = g.autotune(s1, s2, dt, f.h, f.U, reps=2)
+    assert ms > 0
+    cfg = g.get_launch()
+    assert 0 <= cfg["tile"] < cdi.FWD_TILES and cfg["nblocks"] > 0
+    g.step(a, b, dt, f.h, f.U)
+    assert torch.allclose(b, ref, atol=1e-6, rtol=0)
