@@ -240,9 +240,6 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
         for (int d = 0; d < 5; ++d) issue_phi(z0 - 2 + d, d);  // planes z0-2 .. z0+2
         issue_vel(z0, 0);
         cp_async_commit();
-        if (z0 + 3 <= z1 + 1) issue_phi(z0 + 3, 0);            // slot (5 mod 5)
-        if (z0 + 1 < z1) issue_vel(z0 + 1, 1);
-        cp_async_commit();
 
         const int own_x = x0 + tx * VX, own_y = y0 + ty;
         const bool writes = is_own && own_x < nx && own_y < ny;
@@ -254,7 +251,7 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
 #pragma unroll
             for (int i = 0; i < VX; ++i) wlo[i] = __ldg(src + i);
         }
-        cp_async_wait<1>();
+        cp_async_wait<0>();
         __syncthreads();
 
         // Prologue: s_z at plane z0-1 (own), s at plane z0 (own + ring), flux at z0-1/2.
@@ -282,6 +279,11 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
                 ssx[(z0 & 1) * C::SXS + rx_row * SXP + VX + rx_col] = sharp_cell(P0, Pm1, P1, rx_col, rx_row);
             }
         }
+        // Plane z0+3 reuses the slot of plane z0-2, which the prologue just read.
+        __syncthreads();
+        if (z0 + 3 <= z1 + 1) issue_phi(z0 + 3, 0);
+        if (z0 + 1 < z1) issue_vel(z0 + 1, 1);
+        cp_async_commit();
 
         int pk = 2;  // phi slot of plane k
         int vk = 0;  // velocity slot of plane k
