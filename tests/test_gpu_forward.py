@@ -79,8 +79,8 @@ def test_step_parity(dtype, shape, solenoidal):
     n = ref.size
     assert abs(st["sum"] - rs["sum"]) <= TOL[dtype] * n
     assert abs(st["min"] - rs["min"]) <= TOL[dtype] and abs(st["max"] - rs["max"]) <= TOL[dtype]
-    # FP64 sums directly; FP32 keeps compensated float partials (relative ~1e-10)
-    assert abs(st["sum"] - ours.sum()) <= (1e-12 * n if dtype == torch.float64 else 1e-9 * abs(ours.sum()))
+    # FP64 sums directly; FP32 keeps compensated float partials (Kahan bound ~1e-7 relative)
+    assert abs(st["sum"] - ours.sum()) <= (1e-12 * n if dtype == torch.float64 else 1e-7 * abs(ours.sum()))
     assert st["min"] == ours.min() and st["max"] == ours.max()
 
 
@@ -238,7 +238,7 @@ def test_every_launch_configuration(dtype, tile, shape, nchunks):
     ours = b.double().cpu().numpy()
     assert np.abs(ours - ref).max() <= TOL[dtype]
     assert st["min"] == ours.min() and st["max"] == ours.max()
-    assert abs(st["sum"] - ours.sum()) <= 1e-9 * abs(ours.sum())
+    assert abs(st["sum"] - ours.sum()) <= 1e-7 * abs(ours.sum())  # compensated FP32 partials
 
 
 def test_autotune_keeps_result():
