@@ -33,6 +33,14 @@ namespace cdi {
 __device__ __forceinline__ float rsqrt_t(float q) { return rsqrtf(q); }
 __device__ __forceinline__ double rsqrt_t(double q) { return rsqrt(q); }
 
+template <typename T> struct NumLim;
+template <> struct NumLim<float> {
+    __device__ __forceinline__ static float tiny() { return 1.17549435e-38f; }  // FLT_MIN
+};
+template <> struct NumLim<double> {
+    __device__ __forceinline__ static double tiny() { return 2.2250738585072014e-308; }  // DBL_MIN
+};
+
 template <typename T>
 __device__ __forceinline__ T flux(T cadv_u, T cdif, T cshp, T pl, T pr, T sl, T sr)
 {
@@ -158,8 +166,11 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
             const T g0 = (i + 1 < VX ? c[i + 1] : R) - (i > 0 ? c[i - 1] : L);
             const T g1 = yp[i] - yn[i];
             const T g2 = zp[i] - zn[i];
-            const T q = g0 * g0 + g1 * g1 + g2 * g2;
-            const T inv = q > T(0) ? rsqrt_t(q) : T(0);
+            // rsqrt of q + the smallest normal number: finite at g = 0, where
+            // s = wgt * g = 0 exactly; only cells with |g| below ~1e-18 (float)
+            // or ~1e-154 (double), whose s is negligible, see a perturbation.
+            const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, NumLim<T>::tiny())));
+            const T inv = rsqrt_t(q);
             const T wgt = c[i] * (T(1) - c[i]) * inv;
             s0[i] = wgt * g0;
             s1[i] = wgt * g1;
@@ -172,8 +183,8 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
         const T g0 = Pm[off + 1] - Pm[off - 1];
         const T g1 = Pm[off + PP] - Pm[off - PP];
         const T g2 = Pmp[off] - Pmm[off];
-        const T q = g0 * g0 + g1 * g1 + g2 * g2;
-        const T inv = q > T(0) ? rsqrt_t(q) : T(0);
+        const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, NumLim<T>::tiny())));
+        const T inv = rsqrt_t(q);
         return p * (T(1) - p) * inv * g0;  // s_x only
     };
 
@@ -316,9 +327,14 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
             } else if (is_xring) {
                 ssx[b1 * C::SXS + rx_row * SXP + VX + rx_col] = sharp_cell(Pk1, Pk, Pk2, rx_col, rx_row);
             }
-            __syncthreads();
+            // No barrier here: phase C reads only the s_x / s_y of plane k, which
+            // were written before S1, and the s_z of plane k+1 from registers.
+            // The next write of slot k&1 happens after the next S1.
 
-            // C: fluxes and update at plane k.
+            // C: fluxes and update at plane k.  Along x and y the four faces of a
+            // cell telescope to
+            //   c_adv [u_+(c + R) - u_-(L + c)] - c_dif (L + R - 2c) + c_shp (s_R - s_L)
+            // (the cell's own s_x, s_y cancel); the z face below is carried.
             if (is_own) {
                 const int b = k & 1;
                 const int po = (ty + 2) * PP + VX + tx * VX;
@@ -330,9 +346,8 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
                 const T L = Pk[po - 1], R = Pk[po + VX];
                 const T *sxr = ssx + b * C::SXS + ty * SXP + VX + tx * VX;
                 const T *syr = ssy + b * C::SYS + (ty + 1) * W + tx * VX;
-                T sxc[VX], syc[VX], syn[VX], syp[VX];
+                T sxc[VX], syn[VX], syp[VX];
                 VV::ld(sxc, sxr);
-                VV::ld(syc, syr);
                 VV::ld(syn, syr - W);
                 VV::ld(syp, syr + W);
                 const T sxL = sxr[-1], sxR = sxr[VX];
@@ -346,19 +361,21 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
                 VV::ld(vn, vr - W);
                 VV::ld(wc, wr);
                 const T uL = ur[-1];
-                T Fx[VX + 1];
-                Fx[0] = flux(c_adv * uL, c_dif, c_shp, L, c[0], sxL, sxc[0]);
-#pragma unroll
-                for (int i = 1; i < VX; ++i)
-                    Fx[i] = flux(c_adv * uc[i - 1], c_dif, c_shp, c[i - 1], c[i], sxc[i - 1], sxc[i]);
-                Fx[VX] = flux(c_adv * uc[VX - 1], c_dif, c_shp, c[VX - 1], R, sxc[VX - 1], sxR);
                 T o[VX];
 #pragma unroll
                 for (int i = 0; i < VX; ++i) {
-                    const T Fyp = flux(c_adv * vc[i], c_dif, c_shp, c[i], yp[i], syc[i], syp[i]);
-                    const T Fym = flux(c_adv * vn[i], c_dif, c_shp, yn[i], c[i], syn[i], syc[i]);
+                    const T xl = i > 0 ? c[i - 1] : L, xr = i + 1 < VX ? c[i + 1] : R;
+                    const T ul = i > 0 ? uc[i - 1] : uL;
+                    const T sl = i > 0 ? sxc[i - 1] : sxL, sr = i + 1 < VX ? sxc[i + 1] : sxR;
+                    T adv = uc[i] * (c[i] + xr);
+                    adv = fma(-ul, xl + c[i], adv);
+                    adv = fma(vc[i], c[i] + yp[i], adv);
+                    adv = fma(-vn[i], yn[i] + c[i], adv);
+                    const T dif = fma(T(-4), c[i], (xl + xr) + (yn[i] + yp[i]));
+                    const T shp = (sr - sl) + (syp[i] - syn[i]);
                     const T Fzp = flux(c_adv * wc[i], c_dif, c_shp, c[i], zp[i], szc[i], szn[i]);
-                    o[i] = c[i] - c_upd * ((Fx[i + 1] - Fx[i]) + (Fyp - Fym) + (Fzp - Fzm[i]));
+                    const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, Fzp - Fzm[i])));
+                    o[i] = fma(-c_upd, div, c[i]);
                     Fzm[i] = Fzp;
                     szc[i] = szn[i];
                 }

@@ -69,20 +69,26 @@ struct Acc<float> {
         ns += (p < 0.f) | (p > 1.f);
         nt += (p < -tol) | (p > 1.f + tol);
     }
-    // N values at once: compensated sum per value, min/max of the group, and
-    // the exact violation counts only when the group leaves [0, 1].
+    // N values at once: their pairwise sum is added with compensation (the
+    // uncompensated pairwise rounding is random and of relative size ~1e-9 on
+    // a whole field), min/max of the group, and the exact violation counts only
+    // when the group leaves [0, 1].
     template <int N>
     __device__ __forceinline__ void add_group(const float *o, float tol)
     {
         float gmn = o[0], gmx = o[0];
+        float g = o[0];
 #pragma unroll
-        for (int i = 0; i < N; ++i) {
-            const float y = o[i] - c;
+        for (int i = 1; i < N; ++i) {
+            g += o[i];
+            gmn = fminf(gmn, o[i]);
+            gmx = fmaxf(gmx, o[i]);
+        }
+        {
+            const float y = g - c;
             const float t = s + y;
             c = (t - s) - y;
             s = t;
-            gmn = fminf(gmn, o[i]);
-            gmx = fmaxf(gmx, o[i]);
         }
         mn = fminf(mn, gmn);
         mx = fmaxf(mx, gmx);
