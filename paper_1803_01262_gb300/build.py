@@ -22,6 +22,9 @@ OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libcdi.so")
 SOURCES = ["cdi_fwd.cu", "cdi_adj.cu", "cdi_batch.cu", "cdi_rk.cu", "cdi_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The forward step flushes FP32 denormals (values below 1.2e-38) to zero; this
+# removes denormal handling around rsqrtf and is far below every tolerance.
+PER_FILE = {"cdi_fwd.cu": ["-ftz=true"]}
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", INCLUDE, "-I", CSRC]
 
@@ -57,7 +60,7 @@ def build(force: bool = False, ptxas_verbose: bool = False, verbose: bool = Fals
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *PER_FILE.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         return src, obj, r
 

@@ -195,53 +195,62 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
         const Unit un = unit_of(u, ntiles, tiles_x, W, H, zc, nz);
         const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
 
-        // Global in-plane offsets of this thread's 16-byte copy chunks.
-        int gphi[C::RPHI], gu[C::RU], gv[C::RV], gw[C::RW];
+        // The 64 ring threads issue every 16-byte copy (they are idle while the
+        // own warps evaluate fluxes).  Global in-plane offsets of their chunks:
+        constexpr int NC = 64;
+        constexpr int RPHI = (C::CPHI + NC - 1) / NC, RU = (C::CU + NC - 1) / NC;
+        constexpr int RV = (C::CV + NC - 1) / NC, RW = (C::CW + NC - 1) / NC;
+        const int ct = tid - C::NOWN;
+        int gphi[RPHI], gu[RU], gv[RV], gw[RW];
+        if (!is_own) {
 #pragma unroll
-        for (int r = 0; r < C::RPHI; ++r) {
-            const int e = tid + r * C::NT, row = e / (PP / VX), col = e - row * (PP / VX);
-            gphi[r] = wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
-        }
+            for (int r = 0; r < RPHI; ++r) {
+                const int e = ct + r * NC, row = e / (PP / VX), col = e - row * (PP / VX);
+                gphi[r] = wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+            }
 #pragma unroll
-        for (int r = 0; r < C::RU; ++r) {
-            const int e = tid + r * C::NT, row = e / (UP / VX), col = e - row * (UP / VX);
-            gu[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
-        }
+            for (int r = 0; r < RU; ++r) {
+                const int e = ct + r * NC, row = e / (UP / VX), col = e - row * (UP / VX);
+                gu[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+            }
 #pragma unroll
-        for (int r = 0; r < C::RV; ++r) {
-            const int e = tid + r * C::NT, row = e / (W / VX), col = e - row * (W / VX);
-            gv[r] = wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx);
-        }
+            for (int r = 0; r < RV; ++r) {
+                const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
+                gv[r] = wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+            }
 #pragma unroll
-        for (int r = 0; r < C::RW; ++r) {
-            const int e = tid + r * C::NT, row = e / (W / VX), col = e - row * (W / VX);
-            gw[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+            for (int r = 0; r < RW; ++r) {
+                const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
+                gw[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+            }
         }
         auto issue_phi = [&](int z, int slot) {
+            if (is_own) return;
             const T *src = a.phi + (long long)wrapi(z, nz) * plane;
             T *dst = sphi + slot * C::PHI;
 #pragma unroll
-            for (int r = 0; r < C::RPHI; ++r) {
-                const int e = tid + r * C::NT;
+            for (int r = 0; r < RPHI; ++r) {
+                const int e = ct + r * NC;
                 if (e < C::CPHI) cp_async<16>(dst + e * VX, src + gphi[r]);
             }
         };
         auto issue_vel = [&](int z, int slot) {
+            if (is_own) return;
             const long long zo = (long long)z * plane;
             T *dst = svel + slot * C::VEL;
 #pragma unroll
-            for (int r = 0; r < C::RU; ++r) {
-                const int e = tid + r * C::NT;
+            for (int r = 0; r < RU; ++r) {
+                const int e = ct + r * NC;
                 if (e < C::CU) cp_async<16>(dst + e * VX, a.u + zo + gu[r]);
             }
 #pragma unroll
-            for (int r = 0; r < C::RV; ++r) {
-                const int e = tid + r * C::NT;
+            for (int r = 0; r < RV; ++r) {
+                const int e = ct + r * NC;
                 if (e < C::CV) cp_async<16>(dst + C::USZ + e * VX, a.v + zo + gv[r]);
             }
 #pragma unroll
-            for (int r = 0; r < C::RW; ++r) {
-                const int e = tid + r * C::NT;
+            for (int r = 0; r < RW; ++r) {
+                const int e = ct + r * NC;
                 if (e < C::CW) cp_async<16>(dst + C::USZ + C::VSZ + e * VX, a.w + zo + gw[r]);
             }
         };
