@@ -212,6 +212,39 @@ CDI_API int cdi_get_launch(const cdi_grid *g, int which, int *tile, int *nblocks
 CDI_API int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps,
                          double gamma, int reps, double *best_ms, void *stream);
 
+/*
+ * One forward step that allocates nothing (the paper has no counterpart: this
+ * is an interface for callers that may not allocate device memory).
+ *
+ * Some callers cannot call cudaMalloc: code running inside a stream callback
+ * or an allocator hook, a framework that fixes its memory pool up front, or a
+ * latency-critical loop that must never enter the driver's allocator.  The
+ * grid API allocates its reduction scratch in cdi_create_grid; this call
+ * takes no grid.  Its scratch is a fixed device array inside the library
+ * (CDI_NOALLOC_MAX_BLOCKS partials of 40 bytes plus a counter, about 320 KB),
+ * held by every GPU that loads the library until the process exits.
+ *
+ * Arguments are those of cdi_create_grid + cdi_set_velocity + cdi_step:
+ * extents, spacing, dtype, device phi_in / phi_out (not overlapping), face
+ * velocities (v may be NULL only when ny == nz == 1, w only when nz == 1),
+ * dt, eps, gamma, vel_scale.  stats_dev is a caller-owned DEVICE buffer of
+ * sizeof(cdi_stats) bytes; the step writes mass, sum, min, max, n_strict and
+ * n_tol of phi_out into it (the *_run fields are left untouched).  No
+ * condition check is made.  Returns CDI_ERR_DIM if the launch would need more
+ * blocks than the fixed scratch holds (not reachable on a 152-SM GB300).
+ *
+ * The first call on a device, made with that device current, looks up the
+ * scratch's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  Every call shares the one scratch array, which
+ * keeps the last call's contents: calls that overlap on the GPU race on it.
+ * Each call clears the block counter on its stream before its launch.
+ */
+#define CDI_NOALLOC_MAX_BLOCKS 8192
+CDI_API int cdi_step_noalloc(int nx, int ny, int nz, double dx, int dtype, const void *phi_in,
+                             void *phi_out, const void *u, const void *v, const void *w,
+                             double dt, double eps, double gamma, double vel_scale,
+                             void *stats_dev, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 CDI_API const char *cdi_last_error_string(void);
 

@@ -74,6 +74,7 @@ SIGNATURES = {
     "cdi_set_launch": [_V, _I, _I, _I, _I],
     "cdi_get_launch": [_V, _I, _P(_I), _P(_I), _P(_I)],
     "cdi_autotune": [_V, _V, _V, _Dbl, _Dbl, _Dbl, _I, _P(_Dbl), _V],
+    "cdi_step_noalloc": [_I, _I, _I, _Dbl, _I, _V, _V, _V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _V, _V],
 }
 _RESTYPE = {"cdi_last_error_string": ctypes.c_char_p}
 
@@ -132,6 +133,33 @@ def max_dt(dx, eps, gamma, Df, scheme=CDI_EULER):
     out = ctypes.c_double()
     _ck(lib().cdi_max_dt(dx, eps, gamma, Df, scheme, ctypes.byref(out)))
     return out.value
+
+
+def step_noalloc(phi_in, phi_out, u, v, w, dx, dt, eps, gamma, vel_scale, stats_dev, stream=None):
+    """One forward step through cdi_step_noalloc (no device allocation by the library).
+
+    For callers that cannot allocate device memory at step time.  All
+    arguments are preallocated CUDA tensors; ``stats_dev`` is a device tensor
+    of at least ``ctypes.sizeof(Stats)`` bytes that receives the statistics.
+    Returns nothing; read ``stats_dev`` with :func:`stats_from_device`.
+    """
+    nz, ny, nx = phi_in.shape
+    code = _dtype_code(phi_in.dtype)
+    for t in (phi_in, phi_out, u, v, w):
+        if t is not None and (not t.is_cuda or not t.is_contiguous() or t.dtype != phi_in.dtype
+                              or tuple(t.shape) != (nz, ny, nx)):
+            raise ValueError("arrays must be contiguous CUDA tensors of one dtype and shape")
+    if stats_dev.numel() * stats_dev.element_size() < ctypes.sizeof(Stats):
+        raise ValueError("stats_dev is too small")
+    p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+    _ck(lib().cdi_step_noalloc(nx, ny, nz, float(dx), code, p(phi_in), p(phi_out), p(u), p(v), p(w),
+                               dt, eps, gamma, vel_scale, p(stats_dev), _stream(stream)))
+
+
+def stats_from_device(stats_dev):
+    """Decode a cdi_stats record held in a device tensor (synchronises)."""
+    raw = bytes(stats_dev.view(torch.uint8)[:ctypes.sizeof(Stats)].cpu().numpy())
+    return Stats.from_buffer_copy(raw).as_dict()
 
 
 class Grid:

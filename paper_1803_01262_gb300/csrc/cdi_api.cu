@@ -38,6 +38,15 @@ constexpr int kMaxBlocksPerSM = 32;
 
 }  // namespace
 
+int cdi::set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
 struct cdi_grid {
     int nx, ny, nz;
     double dx;

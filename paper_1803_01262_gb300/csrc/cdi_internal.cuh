@@ -106,6 +106,9 @@ cudaError_t launch_adj(const AdjArgs<T> &a, int tile, cudaStream_t s);
 int adj_num_tiles();
 int adj_blocks(int tile, int zchunk, int nx, int ny, int nz);
 
+// Record a message for cdi_last_error_string() and return code (cdi_api.cu).
+int set_error(int code, const char *fmt, ...);
+
 __host__ __device__ inline int wrapi(int a, int n)
 {
     int r = a % n;
