@@ -188,6 +188,46 @@ CDI_API int cdi_check_condition(double eps_over_dx, double gamma_over_U, double 
  * gamma eps) (Eq. 27), RK4 2.79 dx^2/(4 D_f gamma eps) (Eq. 28). */
 CDI_API int cdi_max_dt(double dx, double eps, double gamma, int Df, int scheme, double *dt);
 
+/*
+ * Batched boxes.  Many independent periodic boxes of uneven sizes, each with
+ * its own spacing, eps, gamma, dt and face velocities, advance together: one
+ * kernel launch per step covers every box (a persistent grid taking work
+ * units -- a tile of one box and a chunk of its planes -- from one list), and
+ * cdi_batch_run replays a captured CUDA graph of nsteps such launches.  Each
+ * box evolves exactly as with cdi_step on its own grid.  Arrays follow the
+ * conventions above and are borrowed for the batch's lifetime.
+ */
+typedef struct cdi_box_desc {
+    int nx, ny, nz;
+    double dx, dt, eps, gamma;
+    const void *u, *v, *w;  /* face velocities (v, w NULL as for cdi_set_velocity) */
+    void *phi_a, *phi_b;    /* ping-pong phase fields; the state starts in phi_a */
+} cdi_box_desc;
+
+typedef struct cdi_batch cdi_batch;
+
+/* Build the device box table and work list (allocates). */
+CDI_API int cdi_batch_create(cdi_batch **b, const cdi_box_desc *boxes, int nbox, int dtype);
+CDI_API int cdi_batch_destroy(cdi_batch *b);
+
+/* Which buffer holds the current state (*parity: 0 = phi_a, 1 = phi_b), the
+ * number of work units and blocks per launch, and the total cell count. */
+CDI_API int cdi_batch_info(const cdi_batch *b, int *parity, int *total_units, int *nblocks,
+                           long long *cells);
+
+/* One step of every box with face velocity vel_scale * (u, v, w); flips the
+ * parity.  Per-box statistics of the result are written to the device. */
+CDI_API int cdi_batch_step(cdi_batch *b, double vel_scale, void *stream);
+
+/* nsteps steps (vel_scale = 1) as one CUDA graph launch; the graph is
+ * captured on first use for each (nsteps, parity) and replayed after. */
+CDI_API int cdi_batch_run(cdi_batch *b, int nsteps, void *stream);
+
+/* Copy the nbox statistics records (last step + run accumulators) to out[];
+ * synchronises.  CDI_ERR_NAN if a box's sum is not finite. */
+CDI_API int cdi_batch_stats(cdi_batch *b, cdi_stats *out, void *stream);
+CDI_API int cdi_batch_reset_run_stats(cdi_batch *b, void *stream);
+
 /* Kernels with a tunable launch configuration. */
 enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
 

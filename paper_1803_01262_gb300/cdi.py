@@ -75,6 +75,13 @@ SIGNATURES = {
     "cdi_get_launch": [_V, _I, _P(_I), _P(_I), _P(_I)],
     "cdi_autotune": [_V, _V, _V, _Dbl, _Dbl, _Dbl, _I, _P(_Dbl), _V],
     "cdi_step_noalloc": [_I, _I, _I, _Dbl, _I, _V, _V, _V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _V, _V],
+    "cdi_batch_create": [_P(_V), _V, _I, _I],
+    "cdi_batch_destroy": [_V],
+    "cdi_batch_info": [_V, _P(_I), _P(_I), _P(_I), _P(ctypes.c_longlong)],
+    "cdi_batch_step": [_V, _Dbl, _V],
+    "cdi_batch_run": [_V, _I, _V],
+    "cdi_batch_stats": [_V, _V, _V],
+    "cdi_batch_reset_run_stats": [_V, _V],
 }
 _RESTYPE = {"cdi_last_error_string": ctypes.c_char_p}
 
@@ -279,3 +286,78 @@ class Grid:
                                    self._arr(g[2], "gw"), dt, eps, gamma, vel_scale,
                                    _stream(stream)))
         return lam_k
+
+
+class BoxDesc(ctypes.Structure):
+    """Mirror of cdi_box_desc."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("eps", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("u", ctypes.c_void_p), ("v", ctypes.c_void_p),
+                ("w", ctypes.c_void_p), ("phi_a", ctypes.c_void_p), ("phi_b", ctypes.c_void_p)]
+
+
+class Batch:
+    """Independent periodic boxes advanced by one launch per step (cdi_batch_*).
+
+    ``boxes`` is a list of dicts with keys dx, dt, eps, gamma, u, v, w, phi_a,
+    phi_b (CUDA tensors shaped (nz, ny, nx), one dtype for all boxes).  The
+    state starts in phi_a; :meth:`current` returns the tensor holding it.
+    """
+
+    def __init__(self, boxes):
+        if not boxes:
+            raise ValueError("empty batch")
+        self.dtype = boxes[0]["phi_a"].dtype
+        descs = (BoxDesc * len(boxes))()
+        keep = []
+        for i, b in enumerate(boxes):
+            nz, ny, nx = b["phi_a"].shape
+            for k in ("u", "v", "w", "phi_a", "phi_b"):
+                t = b[k]
+                if (not t.is_cuda or t.dtype != self.dtype or not t.is_contiguous()
+                        or tuple(t.shape) != (nz, ny, nx)):
+                    raise ValueError(f"box {i}: {k} must be a contiguous CUDA tensor of the box shape")
+                keep.append(t)
+            descs[i] = BoxDesc(nx, ny, nz, float(b["dx"]), float(b["dt"]), float(b["eps"]),
+                               float(b["gamma"]), b["u"].data_ptr(), b["v"].data_ptr(),
+                               b["w"].data_ptr(), b["phi_a"].data_ptr(), b["phi_b"].data_ptr())
+        self._keep = keep
+        self.boxes = boxes
+        self._h = ctypes.c_void_p()
+        _ck(lib().cdi_batch_create(ctypes.byref(self._h), ctypes.cast(descs, ctypes.c_void_p),
+                                   len(boxes), _dtype_code(self.dtype)))
+
+    def close(self):
+        if self._h:
+            lib().cdi_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        p, u, n, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+        _ck(lib().cdi_batch_info(self._h, ctypes.byref(p), ctypes.byref(u), ctypes.byref(n),
+                                 ctypes.byref(c)))
+        return dict(parity=p.value, units=u.value, nblocks=n.value, cells=c.value)
+
+    def current(self, i):
+        return self.boxes[i]["phi_b" if self.info()["parity"] else "phi_a"]
+
+    def step(self, vel_scale=1.0, stream=None):
+        _ck(lib().cdi_batch_step(self._h, vel_scale, _stream(stream)))
+
+    def run(self, nsteps, stream=None):
+        """nsteps steps as one replay of a captured CUDA graph."""
+        _ck(lib().cdi_batch_run(self._h, nsteps, _stream(stream)))
+
+    def stats(self, stream=None):
+        out = (Stats * len(self.boxes))()
+        _ck(lib().cdi_batch_stats(self._h, ctypes.cast(out, ctypes.c_void_p), _stream(stream)))
+        return [s.as_dict() for s in out]
+
+    def reset_run_stats(self, stream=None):
+        _ck(lib().cdi_batch_reset_run_stats(self._h, _stream(stream)))

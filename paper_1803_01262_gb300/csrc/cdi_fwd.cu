@@ -27,67 +27,10 @@
 #include "cdi_internal.cuh"
 #include "cdi_reduce.cuh"
 #include "cdi_async.cuh"
+#include "cdi_fwd_common.cuh"
+#include "cdi_fwd_scalar.cuh"
 
 namespace cdi {
-
-__device__ __forceinline__ float rsqrt_t(float q) { return rsqrtf(q); }
-__device__ __forceinline__ double rsqrt_t(double q) { return rsqrt(q); }
-
-template <typename T> struct NumLim;
-template <> struct NumLim<float> {
-    __device__ __forceinline__ static float tiny() { return 1.17549435e-38f; }  // FLT_MIN
-};
-template <> struct NumLim<double> {
-    __device__ __forceinline__ static double tiny() { return 2.2250738585072014e-308; }  // DBL_MIN
-};
-
-template <typename T>
-__device__ __forceinline__ T flux(T cadv_u, T cdif, T cshp, T pl, T pr, T sl, T sr)
-{
-    return cadv_u * (pl + pr) - cdif * (pr - pl) + cshp * (sl + sr);
-}
-
-// 16-byte vector of T.
-template <typename T> struct V16;
-template <> struct V16<float> {
-    static constexpr int N = 4;
-    __device__ __forceinline__ static void ld(float *d, const float *s)
-    {
-        const float4 v = *reinterpret_cast<const float4 *>(s);
-        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
-    }
-    __device__ __forceinline__ static void st(float *d, const float *s)
-    {
-        *reinterpret_cast<float4 *>(d) = make_float4(s[0], s[1], s[2], s[3]);
-    }
-};
-template <> struct V16<double> {
-    static constexpr int N = 2;
-    __device__ __forceinline__ static void ld(double *d, const double *s)
-    {
-        const double2 v = *reinterpret_cast<const double2 *>(s);
-        d[0] = v.x; d[1] = v.y;
-    }
-    __device__ __forceinline__ static void st(double *d, const double *s)
-    {
-        *reinterpret_cast<double2 *>(d) = make_double2(s[0], s[1]);
-    }
-};
-
-// Work unit u -> (tile origin, z range).
-struct Unit {
-    int x0, y0, z0, z1;
-};
-__device__ __forceinline__ Unit unit_of(int u, int ntiles, int tiles_x, int bw, int bh, int zc, int nz)
-{
-    Unit r;
-    const int chunk = u / ntiles, tile = u - chunk * ntiles;
-    r.x0 = (tile % tiles_x) * bw;
-    r.y0 = (tile / tiles_x) * bh;
-    r.z0 = chunk * zc;
-    r.z1 = min(nz, r.z0 + zc);
-    return r;
-}
 
 // ===========================================================================
 // Vector kernel
@@ -402,180 +345,22 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
 }
 
 // ===========================================================================
-// Scalar kernel (any extents)
-
-constexpr int PF_DIST = 2;  // phi plane k+2+PF_DIST is in flight while plane k is updated
-constexpr int NSLOT = 8;    // power of two >= PF_DIST + 3 live planes
-
-template <typename T, int BX, int BY>
-struct FwdSmem {
-    static constexpr int PX = BX + 4, PY = BY + 4;
-    static constexpr size_t bytes =
-        sizeof(T) * (NSLOT * PY * PX + 2 * BY * (BX + 2) + 2 * (BY + 2) * BX);
-};
+// Scalar kernel (any extents): the per-unit body is in cdi_fwd_scalar.cuh.
 
 template <typename T, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY)
 fwd_kernel(const FwdArgs<T> a, const int nchunks)
 {
-    constexpr int PX = BX + 4, PY = BY + 4, PLANE = PX * PY;
-    constexpr int NT = BX * BY;
-    constexpr int NLOAD = (PLANE + NT - 1) / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*sp)[PY][PX] = reinterpret_cast<T(*)[PY][PX]>(smem_raw);           // phi ring [NSLOT]
-    T(*sx)[BY][BX + 2] = reinterpret_cast<T(*)[BY][BX + 2]>(sp + NSLOT);  // s_x, x = -1..BX [2]
-    T(*sy)[BY + 2][BX] = reinterpret_cast<T(*)[BY + 2][BX]>(sx + 2);      // s_y, y = -1..BY [2]
-
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long plane = (long long)nx * ny;
-    const int tiles_x = (nx + BX - 1) / BX;
-    const int ntiles = tiles_x * ((ny + BY - 1) / BY);
-    const int zc = (nz + nchunks - 1) / nchunks;
-    const int units = ntiles * ((nz + zc - 1) / zc);
-
-    // Ring cells: threads [0, 2BX) the y-ring, [2BX, 2BX + 2BY) the x-ring.
-    int rkind = 0, rx = 0, ry = 0;
-    if (tid < 2 * BX) {
-        rkind = 1;
-        rx = tid % BX;
-        ry = tid < BX ? -1 : BY;
-    } else if (tid < 2 * BX + 2 * BY) {
-        rkind = 2;
-        const int r = tid - 2 * BX;
-        ry = r % BY;
-        rx = r < BY ? -1 : BX;
-    }
-    const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_shp = a.c.c_shp, c_upd = a.c.c_upd;
-
-    auto sharp = [&](int z, int lx, int ly, T &s0, T &s1, T &s2) {
-        const int X = lx + 2, Y = ly + 2;
-        const int m = z & (NSLOT - 1), mm = (z - 1) & (NSLOT - 1), mp = (z + 1) & (NSLOT - 1);
-        const T p = sp[m][Y][X];
-        const T g0 = sp[m][Y][X + 1] - sp[m][Y][X - 1];
-        const T g1 = sp[m][Y + 1][X] - sp[m][Y - 1][X];
-        const T g2 = sp[mp][Y][X] - sp[mm][Y][X];
-        const T q = g0 * g0 + g1 * g1 + g2 * g2;
-        const T inv = q > T(0) ? rsqrt_t(q) : T(0);
-        const T wgt = p * (T(1) - p) * inv;
-        s0 = wgt * g0;
-        s1 = wgt * g1;
-        s2 = wgt * g2;
-    };
-    auto sharp_plane = [&](int z, T &szc) {
-        T q0, q1;
-        sharp(z, tx, ty, q0, q1, szc);
-        sx[z & 1][ty][tx + 1] = q0;
-        sy[z & 1][ty + 1][tx] = q1;
-        if (rkind) {
-            T r0, r1, r2;
-            sharp(z, rx, ry, r0, r1, r2);
-            if (rkind == 1) sy[z & 1][ry + 1][rx] = r1;
-            else sx[z & 1][ry][rx + 1] = r0;
-        }
-    };
-
+    const int tiles_x = (a.nx + BX - 1) / BX;
+    const int ntiles = tiles_x * ((a.ny + BY - 1) / BY);
+    const int zc = (a.nz + nchunks - 1) / nchunks;
+    const int units = ntiles * ((a.nz + zc - 1) / zc);
     Acc<T> acc;
     acc.init();
-
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        const Unit un = unit_of(u, ntiles, tiles_x, BX, BY, zc, nz);
-        const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
-
-        int loff[NLOAD];
-#pragma unroll
-        for (int r = 0; r < NLOAD; ++r) {
-            const int e = tid + r * NT;
-            const int ey = e / PX, ex = e - ey * PX;
-            loff[r] = (e < PLANE) ? wrapi(y0 + ey - 2, ny) * nx + wrapi(x0 + ex - 2, nx) : 0;
-        }
-        const int gx = wrapi(x0 + tx, nx), gy = wrapi(y0 + ty, ny);
-        const bool own = (x0 + tx < nx) && (y0 + ty < ny);
-        const int oc = gy * nx + gx;
-        const int oxm = gy * nx + wrapi(gx - 1, nx);
-        const int oym = wrapi(gy - 1, ny) * nx + gx;
-
-        auto issue_plane = [&](int z) {
-            const T *src = a.phi + (long long)wrapi(z, nz) * plane;
-            T *dst = &sp[z & (NSLOT - 1)][0][0];
-#pragma unroll
-            for (int r = 0; r < NLOAD; ++r) {
-                const int e = tid + r * NT;
-                if (e < PLANE) cp_async<sizeof(T)>(dst + e, src + loff[r]);
-            }
-        };
-
-        __syncthreads();  // the previous unit's readers are done with the ring
-        issue_plane(z0 - 2);
-        issue_plane(z0 - 1);
-        issue_plane(z0);
-        issue_plane(z0 + 1);
-        cp_async_commit();
-#pragma unroll
-        for (int d = 0; d < PF_DIST; ++d) {
-            if (z0 + 2 + d <= z1 + 1) issue_plane(z0 + 2 + d);
-            cp_async_commit();
-        }
-        T uc, um, vc, vm, wc;
-        {
-            const long long zb = (long long)z0 * plane;
-            uc = __ldg(a.u + zb + oc); um = __ldg(a.u + zb + oxm);
-            vc = __ldg(a.v + zb + oc); vm = __ldg(a.v + zb + oym);
-            wc = __ldg(a.w + zb + oc);
-        }
-        const T wlo = __ldg(a.w + (long long)wrapi(z0 - 1, nz) * plane + oc);
-        cp_async_wait<PF_DIST>();
-        __syncthreads();
-        T szm, szc;
-        {
-            T d0, d1;
-            sharp(z0 - 1, tx, ty, d0, d1, szm);
-        }
-        sharp_plane(z0, szc);
-        T Fzm;
-        {
-            const T pm = sp[(z0 - 1) & (NSLOT - 1)][ty + 2][tx + 2];
-            const T pc = sp[z0 & (NSLOT - 1)][ty + 2][tx + 2];
-            Fzm = flux(c_adv * wlo, c_dif, c_shp, pm, pc, szm, szc);
-        }
-
-        for (int k = z0; k < z1; ++k) {
-            cp_async_wait<PF_DIST - 1>();
-            __syncthreads();
-            if (k + 2 + PF_DIST <= z1 + 1) issue_plane(k + 2 + PF_DIST);
-            cp_async_commit();
-            T un_ = T(0), umn = T(0), vn = T(0), vmn = T(0), wn = T(0);
-            if (k + 1 < z1) {
-                const long long zb = (long long)(k + 1) * plane;
-                un_ = __ldg(a.u + zb + oc); umn = __ldg(a.u + zb + oxm);
-                vn = __ldg(a.v + zb + oc); vmn = __ldg(a.v + zb + oym);
-                wn = __ldg(a.w + zb + oc);
-            }
-            T szn;
-            sharp_plane(k + 1, szn);
-            __syncthreads();
-            const int m = k & (NSLOT - 1), b = k & 1;
-            const T pc = sp[m][ty + 2][tx + 2];
-            const T pxm = sp[m][ty + 2][tx + 1], pxp = sp[m][ty + 2][tx + 3];
-            const T pym = sp[m][ty + 1][tx + 2], pyp = sp[m][ty + 3][tx + 2];
-            const T pzp = sp[(k + 1) & (NSLOT - 1)][ty + 2][tx + 2];
-            const T sxc = sx[b][ty][tx + 1], sxm = sx[b][ty][tx], sxp = sx[b][ty][tx + 2];
-            const T syc = sy[b][ty + 1][tx], sym = sy[b][ty][tx], syp = sy[b][ty + 2][tx];
-            const T Fxp = flux(c_adv * uc, c_dif, c_shp, pc, pxp, sxc, sxp);
-            const T Fxm = flux(c_adv * um, c_dif, c_shp, pxm, pc, sxm, sxc);
-            const T Fyp = flux(c_adv * vc, c_dif, c_shp, pc, pyp, syc, syp);
-            const T Fym = flux(c_adv * vm, c_dif, c_shp, pym, pc, sym, syc);
-            const T Fzp = flux(c_adv * wc, c_dif, c_shp, pc, pzp, szc, szn);
-            const T o = pc - c_upd * ((Fxp - Fxm) + (Fyp - Fym) + (Fzp - Fzm));
-            if (own) {
-                a.out[(long long)k * plane + oc] = o;
-                acc.add(o, a.c.tol);
-            }
-            Fzm = Fzp;
-            szc = szn;
-            uc = un_; um = umn; vc = vn; vm = vmn; wc = wn;
-        }
-        cp_async_wait<0>();
+        const Unit un = unit_of(u, ntiles, tiles_x, BX, BY, zc, a.nz);
+        scalar_unit<T, BX, BY>(a, un, acc, smem_raw);
     }
     reduce_and_finish(acc.partial(), a.red);
 }

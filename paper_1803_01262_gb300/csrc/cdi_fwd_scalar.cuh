@@ -1,0 +1,192 @@
+// Per-unit body of the one-cell-per-thread CDI step (any extents), shared by
+// the single-box forward kernel and the batched kernel.
+//
+// A unit is a BX x BY tile of one box and a range of planes [z0, z1).  The
+// block stages phi planes with a halo of 2 in x and y by element-wise
+// cp.async into an 8-slot shared ring, PF_DIST planes ahead of use; computes
+// the sharpening vector s = phi (1 - phi) g/|g| of plane k+1 for its cells
+// and a one-cell ring (s_x on the x-ring, s_y on the y-ring); and updates
+// plane k from its six face fluxes
+//   F = c_adv u_f (phi_L + phi_R) - c_dif (phi_R - phi_L) + c_shp (s_L + s_R)
+// with the face below carried in a register.  Velocities are prefetched into
+// registers one plane ahead.  Outputs go to the caller's accumulator.
+#pragma once
+
+#include "cdi_async.cuh"
+#include "cdi_fwd_common.cuh"
+#include "cdi_reduce.cuh"
+
+namespace cdi {
+
+constexpr int PF_DIST = 2;  // phi plane k+2+PF_DIST is in flight while plane k is updated
+constexpr int NSLOT = 8;    // power of two >= PF_DIST + 3 live planes
+
+template <typename T, int BX, int BY>
+struct FwdSmem {
+    static constexpr int PX = BX + 4, PY = BY + 4;
+    static constexpr size_t bytes =
+        sizeof(T) * (NSLOT * PY * PX + 2 * BY * (BX + 2) + 2 * (BY + 2) * BX);
+};
+
+// Must be called by every thread of a (BX, BY) block with the same unit.
+template <typename T, int BX, int BY>
+__device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un, Acc<T> &acc,
+                                            unsigned char *smem_raw)
+{
+    constexpr int PX = BX + 4, PY = BY + 4, PLANE = PX * PY;
+    constexpr int NT = BX * BY;
+    constexpr int NLOAD = (PLANE + NT - 1) / NT;
+    T(*sp)[PY][PX] = reinterpret_cast<T(*)[PY][PX]>(smem_raw);           // phi ring [NSLOT]
+    T(*sx)[BY][BX + 2] = reinterpret_cast<T(*)[BY][BX + 2]>(sp + NSLOT);  // s_x, x = -1..BX [2]
+    T(*sy)[BY + 2][BX] = reinterpret_cast<T(*)[BY + 2][BX]>(sx + 2);      // s_y, y = -1..BY [2]
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long plane = (long long)nx * ny;
+    const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
+
+    // Ring cells: threads [0, 2BX) the y-ring, [2BX, 2BX + 2BY) the x-ring.
+    int rkind = 0, rx = 0, ry = 0;
+    if (tid < 2 * BX) {
+        rkind = 1;
+        rx = tid % BX;
+        ry = tid < BX ? -1 : BY;
+    } else if (tid < 2 * BX + 2 * BY) {
+        rkind = 2;
+        const int r = tid - 2 * BX;
+        ry = r % BY;
+        rx = r < BY ? -1 : BX;
+    }
+    const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_shp = a.c.c_shp, c_upd = a.c.c_upd;
+
+    auto sharp = [&](int z, int lx, int ly, T &s0, T &s1, T &s2) {
+        const int X = lx + 2, Y = ly + 2;
+        const int m = z & (NSLOT - 1), mm = (z - 1) & (NSLOT - 1), mp = (z + 1) & (NSLOT - 1);
+        const T p = sp[m][Y][X];
+        const T g0 = sp[m][Y][X + 1] - sp[m][Y][X - 1];
+        const T g1 = sp[m][Y + 1][X] - sp[m][Y - 1][X];
+        const T g2 = sp[mp][Y][X] - sp[mm][Y][X];
+        const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, NumLim<T>::tiny())));
+        const T inv = rsqrt_t(q);
+        const T wgt = p * (T(1) - p) * inv;
+        s0 = wgt * g0;
+        s1 = wgt * g1;
+        s2 = wgt * g2;
+    };
+    auto sharp_plane = [&](int z, T &szc) {
+        T q0, q1;
+        sharp(z, tx, ty, q0, q1, szc);
+        sx[z & 1][ty][tx + 1] = q0;
+        sy[z & 1][ty + 1][tx] = q1;
+        if (rkind) {
+            T r0, r1, r2;
+            sharp(z, rx, ry, r0, r1, r2);
+            if (rkind == 1) sy[z & 1][ry + 1][rx] = r1;
+            else sx[z & 1][ry][rx + 1] = r0;
+        }
+    };
+
+    int loff[NLOAD];
+#pragma unroll
+    for (int r = 0; r < NLOAD; ++r) {
+        const int e = tid + r * NT;
+        const int ey = e / PX, ex = e - ey * PX;
+        loff[r] = (e < PLANE) ? wrapi(y0 + ey - 2, ny) * nx + wrapi(x0 + ex - 2, nx) : 0;
+    }
+    const int gx = wrapi(x0 + tx, nx), gy = wrapi(y0 + ty, ny);
+    const bool own = (x0 + tx < nx) && (y0 + ty < ny);
+    const int oc = gy * nx + gx;
+    const int oxm = gy * nx + wrapi(gx - 1, nx);
+    const int oym = wrapi(gy - 1, ny) * nx + gx;
+
+    auto issue_plane = [&](int z) {
+        const T *src = a.phi + (long long)wrapi(z, nz) * plane;
+        T *dst = &sp[z & (NSLOT - 1)][0][0];
+#pragma unroll
+        for (int r = 0; r < NLOAD; ++r) {
+            const int e = tid + r * NT;
+            if (e < PLANE) cp_async<sizeof(T)>(dst + e, src + loff[r]);
+        }
+    };
+
+    __syncthreads();  // the previous unit's readers are done with the ring
+    issue_plane(z0 - 2);
+    issue_plane(z0 - 1);
+    issue_plane(z0);
+    issue_plane(z0 + 1);
+    cp_async_commit();
+#pragma unroll
+    for (int d = 0; d < PF_DIST; ++d) {
+        if (z0 + 2 + d <= z1 + 1) issue_plane(z0 + 2 + d);
+        cp_async_commit();
+    }
+    T uc, um, vc, vm, wc;
+    {
+        const long long zb = (long long)z0 * plane;
+        uc = __ldg(a.u + zb + oc); um = __ldg(a.u + zb + oxm);
+        vc = __ldg(a.v + zb + oc); vm = __ldg(a.v + zb + oym);
+        wc = __ldg(a.w + zb + oc);
+    }
+    const T wlo = __ldg(a.w + (long long)wrapi(z0 - 1, nz) * plane + oc);
+    cp_async_wait<PF_DIST>();
+    __syncthreads();
+    T szm, szc;
+    {
+        T d0, d1;
+        sharp(z0 - 1, tx, ty, d0, d1, szm);
+    }
+    sharp_plane(z0, szc);
+    T Fzm;
+    {
+        const T pm = sp[(z0 - 1) & (NSLOT - 1)][ty + 2][tx + 2];
+        const T pc = sp[z0 & (NSLOT - 1)][ty + 2][tx + 2];
+        Fzm = flux(c_adv * wlo, c_dif, c_shp, pm, pc, szm, szc);
+    }
+
+    for (int k = z0; k < z1; ++k) {
+        // S1: plane k+2 has landed and every thread has left iteration k-1.
+        cp_async_wait<PF_DIST - 1>();
+        __syncthreads();
+        if (k + 2 + PF_DIST <= z1 + 1) issue_plane(k + 2 + PF_DIST);
+        cp_async_commit();
+        T un_ = T(0), umn = T(0), vn = T(0), vmn = T(0), wn = T(0);
+        if (k + 1 < z1) {
+            const long long zb = (long long)(k + 1) * plane;
+            un_ = __ldg(a.u + zb + oc); umn = __ldg(a.u + zb + oxm);
+            vn = __ldg(a.v + zb + oc); vmn = __ldg(a.v + zb + oym);
+            wn = __ldg(a.w + zb + oc);
+        }
+        // B: sharpening at plane k+1 (slot (k+1)&1; phase C reads slot k&1, which
+        // was written before S1, so no barrier separates B from C).
+        T szn;
+        sharp_plane(k + 1, szn);
+        // C: fluxes and update at plane k.
+        const int m = k & (NSLOT - 1), b = k & 1;
+        const T pc = sp[m][ty + 2][tx + 2];
+        const T pxm = sp[m][ty + 2][tx + 1], pxp = sp[m][ty + 2][tx + 3];
+        const T pym = sp[m][ty + 1][tx + 2], pyp = sp[m][ty + 3][tx + 2];
+        const T pzp = sp[(k + 1) & (NSLOT - 1)][ty + 2][tx + 2];
+        const T sxm = sx[b][ty][tx], sxp = sx[b][ty][tx + 2];
+        const T sym = sy[b][ty][tx], syp = sy[b][ty + 2][tx];
+        // x and y faces telescoped; the cell's own s_x, s_y cancel.
+        T adv = uc * (pc + pxp);
+        adv = fma(-um, pxm + pc, adv);
+        adv = fma(vc, pc + pyp, adv);
+        adv = fma(-vm, pym + pc, adv);
+        const T dif = fma(T(-4), pc, (pxm + pxp) + (pym + pyp));
+        const T shp = (sxp - sxm) + (syp - sym);
+        const T Fzp = flux(c_adv * wc, c_dif, c_shp, pc, pzp, szc, szn);
+        const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, Fzp - Fzm)));
+        const T o = fma(-c_upd, div, pc);
+        if (own) {
+            a.out[(long long)k * plane + oc] = o;
+            acc.add(o, a.c.tol);
+        }
+        Fzm = Fzp;
+        szc = szn;
+        uc = un_; um = umn; vc = vn; vm = vmn; wc = wn;
+    }
+    cp_async_wait<0>();
+}
+
+}  // namespace cdi

@@ -171,6 +171,27 @@ __device__ __forceinline__ Partial load_partial_cg(const Partial *p)
     return r;
 }
 
+// Block-reduce p (every thread of the block must call this, block size a
+// multiple of 32); the result is valid in thread 0.  Ends with a barrier so
+// the shared buffer may be reused at once.
+__device__ __forceinline__ Partial block_reduce(Partial p)
+{
+    __shared__ Partial wsum_b[32];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    p = warp_reduce(p);
+    if (lane == 0) wsum_b[wid] = p;
+    __syncthreads();
+    Partial q = pidentity();
+    if (wid == 0) {
+        q = lane < nw ? wsum_b[lane] : pidentity();
+        q = warp_reduce(q);
+    }
+    __syncthreads();
+    return q;
+}
+
 // Block-reduce p (every thread of the block must call this), store the block
 // partial, and let the last block to finish combine all partials in index
 // order into red.rec.  The block size must be a multiple of 32.
