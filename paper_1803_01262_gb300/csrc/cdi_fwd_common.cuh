@@ -49,6 +49,13 @@ template <> struct V16<double> {
     }
 };
 
+// Value of the lane one below / above within segments of WIDTH lanes (the
+// first / last lane of a segment gets its own value back).
+template <int WIDTH, typename T>
+__device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1, WIDTH); }
+template <int WIDTH, typename T>
+__device__ __forceinline__ T shfl_down1(T v) { return __shfl_down_sync(0xffffffffu, v, 1, WIDTH); }
+
 // Work unit u -> (tile origin, z range).
 struct Unit {
     int x0, y0, z0, z1;
