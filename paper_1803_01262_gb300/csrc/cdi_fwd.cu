@@ -30,8 +30,6 @@
 #include "cdi_fwd_common.cuh"
 #include "cdi_fwd_scalar.cuh"
 
-#include <type_traits>
-
 namespace cdi {
 
 // ===========================================================================
@@ -58,11 +56,8 @@ struct VecCfg {
     static constexpr int CPHI = PHI / VX, CU = USZ / VX, CV = VSZ / VX, CW = WSZ / VX;
     static constexpr int RPHI = (CPHI + NT - 1) / NT;
     static constexpr int RU = (CU + NT - 1) / NT, RV = (CV + NT - 1) / NT, RW = (CW + NT - 1) / NT;
-    static constexpr int RTOT = (CPHI + 63) / 64 + (CU + 63) / 64 + (CV + 63) / 64 + (CW + 63) / 64;
-    static constexpr size_t bytes =
-        sizeof(T) * (size_t)(NSP * PHI + NSV * VEL + 2 * SXS + 2 * SYS) + sizeof(int) * RTOT * 64;
+    static constexpr size_t bytes = sizeof(T) * (size_t)(NSP * PHI + NSV * VEL + 2 * SXS + 2 * SYS);
     static_assert(2 * TX <= 32 && 2 * TY <= 32, "ring warps hold 2*TX groups and 2*TY cells");
-    static_assert(TX == 16, "x-neighbour shuffles use 16-lane row segments");
 };
 
 template <typename T, int TX, int TY>
@@ -77,7 +72,6 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
     T *const svel = sphi + C::NSP * C::PHI;                // [NSV][VEL] = u | v | w
     T *const ssx = svel + C::NSV * C::VEL;                 // [2][SXS]
     T *const ssy = ssx + 2 * C::SXS;                       // [2][SYS]
-    int *const sgoff = reinterpret_cast<int *>(ssy + 2 * C::SYS);  // copy offsets [RTOT][64]
 
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -109,11 +103,7 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
         VV::ld(yp, Pm + off + PP);
         VV::ld(zn, Pmm + off);
         VV::ld(zp, Pmp + off);
-        // x-neighbours of the group from the adjacent lanes of the 16-lane row
-        // segment; only the segment ends read shared memory.
-        T L = shfl_up1<TX>(c[VX - 1]), R = shfl_down1<TX>(c[0]);
-        if (gc == 0) L = Pm[off - 1];
-        if (gc == TX - 1) R = Pm[off + VX];
+        const T L = Pm[off - 1], R = Pm[off + VX];
 #pragma unroll
         for (int i = 0; i < VX; ++i) {
             const T g0 = (i + 1 < VX ? c[i + 1] : R) - (i > 0 ? c[i - 1] : L);
@@ -154,58 +144,58 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
         constexpr int RPHI = (C::CPHI + NC - 1) / NC, RU = (C::CU + NC - 1) / NC;
         constexpr int RV = (C::CV + NC - 1) / NC, RW = (C::CW + NC - 1) / NC;
         const int ct = tid - C::NOWN;
-        // Each copy thread keeps its chunk offsets in its own column of a small
-        // shared table (rows: phi rounds, then u, v, w), so they hold no
-        // registers on the flux path.
-        int *const gphi = sgoff + ct, *const gu = sgoff + RPHI * NC + ct;
-        int *const gv = gu + RU * NC, *const gw = gv + RV * NC;
+        int gphi[RPHI], gu[RU], gv[RV], gw[RW];
         if (!is_own) {
 #pragma unroll
             for (int r = 0; r < RPHI; ++r) {
                 const int e = ct + r * NC, row = e / (PP / VX), col = e - row * (PP / VX);
-                gphi[r * NC] = wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+                gphi[r] = wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
             }
 #pragma unroll
             for (int r = 0; r < RU; ++r) {
                 const int e = ct + r * NC, row = e / (UP / VX), col = e - row * (UP / VX);
-                gu[r * NC] = wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+                gu[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
             }
 #pragma unroll
             for (int r = 0; r < RV; ++r) {
                 const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
-                gv[r * NC] = wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+                gv[r] = wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx);
             }
 #pragma unroll
             for (int r = 0; r < RW; ++r) {
                 const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
-                gw[r * NC] = wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+                gw[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx);
             }
         }
-        // Full rounds of 64 chunks need no bounds test; only the last may be partial.
-        auto copy_rounds = [&](T *dst, const T *src, const int *goff, auto nchunks_c, auto nrounds_c) {
-            constexpr int NCH = decltype(nchunks_c)::value, NR = decltype(nrounds_c)::value;
-            constexpr int NFULL = NCH / NC;
-#pragma unroll
-            for (int r = 0; r < NFULL; ++r) cp_async<16>(dst + (ct + r * NC) * VX, src + goff[r * NC]);
-            if constexpr (NR > NFULL) {
-                const int e = ct + NFULL * NC;
-                if (e < NCH) cp_async<16>(dst + e * VX, src + goff[NFULL * NC]);
-            }
-        };
         auto issue_phi = [&](int z, int slot) {
             if (is_own) return;
-            copy_rounds(sphi + slot * C::PHI, a.phi + (long long)wrapi(z, nz) * plane, gphi,
-                        std::integral_constant<int, C::CPHI>{}, std::integral_constant<int, RPHI>{});
+            const T *src = a.phi + (long long)wrapi(z, nz) * plane;
+            T *dst = sphi + slot * C::PHI;
+#pragma unroll
+            for (int r = 0; r < RPHI; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CPHI) cp_async<16>(dst + e * VX, src + gphi[r]);
+            }
         };
         auto issue_vel = [&](int z, int slot) {
             if (is_own) return;
             const long long zo = (long long)z * plane;
             T *dst = svel + slot * C::VEL;
-            copy_rounds(dst, a.u + zo, gu, std::integral_constant<int, C::CU>{}, std::integral_constant<int, RU>{});
-            copy_rounds(dst + C::USZ, a.v + zo, gv, std::integral_constant<int, C::CV>{},
-                        std::integral_constant<int, RV>{});
-            copy_rounds(dst + C::USZ + C::VSZ, a.w + zo, gw, std::integral_constant<int, C::CW>{},
-                        std::integral_constant<int, RW>{});
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CU) cp_async<16>(dst + e * VX, a.u + zo + gu[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RV; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CV) cp_async<16>(dst + C::USZ + e * VX, a.v + zo + gv[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CW) cp_async<16>(dst + C::USZ + C::VSZ + e * VX, a.w + zo + gw[r]);
+            }
         };
 
         // phi slot of plane z: (z - z0 + 2) mod 5; velocity slot: (z - z0) mod 3.
@@ -305,18 +295,14 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
                 VV::ld(yn, Pk + po - PP);
                 VV::ld(yp, Pk + po + PP);
                 VV::ld(zp, Pk1 + po);
-                T L = shfl_up1<TX>(c[VX - 1]), R = shfl_down1<TX>(c[0]);
-                if (tx == 0) L = Pk[po - 1];
-                if (tx == TX - 1) R = Pk[po + VX];
+                const T L = Pk[po - 1], R = Pk[po + VX];
                 const T *sxr = ssx + b * C::SXS + ty * SXP + VX + tx * VX;
                 const T *syr = ssy + b * C::SYS + (ty + 1) * W + tx * VX;
                 T sxc[VX], syn[VX], syp[VX];
                 VV::ld(sxc, sxr);
                 VV::ld(syn, syr - W);
                 VV::ld(syp, syr + W);
-                T sxL = shfl_up1<TX>(sxc[VX - 1]), sxR = shfl_down1<TX>(sxc[0]);
-                if (tx == 0) sxL = sxr[-1];
-                if (tx == TX - 1) sxR = sxr[VX];
+                const T sxL = sxr[-1], sxR = sxr[VX];
                 const T *vel = svel + vk * C::VEL;
                 const T *ur = vel + ty * UP + VX + tx * VX;
                 const T *vr = vel + C::USZ + (ty + 1) * W + tx * VX;
@@ -326,8 +312,7 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
                 VV::ld(vc, vr);
                 VV::ld(vn, vr - W);
                 VV::ld(wc, wr);
-                T uL = shfl_up1<TX>(uc[VX - 1]);
-                if (tx == 0) uL = ur[-1];
+                const T uL = ur[-1];
                 T o[VX];
 #pragma unroll
                 for (int i = 0; i < VX; ++i) {
