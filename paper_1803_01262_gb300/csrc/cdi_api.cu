@@ -61,6 +61,7 @@ struct cdi_grid {
     unsigned int *counter;
     StatsRec *rec;    // fused-step record
     StatsRec *rec2;   // stand-alone reductions
+    unsigned int *status;  // bit 0: a bounded device wait gave up
     int capacity;
     // launch configuration of the forward and adjoint kernels
     LaunchCfg fwd, adj;
@@ -88,6 +89,7 @@ static RedScratch scratch(const cdi_grid *g, StatsRec *rec, int update_run)
     r.capacity = g->capacity;
     r.dV = pow(g->dx, (double)g->Df);
     r.update_run = update_run;
+    r.status = g->status;
     return r;
 }
 
@@ -207,13 +209,15 @@ int cdi_create_grid(cdi_grid **out, int nx, int ny, int nz, double dx, int dtype
     if ((e = cudaMalloc(&g->partials, sizeof(cdi::Partial) * (size_t)cap)) != cudaSuccess ||
         (e = cudaMalloc(&g->counter, sizeof(unsigned int))) != cudaSuccess ||
         (e = cudaMalloc(&g->rec, sizeof(StatsRec))) != cudaSuccess ||
-        (e = cudaMalloc(&g->rec2, sizeof(StatsRec))) != cudaSuccess) {
+        (e = cudaMalloc(&g->rec2, sizeof(StatsRec))) != cudaSuccess ||
+        (e = cudaMalloc(&g->status, sizeof(unsigned int))) != cudaSuccess) {
         cdi_destroy_grid(g);
         return cuda_fail(e, "cudaMalloc(scratch)");
     }
     StatsRec h;
     reset_run_host(&h);
     if ((e = cudaMemset(g->counter, 0, sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMemset(g->status, 0, sizeof(unsigned int))) != cudaSuccess ||
         (e = cudaMemcpy(g->rec, &h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(g->rec2, &h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess) {
         cdi_destroy_grid(g);
@@ -235,6 +239,7 @@ int cdi_destroy_grid(cdi_grid *g)
     cudaFree(g->counter);
     cudaFree(g->rec);
     cudaFree(g->rec2);
+    cudaFree(g->status);
     cudaFree(g->stage_in);
     cudaFree(g->stage_out);
     delete g;
@@ -433,15 +438,21 @@ int cdi_run(cdi_grid *g, void *buf_a, void *buf_b, int nsteps, double t0, double
     return CDI_OK;
 }
 
-static int read_rec(const StatsRec *dev, cdi_stats *out, cudaStream_t s)
+static int read_rec(const cdi_grid *g, const StatsRec *dev, cdi_stats *out, cudaStream_t s)
 {
     StatsRec h;
+    unsigned int st = 0;
     cudaError_t e;
     if ((e = cudaMemcpyAsync(&h, dev, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "statistics readback");
     static_assert(sizeof(StatsRec) == sizeof(cdi_stats), "record layout");
     memcpy(out, &h, sizeof(h));
+    if (st) {
+        cudaMemsetAsync(g->status, 0, sizeof(unsigned int), s);
+        return fail(CDI_ERR_TIMEOUT, "a bounded device-side wait gave up; results are unreliable");
+    }
     if (!isfinite(h.sum)) return fail(CDI_ERR_NAN, "non-finite phi (sum = %g)", h.sum);
     return CDI_OK;
 }
@@ -450,7 +461,7 @@ int cdi_step_stats(cdi_grid *g, cdi_stats *out, void *stream)
 {
     if (int rc = check_grid(g)) return rc;
     if (!out) return fail(CDI_ERR_ARG, "out is NULL");
-    return read_rec(g->rec, out, (cudaStream_t)stream);
+    return read_rec(g, g->rec, out, (cudaStream_t)stream);
 }
 
 int cdi_reset_run_stats(cdi_grid *g, void *stream)
@@ -479,7 +490,7 @@ int cdi_mass_and_bounds(cdi_grid *g, const void *phi, cdi_stats *out, void *stre
         ? cdi::launch_stats<double>((const double *)phi, g->n, DBL_EPSILON, r, nb, s)
         : cdi::launch_stats<float>((const float *)phi, g->n, FLT_EPSILON, r, nb, s);
     if (e != cudaSuccess) return cuda_fail(e, "stats launch");
-    return read_rec(g->rec2, out, s);
+    return read_rec(g, g->rec2, out, s);
 }
 
 int cdi_step_host(cdi_grid *g, const void *phi_in_host, void *phi_out_host, double dt, double eps,
@@ -499,7 +510,7 @@ int cdi_step_host(cdi_grid *g, const void *phi_in_host, void *phi_out_host, doub
     if (int rc = cdi_step(g, g->stage_in, g->stage_out, dt, eps, gamma, vel_scale, flags, stream)) return rc;
     if ((e = cudaMemcpyAsync(phi_out_host, g->stage_out, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
         return cuda_fail(e, "device-to-host copy");
-    if (stats_out) return read_rec(g->rec, stats_out, s);
+    if (stats_out) return read_rec(g, g->rec, stats_out, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "synchronise");
     return CDI_OK;
 }

@@ -32,6 +32,7 @@ struct RedScratch {
     int capacity;           // number of partial slots
     double dV;              // cell measure dx^D_f
     int update_run;         // 1: fold this result into the *_run accumulators
+    unsigned int *status;   // nullable: bit 0 set if a bounded device wait gave up
 };
 
 // Coefficients of one step, precomputed on the host in double and cast.

@@ -93,6 +93,7 @@ static int noalloc_t(int nx, int ny, int nz, double dx, const void *in, void *ou
     a.red.capacity = kMaxBlocks;
     a.red.dV = pow(dx, (double)((nx > 1) + (ny > 1) + (nz > 1)));
     a.red.update_run = 0;
+    a.red.status = nullptr;  // bounded waits still end; a time-out is not reported here
     // The counter must start at zero; clear it on the stream (no allocation).
     if ((e = cudaMemsetAsync(&scr->counter, 0, sizeof(unsigned int), s)) != cudaSuccess)
         return na_fail(CDI_ERR_CUDA, "clearing the block counter", e);
