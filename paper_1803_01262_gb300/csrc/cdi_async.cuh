@@ -7,11 +7,12 @@ template <int BYTES>
 __device__ __forceinline__ void cp_async(void *smem, const void *gmem)
 {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    // No "memory" clobber here: ordering against the reads of the landed data
+    // is given by cp_async_wait (which has one) and the barrier after it.
     if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
     else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES)
-                     : "memory");
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
 }
 
 __device__ __forceinline__ void cp_async_commit()

@@ -56,11 +56,8 @@ struct VecCfg {
     static constexpr int CPHI = PHI / VX, CU = USZ / VX, CV = VSZ / VX, CW = WSZ / VX;
     static constexpr int RPHI = (CPHI + NT - 1) / NT;
     static constexpr int RU = (CU + NT - 1) / NT, RV = (CV + NT - 1) / NT, RW = (CW + NT - 1) / NT;
-    static constexpr size_t bytes =
-        sizeof(T) * (size_t)(NSP * PHI + NSV * VEL + 2 * SXS + 2 * SYS) + 32 + 2 * 128 * sizeof(int);
+    static constexpr size_t bytes = sizeof(T) * (size_t)(NSP * PHI + NSV * VEL + 2 * SXS + 2 * SYS);
     static_assert(2 * TX <= 32 && 2 * TY <= 32, "ring warps hold 2*TX groups and 2*TY cells");
-    static_assert(PR + H + (H + 1) + H <= 128, "a ring thread owns at most two rows per stage");
-    static_assert((sizeof(T) * (size_t)(NSP * PHI + NSV * VEL + 2 * SXS + 2 * SYS)) % 8 == 0, "barrier alignment");
 };
 
 template <typename T, int TX, int TY>
@@ -75,7 +72,6 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
     T *const svel = sphi + C::NSP * C::PHI;                // [NSV][VEL] = u | v | w
     T *const ssx = svel + C::NSV * C::VEL;                 // [2][SXS]
     T *const ssy = ssx + 2 * C::SXS;                       // [2][SYS]
-    int *const sgoff = reinterpret_cast<int *>(ssy + 2 * C::SYS);  // barriers + row table
 
     const int tid = threadIdx.x;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -138,92 +134,75 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
     Acc<T> acc;
     acc.init();
 
-    // Staging: whole tile rows are copied global -> shared by bulk async copies
-    // (TMA engine) that complete on one of four mbarriers, one "stage" (a phi
-    // plane and/or a velocity plane) per barrier phase.  The 64 ring threads
-    // own the rows (row q belongs to ring thread q % 64); ring thread 0 arms
-    // each stage with its byte count.  Stage ids run on across units; stage s
-    // uses barrier s & 3 with parity (s >> 2) & 1.
-    unsigned long long *const bars = reinterpret_cast<unsigned long long *>(sgoff);
-    int *const rowp = reinterpret_cast<int *>(bars + 4);  // per ring thread: 2 rows x {base, gx}
-    constexpr int NROWS = C::PR + H + (H + 1) + H;       // phi, u, v, w rows of a stage
-    const int ct = tid - C::NOWN;
-    if (tid == 0) {
-        for (int i = 0; i < 4; ++i) mbar_init(bars + i, 1);
-        fence_barrier_init();
-    }
-    __syncthreads();
-    int sc = 0;  // next stage id
-
-    // Row q of a stage: array kind (0 phi, 1 u, 2 v, 3 w), row within it,
-    // first x, length, and destination offset inside its slot.
-    auto row_info = [&](int q, int &kind, int &i, int &xs_rel, int &len, int &doff) {
-        if (q < C::PR) { kind = 0; i = q; xs_rel = -VX; len = PP; doff = i * PP; return; }
-        q -= C::PR;
-        if (q < H) { kind = 1; i = q; xs_rel = -VX; len = UP; doff = i * UP; return; }
-        q -= H;
-        if (q < H + 1) { kind = 2; i = q; xs_rel = 0; len = W; doff = C::USZ + i * W; return; }
-        q -= H + 1;
-        kind = 3; i = q; xs_rel = 0; len = W; doff = C::USZ + C::VSZ + i * W;
-    };
-    // Issue one stage: phi planes zp0 .. zp0+np-1 into phi slots ps0.. (mod 5)
-    // and, if zv >= 0, the velocity plane zv into velocity slot vs.
-    auto issue_stage = [&](int x0, int y0, int zp0, int np, int ps0, int zv, int vs) {
-        unsigned long long *bar = bars + (sc & 3);
-        if (!is_own) {
-            fence_proxy_async();
-            for (int q = ct; q < NROWS; q += 64) {
-                int kind, i, xs_rel, len, doff;
-                row_info(q, kind, i, xs_rel, len, doff);
-                const int rbase = rowp[(q / 64) * 128 + ct * 2];
-                const int gx0 = rowp[(q / 64) * 128 + ct * 2 + 1];
-                const int nrep = kind == 0 ? np : (zv >= 0 ? 1 : 0);
-                for (int d = 0; d < nrep; ++d) {
-                    const T *arr = kind == 0 ? a.phi : kind == 1 ? a.u : kind == 2 ? a.v : a.w;
-                    const int z = kind == 0 ? zp0 + d : zv;
-                    int slot = kind == 0 ? ps0 + d : vs;
-                    if (kind == 0 && slot >= 5) slot -= 5;
-                    T *dst = (kind == 0 ? sphi + slot * C::PHI : svel + slot * C::VEL) + doff;
-                    const T *src = arr + (long long)wrapi(z, nz) * plane + rbase;
-                    int rem = len, gx = gx0;
-                    while (rem > 0) {  // split where the row wraps around the periodic x edge
-                        const int take = min(rem, nx - gx);
-                        bulk_g2s(dst, src + gx, (unsigned)(take * sizeof(T)), bar);
-                        dst += take;
-                        rem -= take;
-                        gx = 0;
-                    }
-                }
-            }
-            if (ct == 0)
-                mbar_arrive_expect_tx(bar, (unsigned)(sizeof(T) * ((size_t)np * C::PHI + (zv >= 0 ? C::VEL : 0))));
-        }
-        ++sc;
-    };
-    // After a first time-out this thread stops waiting, so the kernel ends quickly.
-    bool timed_out = false;
-    auto wait_stage = [&](int id) {
-        if (!timed_out)
-            timed_out = !mbar_wait_bounded(bars + (id & 3), (unsigned)((id >> 2) & 1), a.red.status);
-    };
-
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
         const Unit un = unit_of(u, ntiles, tiles_x, W, H, zc, nz);
         const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
 
-        __syncthreads();  // the previous unit's readers are done with every slot
-        if (!is_own) {    // this unit's row bases (wrapped y * nx) and first x (wrapped)
-            for (int q = ct; q < NROWS; q += 64) {
-                int kind, i, xs_rel, len, doff;
-                row_info(q, kind, i, xs_rel, len, doff);
-                const int yoff = kind == 0 ? -2 : kind == 2 ? -1 : 0;
-                rowp[(q / 64) * 128 + ct * 2] = wrapi(y0 + yoff + i, ny) * nx;
-                rowp[(q / 64) * 128 + ct * 2 + 1] = wrapi(x0 + xs_rel, nx);
+        // The 64 ring threads issue every 16-byte copy (they are idle while the
+        // own warps evaluate fluxes).  Global in-plane offsets of their chunks:
+        constexpr int NC = 64;
+        constexpr int RPHI = (C::CPHI + NC - 1) / NC, RU = (C::CU + NC - 1) / NC;
+        constexpr int RV = (C::CV + NC - 1) / NC, RW = (C::CW + NC - 1) / NC;
+        const int ct = tid - C::NOWN;
+        int gphi[RPHI], gu[RU], gv[RV], gw[RW];
+        if (!is_own) {
+#pragma unroll
+            for (int r = 0; r < RPHI; ++r) {
+                const int e = ct + r * NC, row = e / (PP / VX), col = e - row * (PP / VX);
+                gphi[r] = wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+            }
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                const int e = ct + r * NC, row = e / (UP / VX), col = e - row * (UP / VX);
+                gu[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+            }
+#pragma unroll
+            for (int r = 0; r < RV; ++r) {
+                const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
+                gv[r] = wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+            }
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
+                gw[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx);
             }
         }
+        auto issue_phi = [&](int z, int slot) {
+            if (is_own) return;
+            const T *src = a.phi + (long long)wrapi(z, nz) * plane;
+            T *dst = sphi + slot * C::PHI;
+#pragma unroll
+            for (int r = 0; r < RPHI; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CPHI) cp_async<16>(dst + e * VX, src + gphi[r]);
+            }
+        };
+        auto issue_vel = [&](int z, int slot) {
+            if (is_own) return;
+            const long long zo = (long long)z * plane;
+            T *dst = svel + slot * C::VEL;
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CU) cp_async<16>(dst + e * VX, a.u + zo + gu[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RV; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CV) cp_async<16>(dst + C::USZ + e * VX, a.v + zo + gv[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CW) cp_async<16>(dst + C::USZ + C::VSZ + e * VX, a.w + zo + gw[r]);
+            }
+        };
+
         // phi slot of plane z: (z - z0 + 2) mod 5; velocity slot: (z - z0) mod 3.
-        const int s0 = sc;
-        issue_stage(x0, y0, z0 - 2, 5, 0, z0, 0);
+        __syncthreads();  // the previous unit's readers are done with every slot
+        for (int d = 0; d < 5; ++d) issue_phi(z0 - 2 + d, d);  // planes z0-2 .. z0+2
+        issue_vel(z0, 0);
+        cp_async_commit();
 
         const int own_x = x0 + tx * VX, own_y = y0 + ty;
         const bool writes = is_own && own_x < nx && own_y < ny;
@@ -235,7 +214,8 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
 #pragma unroll
             for (int i = 0; i < VX; ++i) wlo[i] = __ldg(src + i);
         }
-        wait_stage(s0);
+        cp_async_wait<0>();
+        __syncthreads();
 
         // Prologue: s_z at plane z0-1 (own), s at plane z0 (own + ring), flux at z0-1/2.
         T szc[VX], Fzm[VX];
@@ -243,11 +223,11 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
             const T *P0 = sphi + 2 * C::PHI, *Pm1 = sphi + 1 * C::PHI, *Pm2 = sphi;
             const T *P1 = sphi + 3 * C::PHI;
             if (is_own) {
-                T a0[VX], a1[VX], szm[VX], s0v[VX], s1v[VX];
+                T a0[VX], a1[VX], szm[VX], s0[VX], s1[VX];
                 sharp_group(Pm1, Pm2, P0, tx, ty, a0, a1, szm);
-                sharp_group(P0, Pm1, P1, tx, ty, s0v, s1v, szc);
-                VV::st(ssx + (z0 & 1) * C::SXS + ty * SXP + VX + tx * VX, s0v);
-                VV::st(ssy + (z0 & 1) * C::SYS + (ty + 1) * W + tx * VX, s1v);
+                sharp_group(P0, Pm1, P1, tx, ty, s0, s1, szc);
+                VV::st(ssx + (z0 & 1) * C::SXS + ty * SXP + VX + tx * VX, s0);
+                VV::st(ssy + (z0 & 1) * C::SYS + (ty + 1) * W + tx * VX, s1);
                 T pm[VX], pc[VX];
                 VV::ld(pm, Pm1 + (ty + 2) * PP + VX + tx * VX);
                 VV::ld(pc, P0 + (ty + 2) * PP + VX + tx * VX);
@@ -255,16 +235,18 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
                 for (int i = 0; i < VX; ++i)
                     Fzm[i] = flux(c_adv * wlo[i], c_dif, c_shp, pm[i], pc[i], szm[i], szc[i]);
             } else if (is_yring) {
-                T r0[VX], r1[VX], r2[VX];
-                sharp_group(P0, Pm1, P1, ry_col, ry_row, r0, r1, r2);
-                VV::st(ssy + (z0 & 1) * C::SYS + (ry_row + 1) * W + ry_col * VX, r1);
+                T s0[VX], s1[VX], s2[VX];
+                sharp_group(P0, Pm1, P1, ry_col, ry_row, s0, s1, s2);
+                VV::st(ssy + (z0 & 1) * C::SYS + (ry_row + 1) * W + ry_col * VX, s1);
             } else if (is_xring) {
                 ssx[(z0 & 1) * C::SXS + rx_row * SXP + VX + rx_col] = sharp_cell(P0, Pm1, P1, rx_col, rx_row);
             }
         }
         // Plane z0+3 reuses the slot of plane z0-2, which the prologue just read.
         __syncthreads();
-        issue_stage(x0, y0, z0 + 3, z0 + 3 <= z1 + 1 ? 1 : 0, 0, z0 + 1 < z1 ? z0 + 1 : -1, 1);
+        if (z0 + 3 <= z1 + 1) issue_phi(z0 + 3, 0);
+        if (z0 + 1 < z1) issue_vel(z0 + 1, 1);
+        cp_async_commit();
 
         int pk = 2;  // phi slot of plane k
         int vk = 0;  // velocity slot of plane k
@@ -275,9 +257,11 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
             const int vk2 = vk == 0 ? 2 : vk - 1;   // slot of plane k+2
             // S1: phi plane k+2 and the velocities of plane k have landed, and
             // every thread has left iteration k-1.
-            wait_stage(s0 + (k - z0));
+            cp_async_wait<1>();
             __syncthreads();
-            issue_stage(x0, y0, k + 4, k + 4 <= z1 + 1 ? 1 : 0, pkm, k + 2 < z1 ? k + 2 : -1, vk2);
+            if (k + 4 <= z1 + 1) issue_phi(k + 4, pkm);
+            if (k + 2 < z1) issue_vel(k + 2, vk2);
+            cp_async_commit();
 
             // B: sharpening at plane k+1.
             const T *Pk = sphi + pk * C::PHI, *Pk1 = sphi + pk1 * C::PHI, *Pk2 = sphi + pk2 * C::PHI;
@@ -355,6 +339,7 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
             pk = pk1;
             vk = vk == 2 ? 0 : vk + 1;
         }
+        cp_async_wait<0>();
     }
     reduce_and_finish(acc.partial(), a.red);
 }
