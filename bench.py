@@ -239,6 +239,11 @@ def main():
         g.set_velocity(*vel)
         a = torch.from_numpy(f.phi).to(dev, dtype)
         b = torch.empty_like(a)
+        # untimed set-up: the library's autotuner picks the tile and z chunking
+        # on scratch copies of the field
+        s1, s2 = a.clone(), torch.empty_like(a)
+        g.autotune(s1, s2, dt, eps, gamma, reps=3)
+        del s1, s2
         return g, vel, a, b
 
     def time_steps(step, K, W):
@@ -280,6 +285,7 @@ def main():
 
     # ---- FP32 fused step (the headline) ----
     g32, vel32, a32, b32 = setup(torch.float32)
+    launch32 = g32.get_launch()
     with ClockSampler(local) as clk:
         total_ms, kern_ms = time_steps(fwd_stepper(g32, a32, b32), K, W)
     total_ms = maxrank(total_ms)
@@ -373,6 +379,9 @@ def main():
         ab = torch.from_numpy(fbig.phi).to(dev, torch.float32)
         bb = torch.empty_like(ab)
         dtb = 0.1 * fbig.h / fbig.U
+        s1, s2 = ab.clone(), torch.empty_like(ab)
+        gb.autotune(s1, s2, dtb, 1.0 / 512, gb.U, reps=2)
+        del s1, s2
         del fbig
         buf = [ab, bb]
 
@@ -411,7 +420,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "bytes_per_cell": BYTES_F32,
-                         "kernel_ms": avg_kernel_ms},
+                         "kernel_ms": avg_kernel_ms, "launch": launch32},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "Gcell-updates/s",
                     "h2d_bytes_per_step": cells * 4, "d2h_bytes_per_step": cells * 4 + 88,

@@ -616,7 +616,7 @@ int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps, d
     LaunchCfg best = saved;
     float best_t = 1e30f;
     int rc = CDI_OK;
-    const int chunk_opts[] = {0, 1, 2, 4, 8, 16};
+    const int chunk_opts[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32};
     for (int tile = 0; tile < cdi::fwd_num_tiles() && rc == CDI_OK; ++tile) {
         if (cdi::fwd_tile_is_vec(tile) && g->nx % (16 / (int)esize(g)) != 0) continue;
         for (int oi = 0; oi < (int)(sizeof(chunk_opts) / sizeof(int)); ++oi) {

@@ -1,0 +1,54 @@
+"""Run a fixed number of CDI steps in one launch configuration (for profilers).
+
+The deformation workload of the benchmark (sphere R = 0.15 at (0.35, 0.35,
+0.35) in an n^3 periodic box, deformation face velocity, eps = dx,
+gamma = U, dt = 0.1 dx / U), with the forward (or adjoint) kernel's launch
+configuration set explicitly so that a profiler capture is deterministic:
+
+    python -m paper_1803_01262_gb300.profile_step --n 256 --dtype f32 --tile 4 --nchunks 9 --steps 3
+"""
+from __future__ import annotations
+
+import argparse
+import math
+
+import torch
+
+from . import cdi
+from . import inputs as I
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--kernel", choices=["forward", "adjoint"], default="forward")
+    ap.add_argument("--tile", type=int, default=-1)
+    ap.add_argument("--nchunks", type=int, default=0)
+    ap.add_argument("--steps", type=int, default=3)
+    args = ap.parse_args()
+    dtype = torch.float32 if args.dtype == "f32" else torch.float64
+    n = args.n
+    f = I.deformation_3d(n)
+    g = cdi.Grid(n, n, n, f.h, dtype)
+    vel = [torch.from_numpy(x).cuda().to(dtype) for x in (f.u, f.v, f.w)]
+    g.set_velocity(*vel)
+    which = cdi.CDI_KERNEL_FORWARD if args.kernel == "forward" else cdi.CDI_KERNEL_ADJOINT
+    g.set_launch(which, args.tile, 0, args.nchunks)
+    a = torch.from_numpy(f.phi).cuda().to(dtype)
+    b = torch.empty_like(a)
+    dt, eps, gamma = 0.1 * f.h / f.U, f.h, f.U
+    lam = torch.ones_like(a) if args.kernel == "adjoint" else None
+    for i in range(args.steps):
+        vs = math.cos(math.pi * i * dt / 3.0)
+        if args.kernel == "forward":
+            g.step(a, b, dt, eps, gamma, vs)
+            a, b = b, a
+        else:
+            g.step_adjoint(a, lam, b, dt, eps, gamma, vs)
+    torch.cuda.synchronize()
+    print("launch", g.get_launch(which))
+
+
+if __name__ == "__main__":
+    main()
