@@ -107,6 +107,56 @@ def run(phi, u, v, w, dx, dt, eps, gamma, nsteps, period=0.0, t0=0.0):
     return p
 
 
+# Explicit Runge-Kutta schemes of Section 2.3 (Eq. 26-28), written from their
+# published definitions; each takes a right-hand side f(phi, t).
+RK_SCHEMES = ("euler", "rk2", "rk3", "rk4")
+
+
+def rk_advance(f, phi, t, dt, scheme):
+    """One step of: explicit Euler; the explicit midpoint rule (RK2); Wray's
+    low-storage third-order scheme (RK3: gamma = 8/15, 5/12, 3/4, zeta = 0,
+    -17/60, -5/12, stage times t, t + 8/15 dt, t + 2/3 dt); classic RK4."""
+    if scheme == "euler":
+        return phi + dt * f(phi, t)
+    if scheme == "rk2":
+        half = phi + 0.5 * dt * f(phi, t)
+        return phi + dt * f(half, t + 0.5 * dt)
+    if scheme == "rk3":
+        g = (8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0)
+        z = (0.0, -17.0 / 60.0, -5.0 / 12.0)
+        c = (0.0, 8.0 / 15.0, 2.0 / 3.0)
+        p, prev = phi, None
+        for s in range(3):
+            r = f(p, t + c[s] * dt)
+            p = p + dt * (g[s] * r + (z[s] * prev if prev is not None else 0.0))
+            prev = r
+        return p
+    if scheme == "rk4":
+        k1 = f(phi, t)
+        k2 = f(phi + 0.5 * dt * k1, t + 0.5 * dt)
+        k3 = f(phi + 0.5 * dt * k2, t + 0.5 * dt)
+        k4 = f(phi + dt * k3, t + dt)
+        return phi + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    raise ValueError(scheme)
+
+
+def rk_step(phi, u, v, w, dx, dt, eps, gamma, scheme, t=0.0, period=0.0):
+    """One RK step of the CDI equation; velocity scaled by cos(pi t/period) at each stage time."""
+    phi, u, v, w = _check(phi, u, v, w)
+
+    def f(p, tt):
+        s = np.cos(np.pi * tt / period) if period > 0 else 1.0
+        return rhs(p, u, v, w, dx, eps, gamma, s)
+    return rk_advance(f, phi, t, dt, scheme)
+
+
+def rk_run(phi, u, v, w, dx, dt, eps, gamma, nsteps, scheme, period=0.0, t0=0.0):
+    p = _f64(phi)
+    for i in range(nsteps):
+        p = rk_step(p, u, v, w, dx, dt, eps, gamma, scheme, t0 + i * dt, period)
+    return p
+
+
 def stats(phi, dV, tol):
     """{mass, sum, min, max, n_strict, n_tol} of a field (plain sequential sum)."""
     phi = _f64(phi).ravel()

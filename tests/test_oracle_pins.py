@@ -393,3 +393,67 @@ def test_adjoint_constant_lambda():
     phi, u, v, w, h = rand_case((4, 5, 6), 51, solenoidal=False)
     lam = oracle.adjoint(phi, u, v, w, np.full(phi.shape, 2.5), h, 0.2 * h * h, h, 1.0)
     assert np.abs(lam - 2.5).max() == 0.0
+
+
+# ------------------------------------------------------------ RK pins (Section 2.3)
+
+@pytest.mark.parametrize("scheme,poly", [
+    ("euler", [1, 1]), ("rk2", [1, 1, 1 / 2]), ("rk3", [1, 1, 1 / 2, 1 / 6]),
+    ("rk4", [1, 1, 1 / 2, 1 / 6, 1 / 24])])
+def test_rk_amplification_polynomials(scheme, poly):
+    """On y' = lam y each scheme multiplies y by its stability polynomial R(z), z = lam dt
+    (explicit midpoint and Wray's RK3 and classic RK4 are all order-p, p-stage schemes)."""
+    for z in (-0.7, -0.1, 0.3, -1.9):
+        got = oracle.rk_advance(lambda y, t: z * y, np.array([1.0]), 0.0, 1.0, scheme)[0]
+        assert abs(got - sum(c * z ** k for k, c in enumerate(poly))) < 1e-14
+
+
+def test_rk_time_dependent_stage_times():
+    """Stage times: y' = cos(t) integrated over one step matches sin to the scheme's order."""
+    for scheme, p in (("rk2", 2), ("rk3", 3), ("rk4", 4)):
+        errs = []
+        for dt in (0.2, 0.1):
+            y = np.array([0.0])
+            for i in range(int(round(1.0 / dt))):
+                y = oracle.rk_advance(lambda yy, t: np.cos(t) + 0 * yy, y, i * dt, dt, scheme)
+            errs.append(abs(y[0] - np.sin(1.0)))
+        assert errs[1] < errs[0] and np.log2(errs[0] / errs[1]) > p - 0.3
+
+
+@pytest.mark.parametrize("scheme,order", [("euler", 1), ("rk2", 2), ("rk3", 3), ("rk4", 4)])
+def test_rk_convergence_order_on_cdi(scheme, order):
+    """Temporal order of each scheme on the CDI right-hand side (smooth 2D field)."""
+    shape = (1, 16, 16)
+    h = 1.0 / 16
+    phi = 0.2 + 0.6 * I.random_phi(shape, 3, smooth=True)
+    u, v, w = I.random_velocity(shape, h, 6, 2, 4)
+    eps, gamma, T = h, 1.0, 0.004
+    ref = oracle.rk_run(phi, u, v, w, h, T / 256, eps, gamma, 256, "rk4", period=0.5)
+    errs = []
+    for n in (16, 32):
+        out = oracle.rk_run(phi, u, v, w, h, T / n, eps, gamma, n, scheme, period=0.5)
+        errs.append(np.abs(out - ref).max())
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > order - 0.15, (scheme, errs, rate)
+
+
+@pytest.mark.parametrize("scheme", ["rk2", "rk3", "rk4"])
+def test_rk_conservation_and_boundedness(scheme):
+    """Every stage conserves mass; with dt = Eq. 26-28 and parameters on the crossover line
+    the solution stays in [0, 1] (the paper's observation for RK, Section 2.3)."""
+    rng = np.random.default_rng(9)
+    tol = np.finfo(float).eps
+    lim = {"rk2": 1.0 / 2, "rk3": 2.51 / 4, "rk4": 2.79 / 4}[scheme]
+    for b in range(6):
+        shape = (int(rng.integers(3, 8)), int(rng.integers(3, 8)), int(rng.integers(3, 8)))
+        h = 1.0 / max(shape)
+        phi = I.random_phi(shape, b, smooth=True)
+        u, v, w = I.random_velocity(shape, h, 8, 2, 100 + b)
+        U = I.face_umax(u, v, w)
+        eps, gamma = h, U
+        dt = 0.95 * lim * h * h / (3 * gamma * eps)
+        p = phi
+        for _ in range(20):
+            p = oracle.rk_step(p, u, v, w, h, dt, eps, gamma, scheme)
+            assert ((p < -tol) | (p > 1 + tol)).sum() == 0
+        assert abs(p.sum() - phi.sum()) <= 1e-13 * phi.sum()
