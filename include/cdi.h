@@ -146,6 +146,27 @@ CDI_API int cdi_run(cdi_grid *g, void *buf_a, void *buf_b, int nsteps, double t0
             double eps, double gamma, double period, int flags, int *final_in_b,
             void *stream);
 
+/* One step of a Runge-Kutta scheme of Section 2.3 from phi_in (left unchanged)
+ * to phi_out, with velocity cos(pi t_s/period) (u, v, w) at each stage time
+ * t_s (period <= 0: 1).  scheme: CDI_EULER (= cdi_step), CDI_RK2 (explicit
+ * midpoint), CDI_RK3 (Wray's low-storage scheme: stage weights 8/15, 5/12,
+ * 3/4 and -17/60, -5/12), CDI_RK4 (classic).  Each stage is one fused launch
+ * that evaluates the right-hand side and combines the stage in its
+ * epilogue.  work1 and work2 are caller-owned device arrays of the grid's
+ * size (unused for CDI_EULER); none of phi_in, phi_out, work1, work2 may
+ * overlap.  With CDI_CHECK_CONDITION the diffusive limit is the scheme's
+ * (Eq. 26-28: A <= 1/(2 D_f), 2.51/(4 D_f), 2.79/(4 D_f)).  The statistics
+ * record holds the step's result; the run accumulators count steps. */
+CDI_API int cdi_step_rk(cdi_grid *g, const void *phi_in, void *phi_out, void *work1, void *work2,
+                        double dt, double eps, double gamma, double t, double period, int scheme,
+                        int flags, void *stream);
+
+/* nsteps steps of cdi_step_rk ping-ponging buf_a (phi at t0) and buf_b;
+ * *final_in_b tells which buffer holds the result. */
+CDI_API int cdi_run_rk(cdi_grid *g, void *buf_a, void *buf_b, void *work1, void *work2, int nsteps,
+                       double t0, double dt, double eps, double gamma, double period, int scheme,
+                       int flags, int *final_in_b, void *stream);
+
 /* Copy the device statistics record of the last fused step to *out;
  * synchronises the stream.  Returns CDI_ERR_NAN if the sum is not finite. */
 CDI_API int cdi_step_stats(cdi_grid *g, cdi_stats *out, void *stream);

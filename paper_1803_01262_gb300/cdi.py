@@ -82,7 +82,10 @@ SIGNATURES = {
     "cdi_batch_run": [_V, _I, _V],
     "cdi_batch_stats": [_V, _V, _V],
     "cdi_batch_reset_run_stats": [_V, _V],
+    "cdi_step_rk": [_V, _V, _V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _Dbl, _I, _I, _V],
+    "cdi_run_rk": [_V, _V, _V, _V, _V, _I, _Dbl, _Dbl, _Dbl, _Dbl, _Dbl, _I, _I, _P(_I), _V],
 }
+SCHEMES = {"euler": CDI_EULER, "rk2": CDI_RK2, "rk3": CDI_RK3, "rk4": CDI_RK4}
 _RESTYPE = {"cdi_last_error_string": ctypes.c_char_p}
 
 _lib = None
@@ -230,6 +233,25 @@ class Grid:
         _ck(lib().cdi_run(self._h, self._arr(a, "a"), self._arr(b, "b"), nsteps, t0, dt, eps,
                           gamma, period, CDI_CHECK_CONDITION if check else 0, ctypes.byref(fb),
                           _stream(stream)))
+        return b if fb.value else a
+
+    def step_rk(self, phi_in, phi_out, work1, work2, dt, eps, gamma, scheme="rk4", t=0.0,
+                period=0.0, check=False, stream=None):
+        """One Runge-Kutta step (Section 2.3); work1/work2 are scratch tensors of the grid's shape."""
+        _ck(lib().cdi_step_rk(self._h, self._arr(phi_in, "phi_in"), self._arr(phi_out, "phi_out"),
+                              self._arr(work1, "work1"), self._arr(work2, "work2"), dt, eps, gamma,
+                              t, period, SCHEMES[scheme], CDI_CHECK_CONDITION if check else 0,
+                              _stream(stream)))
+        return phi_out
+
+    def run_rk(self, a, b, work1, work2, nsteps, dt, eps, gamma, scheme="rk4", period=0.0, t0=0.0,
+               check=False, stream=None):
+        """nsteps RK steps ping-ponging a <-> b; returns the tensor holding the result."""
+        fb = ctypes.c_int()
+        _ck(lib().cdi_run_rk(self._h, self._arr(a, "a"), self._arr(b, "b"), self._arr(work1, "work1"),
+                             self._arr(work2, "work2"), nsteps, t0, dt, eps, gamma, period,
+                             SCHEMES[scheme], CDI_CHECK_CONDITION if check else 0, ctypes.byref(fb),
+                             _stream(stream)))
         return b if fb.value else a
 
     def stats(self, stream=None):

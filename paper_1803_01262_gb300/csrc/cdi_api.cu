@@ -65,6 +65,7 @@ struct cdi_grid {
     int capacity;
     // launch configuration of the forward and adjoint kernels
     LaunchCfg fwd, adj;
+    LaunchCfg rk;  // Runge-Kutta stage kernels (set on first use; nblocks 0 = unset)
     // staging for cdi_step_host (owned, allocated on first use)
     void *stage_in, *stage_out;
     int sm_count;
@@ -108,16 +109,18 @@ static void reset_run_host(StatsRec *r)
 //   max(rounds * (planes per unit + 3), units * (planes per unit + 1) / blocks),
 // a per-block critical path (3 planes of prologue per unit) against the
 // average load (1 plane of re-read per unit).
-static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, LaunchCfg *c)
+static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, LaunchCfg *c,
+                   bool rk = false)
 {
     if (tile < 0 || tile >= cdi::fwd_num_tiles())
         return fail(CDI_ERR_ARG, "forward tile %d out of range", tile);
+    if (rk && !cdi::fwd_tile_has_rk(tile)) return fail(CDI_ERR_ARG, "no Runge-Kutta kernel for tile %d", tile);
     const int es = (int)esize(g);
     if (cdi::fwd_tile_is_vec(tile) && g->nx % (16 / es) != 0)
         return fail(CDI_ERR_ARG, "vector tile needs nx %% %d == 0", 16 / es);
     int resident = 0;
-    cudaError_t e = g->dtype == CDI_F64 ? cdi::fwd_occupancy<double>(tile, &resident)
-                                        : cdi::fwd_occupancy<float>(tile, &resident);
+    cudaError_t e = g->dtype == CDI_F64 ? cdi::fwd_occupancy<double>(tile, rk, &resident)
+                                        : cdi::fwd_occupancy<float>(tile, rk, &resident);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (resident < 1) return fail(CDI_ERR_CUDA, "forward kernel does not fit on an SM");
     if (blocks_per_sm > 0 && blocks_per_sm < resident) resident = blocks_per_sm;
@@ -149,6 +152,8 @@ static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, 
     c->nchunks = nchunks;
     return CDI_OK;
 }
+
+static int fwd_cfg_rk(const cdi_grid *g, int tile, LaunchCfg *c) { return fwd_cfg(g, tile, 0, 0, c, true); }
 
 static int default_fwd_tile(const cdi_grid *g)
 {
@@ -302,14 +307,16 @@ int cdi_get_umax(const cdi_grid *g, double *U)
 
 // Eq. 17 / 24: eps/dx >= (g + 1) / (2 g), g = gamma / U (g -> inf gives 1/2), and
 // Eq. 25: A = dt gamma eps / dx^2 <= 1 / (2 D_f); both with relative slack rel.
-static int condition_holds(double eps_over_dx, double gamma_over_U, double A, int Df, double rel)
+// ascale widens the diffusive limit for RK3 (2.51/2, Eq. 27) and RK4 (2.79/2, Eq. 28).
+static int condition_holds(double eps_over_dx, double gamma_over_U, double A, int Df, double rel,
+                           double ascale = 1.0)
 {
     if (!(eps_over_dx > 0) || !(gamma_over_U > 0) || !(A >= 0) || Df < 0 || Df > 3)
         return fail(CDI_ERR_ARG, "bad condition arguments");
     const double rhs = isinf(gamma_over_U) ? 0.5 : (gamma_over_U + 1.0) / (2.0 * gamma_over_U);
     const bool line_ok = eps_over_dx >= rhs * (1.0 - rel);
     const int d = Df > 0 ? Df : 1;
-    const bool a_ok = A <= (1.0 / (2.0 * d)) * (1.0 + rel);
+    const bool a_ok = A <= (ascale / (2.0 * d)) * (1.0 + rel);
     return (line_ok && a_ok) ? 1 : 0;
 }
 
@@ -351,8 +358,17 @@ static int check_step_args(const cdi_grid *g, const void *a, void *b, double dt,
     return CDI_OK;
 }
 
+static int check_condition_flag_scaled(const cdi_grid *g, double dt, double eps, double gamma,
+                                       double vel_scale, double ascale);
+
 static int check_condition_flag(const cdi_grid *g, double dt, double eps, double gamma,
                                 double vel_scale)
+{
+    return check_condition_flag_scaled(g, dt, eps, gamma, vel_scale, 1.0);
+}
+
+static int check_condition_flag_scaled(const cdi_grid *g, double dt, double eps, double gamma,
+                                       double vel_scale, double ascale)
 {
     const double Ueff = fabs(vel_scale) * g->U;
     const double gU = Ueff > 0 ? gamma / Ueff : INFINITY;
@@ -362,13 +378,13 @@ static int check_condition_flag(const cdi_grid *g, double dt, double eps, double
     // configuration placed on the line with a double gamma may sit a rounding
     // error below it: allow a slack of four units of the storage precision.
     const double rel = g->dtype == CDI_F32 ? 4.0 * FLT_EPSILON : 1e-12;
-    int ok = condition_holds(eps / g->dx, gU, A, g->Df, rel);
+    int ok = condition_holds(eps / g->dx, gU, A, g->Df, rel, ascale);
     if (ok < 0) return ok;
     if (!ok)
         return fail(CDI_ERR_CONDITION,
                     "boundedness condition fails: eps/dx=%.6g gamma/U=%.6g A=%.6g Df=%d "
-                    "(need eps/dx >= (g+1)/(2g) and A <= 1/(2 Df))",
-                    eps / g->dx, gU, A, g->Df);
+                    "(need eps/dx >= (g+1)/(2g) and A <= %.4g/(2 Df))",
+                    eps / g->dx, gU, A, g->Df, ascale);
     return CDI_OK;
 }
 
@@ -397,10 +413,147 @@ static int step_t(cdi_grid *g, const void *in, void *out, double dt, double eps,
     a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
     a.c = coefs<T>(g, dt, eps, gamma, vs);
     a.red = scratch(g, g->rec, 1);
+    a.rk_base = nullptr;
+    a.rk_q = nullptr;
+    a.rk_qout = nullptr;
+    a.rk_alpha = a.rk_delta = a.rk_mu = a.rk_beta = T(0);
     if (g->fwd.nblocks > g->capacity)
         return fail(CDI_ERR_STATE, "launch configuration exceeds the reduction scratch");
-    cudaError_t e = cdi::launch_fwd<T>(a, g->fwd.tile, g->fwd.nblocks, g->fwd.nchunks, s);
+    cudaError_t e = cdi::launch_fwd<T>(a, g->fwd.tile, g->fwd.nblocks, g->fwd.nchunks, false, s);
     if (e != cudaSuccess) return cuda_fail(e, "forward step launch");
+    return CDI_OK;
+}
+
+// One Runge-Kutta stage: evaluates r = dt * RHS(in) and writes
+//   out = (base ? base : in) + alpha r + (q ? delta q : 0),  qout = mu (q ? q : in) + beta r.
+// Uses the RK variant of the configured tile's kernel family (vector 16x16, or
+// the scalar 32x16 / 32x4 tile).
+struct RkStage {
+    const void *in, *base, *q;
+    void *out, *qout;
+    double alpha, delta, mu, beta, vs;
+    int last;  // fold the result into the run statistics
+};
+
+template <typename T>
+static int rk_stage_t(cdi_grid *g, const RkStage &st, double dt, double eps, double gamma, cudaStream_t s)
+{
+    if (g->rk.nblocks == 0) {  // first use: RK launch configuration for this grid
+        int tile = cdi::fwd_tile_is_vec(g->fwd.tile) ? 4 : ((g->nx >= 32 && g->ny >= 16) ? 1 : 3);
+        if (int rc = fwd_cfg_rk(g, tile, &g->rk)) return rc;
+    }
+    cdi::FwdArgs<T> a;
+    a.phi = (const T *)st.in;
+    a.out = (T *)st.out;
+    a.u = (const T *)g->u;
+    a.v = (const T *)(g->v ? g->v : g->u);
+    a.w = (const T *)(g->w ? g->w : g->u);
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
+    a.c = coefs<T>(g, dt, eps, gamma, st.vs);
+    a.red = scratch(g, g->rec, st.last);
+    a.rk_base = (const T *)st.base;
+    a.rk_q = (const T *)st.q;
+    a.rk_qout = (T *)st.qout;
+    a.rk_alpha = (T)st.alpha;
+    a.rk_delta = (T)st.delta;
+    a.rk_mu = (T)st.mu;
+    a.rk_beta = (T)st.beta;
+    cudaError_t e = cdi::launch_fwd<T>(a, g->rk.tile, g->rk.nblocks, g->rk.nchunks, true, s);
+    if (e != cudaSuccess) return cuda_fail(e, "Runge-Kutta stage launch");
+    return CDI_OK;
+}
+
+static int rk_stage(cdi_grid *g, const RkStage &st, double dt, double eps, double gamma, cudaStream_t s)
+{
+    return g->dtype == CDI_F64 ? rk_stage_t<double>(g, st, dt, eps, gamma, s)
+                               : rk_stage_t<float>(g, st, dt, eps, gamma, s);
+}
+
+static double vscale(double t, double period) { return period > 0 ? cos(M_PI * t / period) : 1.0; }
+
+// One step of the scheme from phi_in (kept) to phi_out, with work arrays w1, w2.
+static int rk_step_impl(cdi_grid *g, const void *pin, void *pout, void *w1, void *w2, double dt,
+                        double eps, double gamma, double t, double period, int scheme, cudaStream_t s)
+{
+    auto S = [&](const void *in, void *out, const void *base, const void *q, void *qout, double al,
+                 double de, double mu, double be, double tt, int last) {
+        RkStage st{in, base, q, out, qout, al, de, mu, be, vscale(tt, period), last};
+        return rk_stage(g, st, dt, eps, gamma, s);
+    };
+    int rc = CDI_OK;
+    switch (scheme) {
+    case CDI_EULER:
+        rc = S(pin, pout, nullptr, nullptr, nullptr, 1.0, 0.0, 0.0, 0.0, t, 1);
+        break;
+    case CDI_RK2:  // explicit midpoint
+        if (!(rc = S(pin, w1, nullptr, nullptr, nullptr, 0.5, 0.0, 0.0, 0.0, t, 0)))
+            rc = S(w1, pout, pin, nullptr, nullptr, 1.0, 0.0, 0.0, 0.0, t + 0.5 * dt, 1);
+        break;
+    case CDI_RK3: {  // Wray's low-storage scheme; w2 carries the previous stage's r
+        const double g1 = 8.0 / 15.0, g2 = 5.0 / 12.0, g3 = 3.0 / 4.0, z2 = -17.0 / 60.0, z3 = -5.0 / 12.0;
+        if (!(rc = S(pin, pout, nullptr, nullptr, w2, g1, 0.0, 0.0, 1.0, t, 0)) &&
+            !(rc = S(pout, w1, nullptr, w2, w2, g2, z2, 0.0, 1.0, t + g1 * dt, 0)))
+            rc = S(w1, pout, nullptr, w2, nullptr, g3, z3, 0.0, 0.0, t + (g1 + g2 + z2) * dt, 1);
+        break;
+    }
+    case CDI_RK4:  // classic; w2 accumulates phi + dt/6 (k1 + 2 k2 + 2 k3)
+        if (!(rc = S(pin, w1, nullptr, nullptr, w2, 0.5, 0.0, 1.0, 1.0 / 6.0, t, 0)) &&
+            !(rc = S(w1, pout, pin, w2, w2, 0.5, 0.0, 1.0, 1.0 / 3.0, t + 0.5 * dt, 0)) &&
+            !(rc = S(pout, w1, pin, w2, w2, 1.0, 0.0, 1.0, 1.0 / 3.0, t + 0.5 * dt, 0)))
+            rc = S(w1, pout, w2, nullptr, nullptr, 1.0 / 6.0, 0.0, 0.0, 0.0, t + dt, 1);
+        break;
+    default:
+        rc = fail(CDI_ERR_ARG, "unknown scheme %d", scheme);
+    }
+    return rc;
+}
+
+static int check_rk_args(cdi_grid *g, const void *a, void *b, void *w1, void *w2, double dt, double eps,
+                         double gamma, int scheme, int flags)
+{
+    if (int rc = check_step_args(g, a, b, dt, eps, gamma, 1.0)) return rc;
+    if (scheme < CDI_EULER || scheme > CDI_RK4) return fail(CDI_ERR_ARG, "unknown scheme %d", scheme);
+    if (scheme != CDI_EULER) {
+        if (!w1 || !w2) return fail(CDI_ERR_ARG, "work arrays are required for RK schemes");
+        if (!aligned16(w1) || !aligned16(w2)) return fail(CDI_ERR_ARG, "work arrays must be 16-byte aligned");
+        const size_t bytes = (size_t)g->n * esize(g);
+        const char *p[4] = {(const char *)a, (const char *)b, (const char *)w1, (const char *)w2};
+        for (int i = 0; i < 4; ++i)
+            for (int j = i + 1; j < 4; ++j)
+                if (p[i] < p[j] + bytes && p[j] < p[i] + bytes)
+                    return fail(CDI_ERR_ARG, "phi_in, phi_out and the work arrays must not overlap");
+    }
+    if (flags & CDI_CHECK_CONDITION) {
+        const double scale = scheme == CDI_RK3 ? 2.51 / 2.0 : scheme == CDI_RK4 ? 2.79 / 2.0 : 1.0;
+        if (int rc = check_condition_flag_scaled(g, dt, eps, gamma, 1.0, scale)) return rc;
+    }
+    return CDI_OK;
+}
+
+int cdi_step_rk(cdi_grid *g, const void *phi_in, void *phi_out, void *work1, void *work2, double dt,
+                double eps, double gamma, double t, double period, int scheme, int flags, void *stream)
+{
+    if (int rc = check_rk_args(g, phi_in, phi_out, work1, work2, dt, eps, gamma, scheme, flags)) return rc;
+    return rk_step_impl(g, phi_in, phi_out, work1, work2, dt, eps, gamma, t, period, scheme,
+                        (cudaStream_t)stream);
+}
+
+int cdi_run_rk(cdi_grid *g, void *buf_a, void *buf_b, void *work1, void *work2, int nsteps, double t0,
+               double dt, double eps, double gamma, double period, int scheme, int flags, int *final_in_b,
+               void *stream)
+{
+    if (nsteps < 0) return fail(CDI_ERR_ARG, "nsteps must be >= 0");
+    if (int rc = check_rk_args(g, buf_a, buf_b, work1, work2, dt, eps, gamma, scheme, flags)) return rc;
+    void *src = buf_a, *dst = buf_b;
+    for (int i = 0; i < nsteps; ++i) {
+        if (int rc = rk_step_impl(g, src, dst, work1, work2, dt, eps, gamma, t0 + i * dt, period, scheme,
+                                  (cudaStream_t)stream))
+            return rc;
+        void *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    if (final_in_b) *final_in_b = (src == buf_b);
     return CDI_OK;
 }
 

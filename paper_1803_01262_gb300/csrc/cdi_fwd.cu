@@ -60,7 +60,7 @@ struct VecCfg {
     static_assert(2 * TX <= 32 && 2 * TY <= 32, "ring warps hold 2*TX groups and 2*TY cells");
 };
 
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, bool RK>
 __global__ void __launch_bounds__(VecCfg<T, TX, TY>::NT, 2)
 fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
 {
@@ -263,6 +263,16 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
             if (k + 2 < z1) issue_vel(k + 2, vk2);
             cp_async_commit();
 
+            // Runge-Kutta stage operands of plane k, fetched now to overlap phase B.
+            T rb[VX], rq[VX];
+            if constexpr (RK) {
+                if (writes) {
+                    const long long o = (long long)k * plane + own_off;
+                    if (a.rk_base) VV::ld(rb, a.rk_base + o);
+                    if (a.rk_q) VV::ld(rq, a.rk_q + o);
+                }
+            }
+
             // B: sharpening at plane k+1.
             const T *Pk = sphi + pk * C::PHI, *Pk1 = sphi + pk1 * C::PHI, *Pk2 = sphi + pk2 * C::PHI;
             const int b1 = (k + 1) & 1;
@@ -327,12 +337,26 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
                     const T shp = (sr - sl) + (syp[i] - syn[i]);
                     const T Fzp = flux(c_adv * wc[i], c_dif, c_shp, c[i], zp[i], szc[i], szn[i]);
                     const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, Fzp - Fzm[i])));
-                    o[i] = fma(-c_upd, div, c[i]);
+                    if constexpr (RK) o[i] = -c_upd * div;  // r = dt * RHS, combined below
+                    else o[i] = fma(-c_upd, div, c[i]);
                     Fzm[i] = Fzp;
                     szc[i] = szn[i];
                 }
                 if (writes) {
-                    VV::st(a.out + (long long)k * plane + own_off, o);
+                    const long long ko = (long long)k * plane + own_off;
+                    if constexpr (RK) {
+                        T qo[VX];
+#pragma unroll
+                        for (int i = 0; i < VX; ++i) {
+                            const T r = o[i];
+                            const T base = a.rk_base ? rb[i] : c[i];
+                            const T q = a.rk_q ? rq[i] : T(0);
+                            o[i] = fma(a.rk_delta, q, fma(a.rk_alpha, r, base));
+                            qo[i] = fma(a.rk_beta, r, a.rk_mu * (a.rk_q ? q : c[i]));
+                        }
+                        if (a.rk_qout) VV::st(a.rk_qout + ko, qo);
+                    }
+                    VV::st(a.out + ko, o);
                     acc.template add_group<VX>(o, a.c.tol);
                 }
             }
@@ -347,7 +371,7 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
 // ===========================================================================
 // Scalar kernel (any extents): the per-unit body is in cdi_fwd_scalar.cuh.
 
-template <typename T, int BX, int BY>
+template <typename T, int BX, int BY, bool RK>
 __global__ void __launch_bounds__(BX * BY)
 fwd_kernel(const FwdArgs<T> a, const int nchunks)
 {
@@ -360,7 +384,7 @@ fwd_kernel(const FwdArgs<T> a, const int nchunks)
     acc.init();
     for (int u = blockIdx.x; u < units; u += gridDim.x) {
         const Unit un = unit_of(u, ntiles, tiles_x, BX, BY, zc, a.nz);
-        scalar_unit<T, BX, BY>(a, un, acc, smem_raw);
+        scalar_unit<T, BX, BY, RK>(a, un, acc, smem_raw);
     }
     reduce_and_finish(acc.partial(), a.red);
 }
@@ -402,43 +426,65 @@ static cudaError_t occ(K kernel, int threads, size_t smem, int *resident)
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, kernel, threads, smem);
 }
 
+// Runge-Kutta stage kernels exist for tiles 1, 3 (scalar) and 4 (vector) only.
+bool fwd_tile_has_rk(int tile) { return tile == 1 || tile == 3 || tile == 4; }
+
 template <typename T>
-cudaError_t fwd_occupancy(int tile, int *resident)
+cudaError_t fwd_occupancy(int tile, bool rk, int *resident)
 {
+    if (rk) {
+        switch (tile) {
+        case 1: return occ(fwd_kernel<T, 32, 16, true>, 512, FwdSmem<T, 32, 16>::bytes, resident);
+        case 3: return occ(fwd_kernel<T, 32, 4, true>, 128, FwdSmem<T, 32, 4>::bytes, resident);
+        case 4: return occ(fwd_vec_kernel<T, 16, 16, true>, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, resident);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (tile) {
-    case 0: return occ(fwd_kernel<T, 32, 8>, 256, FwdSmem<T, 32, 8>::bytes, resident);
-    case 1: return occ(fwd_kernel<T, 32, 16>, 512, FwdSmem<T, 32, 16>::bytes, resident);
-    case 2: return occ(fwd_kernel<T, 64, 8>, 512, FwdSmem<T, 64, 8>::bytes, resident);
-    case 3: return occ(fwd_kernel<T, 32, 4>, 128, FwdSmem<T, 32, 4>::bytes, resident);
-    case 4: return occ(fwd_vec_kernel<T, 16, 16>, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, resident);
-    case 5: return occ(fwd_vec_kernel<T, 16, 8>, VecCfg<T, 16, 8>::NT, VecCfg<T, 16, 8>::bytes, resident);
+    case 0: return occ(fwd_kernel<T, 32, 8, false>, 256, FwdSmem<T, 32, 8>::bytes, resident);
+    case 1: return occ(fwd_kernel<T, 32, 16, false>, 512, FwdSmem<T, 32, 16>::bytes, resident);
+    case 2: return occ(fwd_kernel<T, 64, 8, false>, 512, FwdSmem<T, 64, 8>::bytes, resident);
+    case 3: return occ(fwd_kernel<T, 32, 4, false>, 128, FwdSmem<T, 32, 4>::bytes, resident);
+    case 4: return occ(fwd_vec_kernel<T, 16, 16, false>, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, resident);
+    case 5: return occ(fwd_vec_kernel<T, 16, 8, false>, VecCfg<T, 16, 8>::NT, VecCfg<T, 16, 8>::bytes, resident);
     default: return cudaErrorInvalidValue;
     }
 }
-template cudaError_t fwd_occupancy<float>(int, int *);
-template cudaError_t fwd_occupancy<double>(int, int *);
+template cudaError_t fwd_occupancy<float>(int, bool, int *);
+template cudaError_t fwd_occupancy<double>(int, bool, int *);
 
 template <typename T>
-cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, cudaStream_t s)
+cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, bool rk, cudaStream_t s)
 {
+    if (rk) {
+        switch (tile) {
+        case 1: fwd_kernel<T, 32, 16, true><<<nblocks, dim3(32, 16), FwdSmem<T, 32, 16>::bytes, s>>>(a, nchunks); break;
+        case 3: fwd_kernel<T, 32, 4, true><<<nblocks, dim3(32, 4), FwdSmem<T, 32, 4>::bytes, s>>>(a, nchunks); break;
+        case 4:
+            fwd_vec_kernel<T, 16, 16, true><<<nblocks, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, s>>>(a, nchunks);
+            break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (tile) {
-    case 0: fwd_kernel<T, 32, 8><<<nblocks, dim3(32, 8), FwdSmem<T, 32, 8>::bytes, s>>>(a, nchunks); break;
-    case 1: fwd_kernel<T, 32, 16><<<nblocks, dim3(32, 16), FwdSmem<T, 32, 16>::bytes, s>>>(a, nchunks); break;
-    case 2: fwd_kernel<T, 64, 8><<<nblocks, dim3(64, 8), FwdSmem<T, 64, 8>::bytes, s>>>(a, nchunks); break;
-    case 3: fwd_kernel<T, 32, 4><<<nblocks, dim3(32, 4), FwdSmem<T, 32, 4>::bytes, s>>>(a, nchunks); break;
+    case 0: fwd_kernel<T, 32, 8, false><<<nblocks, dim3(32, 8), FwdSmem<T, 32, 8>::bytes, s>>>(a, nchunks); break;
+    case 1: fwd_kernel<T, 32, 16, false><<<nblocks, dim3(32, 16), FwdSmem<T, 32, 16>::bytes, s>>>(a, nchunks); break;
+    case 2: fwd_kernel<T, 64, 8, false><<<nblocks, dim3(64, 8), FwdSmem<T, 64, 8>::bytes, s>>>(a, nchunks); break;
+    case 3: fwd_kernel<T, 32, 4, false><<<nblocks, dim3(32, 4), FwdSmem<T, 32, 4>::bytes, s>>>(a, nchunks); break;
     case 4:
-        fwd_vec_kernel<T, 16, 16><<<nblocks, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, s>>>(a, nchunks);
+        fwd_vec_kernel<T, 16, 16, false><<<nblocks, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, s>>>(a, nchunks);
         break;
     case 5:
-        fwd_vec_kernel<T, 16, 8><<<nblocks, VecCfg<T, 16, 8>::NT, VecCfg<T, 16, 8>::bytes, s>>>(a, nchunks);
+        fwd_vec_kernel<T, 16, 8, false><<<nblocks, VecCfg<T, 16, 8>::NT, VecCfg<T, 16, 8>::bytes, s>>>(a, nchunks);
         break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template cudaError_t launch_fwd<float>(const FwdArgs<float> &, int, int, int, cudaStream_t);
-template cudaError_t launch_fwd<double>(const FwdArgs<double> &, int, int, int, cudaStream_t);
+template cudaError_t launch_fwd<float>(const FwdArgs<float> &, int, int, int, bool, cudaStream_t);
+template cudaError_t launch_fwd<double>(const FwdArgs<double> &, int, int, int, bool, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Stand-alone reductions: statistics of any field, and max |component| of

@@ -29,7 +29,9 @@ struct FwdSmem {
 };
 
 // Must be called by every thread of a (BX, BY) block with the same unit.
-template <typename T, int BX, int BY>
+// With RK the output is the Runge-Kutta stage combination of FwdArgs (see
+// cdi_internal.cuh) instead of the Euler update.
+template <typename T, int BX, int BY, bool RK = false>
 __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un, Acc<T> &acc,
                                             unsigned char *smem_raw)
 {
@@ -149,6 +151,14 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
         __syncthreads();
         if (k + 2 + PF_DIST <= z1 + 1) issue_plane(k + 2 + PF_DIST);
         cp_async_commit();
+        T rb = T(0), rq = T(0);
+        if constexpr (RK) {
+            if (own) {
+                const long long o = (long long)k * plane + oc;
+                if (a.rk_base) rb = __ldg(a.rk_base + o);
+                if (a.rk_q) rq = a.rk_q[o];
+            }
+        }
         T un_ = T(0), umn = T(0), vn = T(0), vmn = T(0), wn = T(0);
         if (k + 1 < z1) {
             const long long zb = (long long)(k + 1) * plane;
@@ -177,9 +187,17 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
         const T shp = (sxp - sxm) + (syp - sym);
         const T Fzp = flux(c_adv * wc, c_dif, c_shp, pc, pzp, szc, szn);
         const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, Fzp - Fzm)));
-        const T o = fma(-c_upd, div, pc);
+        T o = fma(-c_upd, div, pc);
         if (own) {
-            a.out[(long long)k * plane + oc] = o;
+            const long long ko = (long long)k * plane + oc;
+            if constexpr (RK) {
+                const T r = -c_upd * div;  // dt * RHS
+                const T base = a.rk_base ? rb : pc;
+                const T q = a.rk_q ? rq : T(0);
+                o = fma(a.rk_delta, q, fma(a.rk_alpha, r, base));
+                if (a.rk_qout) a.rk_qout[ko] = fma(a.rk_beta, r, a.rk_mu * (a.rk_q ? q : pc));
+            }
+            a.out[ko] = o;
             acc.add(o, a.c.tol);
         }
         Fzm = Fzp;

@@ -55,6 +55,15 @@ struct FwdArgs {
     int nx, ny, nz;
     StepCoef<T> c;
     RedScratch red;
+    // Runge-Kutta stage epilogue (kernels instantiated with RK), per cell with
+    // r = dt * RHS(phi) = -c_upd * (flux divergence) and c = phi at the cell:
+    //   out  = (rk_base ? rk_base : c) + rk_alpha r + (rk_q ? rk_delta rk_q : 0)
+    //   qout = rk_mu (rk_q ? rk_q : c) + rk_beta r          (if rk_qout)
+    // rk_q and rk_qout may be the same array (each cell reads before it writes).
+    const T *rk_base;
+    const T *rk_q;
+    T *rk_qout;
+    T rk_alpha, rk_delta, rk_mu, rk_beta;
 };
 
 template <typename T>
@@ -88,10 +97,13 @@ long long fwd_tiles_xy(int tile, int esize, int nx, int ny);
 
 // Blocks of the forward kernel with this tile that fit on one SM (sets the smem attribute).
 template <typename T>
-cudaError_t fwd_occupancy(int tile, int *resident);
+cudaError_t fwd_occupancy(int tile, bool rk, int *resident);
+
+// rk selects the Runge-Kutta stage variant (tiles with fwd_tile_has_rk only).
+bool fwd_tile_has_rk(int tile);
 
 template <typename T>
-cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, cudaStream_t s);
+cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, bool rk, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_stats(const T *phi, long long n, T tol, RedScratch red, int nblocks,

@@ -62,7 +62,7 @@ static int noalloc_t(int nx, int ny, int nz, double dx, const void *in, void *ou
     if (nx % vx == 0 && nx >= 48) tile = ny >= 12 ? 4 : 5;
     else tile = (nx >= 32 && ny >= 16) ? 1 : 3;
     int resident = 0;
-    cudaError_t e = cdi::fwd_occupancy<T>(tile, &resident);
+    cudaError_t e = cdi::fwd_occupancy<T>(tile, false, &resident);
     if (e != cudaSuccess) return na_fail(CDI_ERR_CUDA, "occupancy query", e);
     const long long tiles = cdi::fwd_tiles_xy(tile, es, nx, ny);
     long long nb = (long long)resident * sms;
@@ -97,7 +97,11 @@ static int noalloc_t(int nx, int ny, int nz, double dx, const void *in, void *ou
     // The counter must start at zero; clear it on the stream (no allocation).
     if ((e = cudaMemsetAsync(&scr->counter, 0, sizeof(unsigned int), s)) != cudaSuccess)
         return na_fail(CDI_ERR_CUDA, "clearing the block counter", e);
-    if ((e = cdi::launch_fwd<T>(a, tile, (int)nb, nchunks, s)) != cudaSuccess)
+    a.rk_base = nullptr;
+    a.rk_q = nullptr;
+    a.rk_qout = nullptr;
+    a.rk_alpha = a.rk_delta = a.rk_mu = a.rk_beta = T(0);
+    if ((e = cdi::launch_fwd<T>(a, tile, (int)nb, nchunks, false, s)) != cudaSuccess)
         return na_fail(CDI_ERR_CUDA, "forward step launch", e);
     return CDI_OK;
 }
