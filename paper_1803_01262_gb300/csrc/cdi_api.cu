@@ -722,6 +722,7 @@ int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchu
         LaunchCfg c;
         if (int rc = fwd_cfg(g, tile, blocks_per_sm, nchunks, &c)) return rc;
         g->fwd = c;
+        g->rk.nblocks = 0;  // the Runge-Kutta configuration follows on next use
         return CDI_OK;
     }
     if (which == CDI_KERNEL_ADJOINT) {
@@ -803,6 +804,7 @@ int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps, d
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     g->fwd = rc == CDI_OK ? best : saved;
+    g->rk.nblocks = 0;
     if (rc == CDI_OK && best_ms) *best_ms = best_t;
     return rc;
 }
