@@ -24,7 +24,7 @@ CDI_F32, CDI_F64 = 0, 1
 CDI_EULER, CDI_RK2, CDI_RK3, CDI_RK4 = 0, 1, 2, 3
 CDI_CHECK_CONDITION = 1
 CDI_KERNEL_FORWARD, CDI_KERNEL_ADJOINT = 0, 1
-FWD_TILES = 6
+FWD_TILES = 7
 ADJ_TILES = 3
 
 _ERRNAMES = {-1: "CDI_ERR_ARG", -2: "CDI_ERR_DIM", -3: "CDI_ERR_CUDA", -4: "CDI_ERR_CONDITION",

@@ -118,6 +118,8 @@ static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, 
     const int es = (int)esize(g);
     if (cdi::fwd_tile_is_vec(tile) && g->nx % (16 / es) != 0)
         return fail(CDI_ERR_ARG, "vector tile needs nx %% %d == 0", 16 / es);
+    if (tile == 6 && !cdi::tma_eligible(es, g->nx, g->ny, g->nz))
+        return fail(CDI_ERR_ARG, "tile 6 needs nx %% %d == 0 and ny %% 16 == 0", 16 * (16 / es));
     int resident = 0;
     cudaError_t e = g->dtype == CDI_F64 ? cdi::fwd_occupancy<double>(tile, rk, &resident)
                                         : cdi::fwd_occupancy<float>(tile, rk, &resident);

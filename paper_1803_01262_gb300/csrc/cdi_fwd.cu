@@ -393,9 +393,10 @@ fwd_kernel(const FwdArgs<T> a, const int nchunks)
 // Kernel table and launch
 //
 // Forward tiles: 0..3 scalar BX x BY = 32x8, 32x16, 64x8, 32x4;
-//                4, 5 vector TX x TY = 16x16, 16x8 (x width 16 * 16/sizeof(T)).
+//                4, 5 vector TX x TY = 16x16, 16x8 (x width 16 * 16/sizeof(T));
+//                6 vector 16x16 with tensor-memory-accelerator staging (cdi_fwd_tma.cu).
 
-int fwd_num_tiles() { return 6; }
+int fwd_num_tiles() { return 7; }
 
 bool fwd_tile_is_vec(int tile) { return tile >= 4; }
 
@@ -407,7 +408,7 @@ void fwd_tile_dims(int tile, int esize, int *bw, int *bh)
         *bh = sdim[tile][1];
     } else {
         *bw = 16 * (16 / esize);
-        *bh = tile == 4 ? 16 : 8;
+        *bh = tile == 5 ? 8 : 16;
     }
 }
 
@@ -447,6 +448,7 @@ cudaError_t fwd_occupancy(int tile, bool rk, int *resident)
     case 3: return occ(fwd_kernel<T, 32, 4, false>, 128, FwdSmem<T, 32, 4>::bytes, resident);
     case 4: return occ(fwd_vec_kernel<T, 16, 16, false>, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, resident);
     case 5: return occ(fwd_vec_kernel<T, 16, 8, false>, VecCfg<T, 16, 8>::NT, VecCfg<T, 16, 8>::bytes, resident);
+    case 6: return tma_occupancy<T>(resident);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -478,6 +480,7 @@ cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, 
     case 5:
         fwd_vec_kernel<T, 16, 8, false><<<nblocks, VecCfg<T, 16, 8>::NT, VecCfg<T, 16, 8>::bytes, s>>>(a, nchunks);
         break;
+    case 6: return launch_fwd_tma<T>(a, nblocks, nchunks, s);
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

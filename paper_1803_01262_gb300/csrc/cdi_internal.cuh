@@ -99,6 +99,14 @@ long long fwd_tiles_xy(int tile, int esize, int nx, int ny);
 template <typename T>
 cudaError_t fwd_occupancy(int tile, bool rk, int *resident);
 
+// Tile 6: tensor-memory-accelerator staging (cdi_fwd_tma.cu); needs
+// nx % W == 0 and ny % 16 == 0 with W = 16 * 16 / sizeof(T).
+bool tma_eligible(int esize, int nx, int ny, int nz);
+template <typename T>
+cudaError_t tma_occupancy(int *resident);
+template <typename T>
+cudaError_t launch_fwd_tma(const FwdArgs<T> &a, int nblocks, int nchunks, cudaStream_t s);
+
 // rk selects the Runge-Kutta stage variant (tiles with fwd_tile_has_rk only).
 bool fwd_tile_has_rk(int tile);
 
