@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--n", type=int, default=N, help="box edge (default 256)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and 512^3 lines")
+    ap.add_argument("--launch", default="",
+                    help="TILE,NCHUNKS: fixed FP32 forward launch instead of the autotuner "
+                         "(FP64 then keeps its default launch); for profiler captures")
     return ap.parse_args()
 
 
@@ -239,6 +242,11 @@ def main():
         g.set_velocity(*vel)
         a = torch.from_numpy(f.phi).to(dev, dtype)
         b = torch.empty_like(a)
+        if args.launch:
+            if dtype == torch.float32:
+                tile, nch = (int(x) for x in args.launch.split(","))
+                g.set_launch(cdi.CDI_KERNEL_FORWARD, tile, 0, nch)
+            return g, vel, a, b
         # untimed set-up: the library's autotuner picks the tile and z chunking
         # on scratch copies of the field
         s1, s2 = a.clone(), torch.empty_like(a)
