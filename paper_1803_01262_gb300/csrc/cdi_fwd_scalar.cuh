@@ -2,14 +2,16 @@
 // the single-box forward kernel and the batched kernel.
 //
 // A unit is a BX x BY tile of one box and a range of planes [z0, z1).  The
-// block stages phi planes with a halo of 2 in x and y by element-wise
-// cp.async into an 8-slot shared ring, PF_DIST planes ahead of use; computes
-// the sharpening vector s = phi (1 - phi) g/|g| of plane k+1 for its cells
-// and a one-cell ring (s_x on the x-ring, s_y on the y-ring); and updates
-// plane k from its six face fluxes
+// block stages phi planes with a halo of 2 in x and y, and the face-velocity
+// planes u (x from x0-1), v (y from y0-1) and w, by element-wise cp.async into
+// shared rings, PF planes ahead of use (phi plane j+2 and velocity plane j
+// travel in one commit group); computes the sharpening vector
+// s = phi (1 - phi) g/|g| of plane k+1 for its cells and a one-cell ring (s_x
+// on the x-ring, s_y on the y-ring); and updates plane k from its six face
+// fluxes
 //   F = c_adv u_f (phi_L + phi_R) - c_dif (phi_R - phi_L) + c_shp (s_L + s_R)
-// with the face below carried in a register.  Velocities are prefetched into
-// registers one plane ahead.  Outputs go to the caller's accumulator.
+// with the face below carried in a register.  Outputs go to the caller's
+// accumulator.
 #pragma once
 
 #include "cdi_async.cuh"
@@ -18,29 +20,36 @@
 
 namespace cdi {
 
-constexpr int PF_DIST = 2;  // phi plane k+2+PF_DIST is in flight while plane k is updated
-constexpr int NSLOT = 8;    // power of two >= PF_DIST + 3 live planes
+constexpr int SCALAR_PF = 3;  // default prefetch distance (planes) of the scalar body
+constexpr int NSLOT = 8;      // phi ring: power of two >= PF + 3 live planes (PF <= 5)
 
-template <typename T, int BX, int BY>
+__host__ __device__ constexpr int vel_slots(int pf) { return pf + 1 <= 4 ? 4 : 8; }
+
+template <typename T, int BX, int BY, int PF = SCALAR_PF>
 struct FwdSmem {
+    static_assert(PF >= 1 && PF + 3 <= NSLOT, "prefetch distance out of range");
     static constexpr int PX = BX + 4, PY = BY + 4;
+    static constexpr int NU = BY * (BX + 1), NV = (BY + 1) * BX, NW = BY * BX;
+    static constexpr int VPL = NU + NV + NW;  // one velocity plane: u | v | w
+    static constexpr int NVS = vel_slots(PF);
     static constexpr size_t bytes =
-        sizeof(T) * (NSLOT * PY * PX + 2 * BY * (BX + 2) + 2 * (BY + 2) * BX);
+        sizeof(T) * (NSLOT * PY * PX + 2 * BY * (BX + 2) + 2 * (BY + 2) * BX + NVS * VPL);
 };
 
-// Must be called by every thread of a (BX, BY) block with the same unit.
-// With RK the output is the Runge-Kutta stage combination of FwdArgs (see
-// cdi_internal.cuh) instead of the Euler update.
-template <typename T, int BX, int BY, bool RK = false>
+template <typename T, int BX, int BY, bool RK = false, int PF = SCALAR_PF>
 __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un, Acc<T> &acc,
                                             unsigned char *smem_raw)
 {
+    using S = FwdSmem<T, BX, BY, PF>;
     constexpr int PX = BX + 4, PY = BY + 4, PLANE = PX * PY;
     constexpr int NT = BX * BY;
     constexpr int NLOAD = (PLANE + NT - 1) / NT;
+    constexpr int NU = S::NU, NV = S::NV, NW = S::NW, NVS = S::NVS;
+    constexpr int RU = (NU + NT - 1) / NT, RV = (NV + NT - 1) / NT, RW = (NW + NT - 1) / NT;
     T(*sp)[PY][PX] = reinterpret_cast<T(*)[PY][PX]>(smem_raw);           // phi ring [NSLOT]
     T(*sx)[BY][BX + 2] = reinterpret_cast<T(*)[BY][BX + 2]>(sp + NSLOT);  // s_x, x = -1..BX [2]
     T(*sy)[BY + 2][BX] = reinterpret_cast<T(*)[BY + 2][BX]>(sx + 2);      // s_y, y = -1..BY [2]
+    T *const sv = reinterpret_cast<T *>(sy + 2);                          // velocity ring [NVS][VPL]
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -98,8 +107,6 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
     const int gx = wrapi(x0 + tx, nx), gy = wrapi(y0 + ty, ny);
     const bool own = (x0 + tx < nx) && (y0 + ty < ny);
     const int oc = gy * nx + gx;
-    const int oxm = gy * nx + wrapi(gx - 1, nx);
-    const int oym = wrapi(gy - 1, ny) * nx + gx;
 
     auto issue_plane = [&](int z) {
         const T *src = a.phi + (long long)wrapi(z, nz) * plane;
@@ -110,27 +117,63 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
             if (e < PLANE) cp_async<sizeof(T)>(dst + e, src + loff[r]);
         }
     };
+    // Velocity plane offsets: u rows y0.., columns x0-1..; v rows y0-1.., columns
+    // x0..; w rows y0.., columns x0.. (periodic wrap of overhanging tiles).
+    int uoff[RU], voff[RV], woff[RW];
+#pragma unroll
+    for (int r = 0; r < RU; ++r) {
+        const int e = tid + r * NT, ey = e / (BX + 1), ex = e - ey * (BX + 1);
+        uoff[r] = (e < NU) ? wrapi(y0 + ey, ny) * nx + wrapi(x0 - 1 + ex, nx) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < RV; ++r) {
+        const int e = tid + r * NT, ey = e / BX, ex = e - ey * BX;
+        voff[r] = (e < NV) ? wrapi(y0 - 1 + ey, ny) * nx + wrapi(x0 + ex, nx) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int e = tid + r * NT, ey = e / BX, ex = e - ey * BX;
+        woff[r] = (e < NW) ? wrapi(y0 + ey, ny) * nx + wrapi(x0 + ex, nx) : 0;
+    }
+    auto issue_vel = [&](int z) {  // 0 <= z < nz
+        const long long zo = (long long)z * plane;
+        T *dst = sv + (z & (NVS - 1)) * S::VPL;
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+            const int e = tid + r * NT;
+            if (e < NU) cp_async<sizeof(T)>(dst + e, a.u + zo + uoff[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < RV; ++r) {
+            const int e = tid + r * NT;
+            if (e < NV) cp_async<sizeof(T)>(dst + NU + e, a.v + zo + voff[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const int e = tid + r * NT;
+            if (e < NW) cp_async<sizeof(T)>(dst + NU + NV + e, a.w + zo + woff[r]);
+        }
+    };
 
-    __syncthreads();  // the previous unit's readers are done with the ring
+    // Commit groups: first phi planes z0-2 .. z0+1; then PF prologue groups,
+    // the d-th holding phi plane z0+2+d and velocity plane z0+d; then one group
+    // per iteration j holding phi plane j+2+PF and velocity plane j+PF.  At
+    // iteration k, waiting until at most PF-1 groups are pending therefore
+    // lands phi plane k+2 and velocity plane k.
+    __syncthreads();  // the previous unit's readers are done with the rings
     issue_plane(z0 - 2);
     issue_plane(z0 - 1);
     issue_plane(z0);
     issue_plane(z0 + 1);
     cp_async_commit();
 #pragma unroll
-    for (int d = 0; d < PF_DIST; ++d) {
+    for (int d = 0; d < PF; ++d) {
         if (z0 + 2 + d <= z1 + 1) issue_plane(z0 + 2 + d);
+        if (z0 + d < z1) issue_vel(z0 + d);
         cp_async_commit();
     }
-    T uc, um, vc, vm, wc;
-    {
-        const long long zb = (long long)z0 * plane;
-        uc = __ldg(a.u + zb + oc); um = __ldg(a.u + zb + oxm);
-        vc = __ldg(a.v + zb + oc); vm = __ldg(a.v + zb + oym);
-        wc = __ldg(a.w + zb + oc);
-    }
     const T wlo = __ldg(a.w + (long long)wrapi(z0 - 1, nz) * plane + oc);
-    cp_async_wait<PF_DIST>();
+    cp_async_wait<PF>();
     __syncthreads();
     T szm, szc;
     {
@@ -146,10 +189,12 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
     }
 
     for (int k = z0; k < z1; ++k) {
-        // S1: plane k+2 has landed and every thread has left iteration k-1.
-        cp_async_wait<PF_DIST - 1>();
+        // S1: phi plane k+2 and velocity plane k have landed, and every thread
+        // has left iteration k-1 (so the slots written below are free).
+        cp_async_wait<PF - 1>();
         __syncthreads();
-        if (k + 2 + PF_DIST <= z1 + 1) issue_plane(k + 2 + PF_DIST);
+        if (k + 2 + PF <= z1 + 1) issue_plane(k + 2 + PF);
+        if (k + PF < z1) issue_vel(k + PF);
         cp_async_commit();
         T rb = T(0), rq = T(0);
         if constexpr (RK) {
@@ -158,13 +203,6 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
                 if (a.rk_base) rb = __ldg(a.rk_base + o);
                 if (a.rk_q) rq = a.rk_q[o];
             }
-        }
-        T un_ = T(0), umn = T(0), vn = T(0), vmn = T(0), wn = T(0);
-        if (k + 1 < z1) {
-            const long long zb = (long long)(k + 1) * plane;
-            un_ = __ldg(a.u + zb + oc); umn = __ldg(a.u + zb + oxm);
-            vn = __ldg(a.v + zb + oc); vmn = __ldg(a.v + zb + oym);
-            wn = __ldg(a.w + zb + oc);
         }
         // B: sharpening at plane k+1 (slot (k+1)&1; phase C reads slot k&1, which
         // was written before S1, so no barrier separates B from C).
@@ -178,6 +216,10 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
         const T pzp = sp[(k + 1) & (NSLOT - 1)][ty + 2][tx + 2];
         const T sxm = sx[b][ty][tx], sxp = sx[b][ty][tx + 2];
         const T sym = sy[b][ty][tx], syp = sy[b][ty + 2][tx];
+        const T *vel = sv + (k & (NVS - 1)) * S::VPL;
+        const T uc = vel[ty * (BX + 1) + tx + 1], um = vel[ty * (BX + 1) + tx];
+        const T vc = vel[NU + (ty + 1) * BX + tx], vm = vel[NU + ty * BX + tx];
+        const T wc = vel[NU + NV + ty * BX + tx];
         // x and y faces telescoped; the cell's own s_x, s_y cancel.
         T adv = uc * (pc + pxp);
         adv = fma(-um, pxm + pc, adv);
@@ -202,7 +244,6 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
         }
         Fzm = Fzp;
         szc = szn;
-        uc = un_; um = umn; vc = vn; vm = vmn; wc = wn;
     }
     cp_async_wait<0>();
 }
