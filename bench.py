@@ -357,7 +357,9 @@ def main():
                               phi_b=torch.empty(fb.phi.shape, dtype=torch.float32, device=dev)))
         del raw
         bt = cdi.Batch(boxes)
+        bt.autotune(reps=3)   # untimed set-up: work-unit tile and z depth
         binfo = bt.info()
+        blaunch = bt.get_launch()
         Kb = max(4, min(K, 400)) // 2 * 2
         bt.run(Kb)      # capture + warm-up
         barrier()
@@ -373,6 +375,8 @@ def main():
                  "cells": binfo["cells"], "units": binfo["units"], "blocks": binfo["nblocks"],
                  "value": ws * binfo["cells"] * Kb / (tb * 1e-3) / 1e9, "unit": "Gcell-updates/s",
                  "ms_per_step": tb / Kb, "steps": Kb, "launch": "one kernel per step, CUDA graph",
+                 "tile": ["32x8", "32x16", "64x8", "32x4"][blaunch["tile"]],
+                 "zdepth": blaunch["zdepth"],
                  "achieved_gbs": BYTES_F32 * binfo["cells"] / (tb / Kb * 1e-3) / 1e9,
                  "n_tol_run_total": int(sum(x["n_tol_run"] for x in bst))}
         del bt, boxes

@@ -249,6 +249,23 @@ CDI_API int cdi_batch_run(cdi_batch *b, int nsteps, void *stream);
 CDI_API int cdi_batch_stats(cdi_batch *b, cdi_stats *out, void *stream);
 CDI_API int cdi_batch_reset_run_stats(cdi_batch *b, void *stream);
 
+/* Launch configuration of the batch (a performance control, not part of the
+ * paper): tile 0..3 = 32x8, 32x16, 64x8, 32x4 cells per work unit (one cell
+ * per thread), zdepth = about that many planes per unit (0: whole box depth).
+ * tile = -1 / zdepth = -1 restore the defaults (32x8, CDI_BATCH_DEFAULT_ZDEPTH).
+ * Rebuilds the work list (synchronises the device; drops captured graphs). */
+#define CDI_BATCH_DEFAULT_ZDEPTH 32
+CDI_API int cdi_batch_set_launch(cdi_batch *b, int tile, int zdepth);
+CDI_API int cdi_batch_get_launch(const cdi_batch *b, int *tile, int *zdepth, int *nblocks,
+                                 int *total_units);
+
+/* Time every tile x zdepth in {8, 16, 32, 64, whole} with reps launches each
+ * (after one warm-up) and keep the fastest; *best_ms (nullable) gets its time
+ * per launch.  The trial launches read the current state and write the other
+ * buffer only, and the statistics records are restored, so the batch's state
+ * and records are as before the call.  Synchronises. */
+CDI_API int cdi_batch_autotune(cdi_batch *b, int reps, float *best_ms, void *stream);
+
 /* Kernels with a tunable launch configuration. */
 enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
 

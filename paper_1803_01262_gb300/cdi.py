@@ -82,6 +82,9 @@ SIGNATURES = {
     "cdi_batch_run": [_V, _I, _V],
     "cdi_batch_stats": [_V, _V, _V],
     "cdi_batch_reset_run_stats": [_V, _V],
+    "cdi_batch_set_launch": [_V, _I, _I],
+    "cdi_batch_get_launch": [_V, _P(_I), _P(_I), _P(_I), _P(_I)],
+    "cdi_batch_autotune": [_V, _I, _P(ctypes.c_float), _V],
     "cdi_step_rk": [_V, _V, _V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _Dbl, _I, _I, _V],
     "cdi_run_rk": [_V, _V, _V, _V, _V, _I, _Dbl, _Dbl, _Dbl, _Dbl, _Dbl, _I, _I, _P(_I), _V],
 }
@@ -375,6 +378,22 @@ class Batch:
     def run(self, nsteps, stream=None):
         """nsteps steps as one replay of a captured CUDA graph."""
         _ck(lib().cdi_batch_run(self._h, nsteps, _stream(stream)))
+
+    def set_launch(self, tile=-1, zdepth=-1):
+        """Work-unit tile (0..3: 32x8, 32x16, 64x8, 32x4) and planes per unit (0: whole box)."""
+        _ck(lib().cdi_batch_set_launch(self._h, tile, zdepth))
+
+    def get_launch(self):
+        t, z, n, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _ck(lib().cdi_batch_get_launch(self._h, ctypes.byref(t), ctypes.byref(z), ctypes.byref(n),
+                                       ctypes.byref(u)))
+        return dict(tile=t.value, zdepth=z.value, nblocks=n.value, units=u.value)
+
+    def autotune(self, reps=3, stream=None):
+        """Time every tile x z depth and keep the fastest; returns its ms per launch."""
+        ms = ctypes.c_float()
+        _ck(lib().cdi_batch_autotune(self._h, reps, ctypes.byref(ms), _stream(stream)))
+        return ms.value
 
     def stats(self, stream=None):
         out = (Stats * len(self.boxes))()

@@ -2,13 +2,16 @@
 // with its own face velocities, spacing, eps, gamma and dt, advanced by ONE
 // launch per step.  The launch is a persistent grid of resident blocks that
 // takes work units round-robin from one list covering every box: a unit is a
-// 32 x 8 tile of one box and a chunk of its planes, processed by the same
+// BX x BY tile of one box and a chunk of its planes, processed by the same
 // per-unit body as the single-box kernel (cdi_fwd_scalar.cuh).  Units of a box
-// are contiguous in the list, so blocks resident together share halo planes
-// through L2.  Each unit's outputs are reduced to one partial slot; the last
-// block to finish folds each box's slots, in order, into that box's
-// statistics record.  Multi-step runs are captured once into a CUDA graph and
-// replayed.
+// are contiguous in the list (chunk-major), so blocks resident together share
+// halo planes through L2.  Each unit's outputs are reduced to one partial
+// slot; the block that completes a box's last unit folds that box's slots, in
+// unit order, into the box's statistics record (reproducible, and spread over
+// the launch instead of serialised at its end).  The tile shape and the number
+// of planes per unit are a launch configuration (cdi_batch_set_launch), which
+// cdi_batch_autotune picks by timing.  Multi-step runs are captured once into
+// a CUDA graph and replayed.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -32,16 +35,15 @@ struct BoxDev {
     int tiles_x, ntiles, zc, unit0, nunits;
 };
 
-constexpr int BBX = 32, BBY = 8;
-
-template <typename T>
-__global__ void __launch_bounds__(BBX * BBY)
-batch_kernel(const BoxDev<T> *__restrict__ boxes, const int nbox, const int *__restrict__ unit_box,
+template <typename T, int BX, int BY>
+__global__ void __launch_bounds__(BX * BY)
+batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_box,
              const int total_units, const int parity, const T vs, Partial *partials,
-             unsigned int *counter, StatsRec *recs)
+             unsigned int *box_done, StatsRec *recs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int tid = threadIdx.x + BBX * threadIdx.y;
+    __shared__ int fold;
+    const int tid = threadIdx.x + BX * threadIdx.y;
     for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
         const int bi = unit_box[u];
         FwdArgs<T> a = boxes[bi].a;
@@ -52,49 +54,48 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int nbox, const int *__r
         }
         a.c.c_adv *= vs;
         const int lu = u - boxes[bi].unit0;
-        const Unit un = unit_of(lu, boxes[bi].ntiles, boxes[bi].tiles_x, BBX, BBY, boxes[bi].zc, a.nz);
+        const Unit un = unit_of(lu, boxes[bi].ntiles, boxes[bi].tiles_x, BX, BY, boxes[bi].zc, a.nz);
         Acc<T> acc;
         acc.init();
-        scalar_unit<T, BBX, BBY>(a, un, acc, smem_raw);
+        scalar_unit<T, BX, BY>(a, un, acc, smem_raw);
         const Partial p = block_reduce(acc.partial());
-        if (tid == 0) partials[u] = p;
-    }
-    // The last block to arrive folds each box's unit partials (in unit order).
-    __shared__ int is_last;
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(counter, 1u);
-        is_last = prev == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    for (int bi = 0; bi < nbox; ++bi) {
-        const int u0 = boxes[bi].unit0, nu = boxes[bi].nunits;
-        Partial acc = pidentity();
-        for (int i = tid; i < nu; i += BBX * BBY) acc = pcombine(acc, load_partial_cg(partials + u0 + i));
-        acc = block_reduce(acc);
         if (tid == 0) {
-            StatsRec *r = recs + bi;
-            r->mass = boxes[bi].dV * acc.sum;
-            r->sum = acc.sum;
-            r->mn = acc.mn;
-            r->mx = acc.mx;
-            r->ns = acc.ns;
-            r->nt = acc.nt;
-            r->mn_run = fmin(r->mn_run, acc.mn);
-            r->mx_run = fmax(r->mx_run, acc.mx);
-            r->ns_run += acc.ns;
-            r->nt_run += acc.nt;
-            r->steps_run += 1;
+            partials[u] = p;
+            __threadfence();
+            const unsigned done = atomicAdd(box_done + bi, 1u) + 1u;
+            fold = done == (unsigned)boxes[bi].nunits ? bi : -1;
         }
-    }
-    if (tid == 0) {
-        __threadfence();
-        *counter = 0u;
+        __syncthreads();
+        const int fb = fold;
+        if (fb >= 0) {  // this block completed box fb: fold its slots in unit order
+            __threadfence();
+            const int u0 = boxes[fb].unit0, nu = boxes[fb].nunits;
+            Partial q = pidentity();
+            for (int i = tid; i < nu; i += BX * BY) q = pcombine(q, load_partial_cg(partials + u0 + i));
+            q = block_reduce(q);
+            if (tid == 0) {
+                StatsRec *r = recs + fb;
+                r->mass = boxes[fb].dV * q.sum;
+                r->sum = q.sum;
+                r->mn = q.mn;
+                r->mx = q.mx;
+                r->ns = q.ns;
+                r->nt = q.nt;
+                r->mn_run = fmin(r->mn_run, q.mn);
+                r->mx_run = fmax(r->mx_run, q.mx);
+                r->ns_run += q.ns;
+                r->nt_run += q.nt;
+                r->steps_run += 1;
+                box_done[fb] = 0u;  // every unit of the box has counted in this launch
+            }
+        }
+        __syncthreads();  // every thread has read `fold` before it is written again
     }
 }
+
+// Batch tiles: the scalar tiles of the single-box kernel.
+constexpr int BATCH_TILES = 4;
+static const int batch_tile_dims[BATCH_TILES][2] = {{32, 8}, {32, 16}, {64, 8}, {32, 4}};
 
 }  // namespace cdi
 
@@ -103,20 +104,40 @@ using cdi::StatsRec;
 
 struct cdi_batch {
     int nbox, dtype, total_units, nblocks, parity;
+    int tile, zdepth;          // launch configuration: batch tile, planes per unit (0: whole box)
+    std::vector<cdi_box_desc> desc;
     void *boxes_dev;           // BoxDev<T>[nbox]
-    int *unit_box;             // [total_units]
-    cdi::Partial *partials;    // [total_units]
-    unsigned int *counter;
+    int *unit_box;             // [unit_cap]
+    cdi::Partial *partials;    // [unit_cap]
+    size_t unit_cap;
+    unsigned int *box_done;    // [nbox] units completed in the current launch
     StatsRec *recs;            // [nbox]
     long long cells;
+    int sms;
     cudaStream_t cap;          // capture stream for graphs
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (nsteps, parity) -> exec
 };
 
-static size_t batch_smem(int dtype)
+template <typename T, int BX, int BY>
+static cudaError_t batch_occ_one(int *resident)
 {
-    return dtype == CDI_F64 ? cdi::FwdSmem<double, cdi::BBX, cdi::BBY>::bytes
-                            : cdi::FwdSmem<float, cdi::BBX, cdi::BBY>::bytes;
+    const size_t smem = cdi::FwdSmem<T, BX, BY>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, BX, BY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, BX, BY>, BX * BY, smem);
+}
+
+template <typename T>
+static cudaError_t batch_occ(int tile, int *resident)
+{
+    switch (tile) {
+    case 0: return batch_occ_one<T, 32, 8>(resident);
+    case 1: return batch_occ_one<T, 32, 16>(resident);
+    case 2: return batch_occ_one<T, 64, 8>(resident);
+    case 3: return batch_occ_one<T, 32, 4>(resident);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 static int batch_free(cdi_batch *b)
@@ -127,25 +148,30 @@ static int batch_free(cdi_batch *b)
     cudaFree(b->boxes_dev);
     cudaFree(b->unit_box);
     cudaFree(b->partials);
-    cudaFree(b->counter);
+    cudaFree(b->box_done);
     cudaFree(b->recs);
     delete b;
     return CDI_OK;
 }
 
-template <typename T>
-static int build_table(cdi_batch *b, const cdi_box_desc *d, int nbox, std::vector<BoxDev<T>> &tab,
-                       std::vector<int> &ub)
+static void drop_graphs(cdi_batch *b)
 {
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+// Box table and work list for a tile and a z depth, uploaded to the device
+// (synchronous; the device arrays grow when needed).
+template <typename T>
+static int build_units(cdi_batch *b, int tile, int zdepth)
+{
+    const int bw = cdi::batch_tile_dims[tile][0], bh = cdi::batch_tile_dims[tile][1];
+    std::vector<BoxDev<T>> tab;
+    std::vector<int> ub;
     int unit = 0;
-    for (int i = 0; i < nbox; ++i) {
-        const cdi_box_desc &x = d[i];
-        if (x.nx < 1 || x.ny < 1 || x.nz < 1 || (long long)x.nx * x.ny >= (1LL << 31))
-            return cdi::set_error(CDI_ERR_DIM, "box %d: bad extents", i);
-        if (!(x.dx > 0) || !(x.dt >= 0) || !(x.eps > 0) || !(x.gamma >= 0))
-            return cdi::set_error(CDI_ERR_ARG, "box %d: bad dx, dt, eps or gamma", i);
-        if (!x.phi_a || !x.phi_b || !x.u || (!x.v && !(x.ny == 1 && x.nz == 1)) || (!x.w && x.nz != 1))
-            return cdi::set_error(CDI_ERR_ARG, "box %d: NULL array", i);
+    long long cells = 0;
+    for (int i = 0; i < b->nbox; ++i) {
+        const cdi_box_desc &x = b->desc[i];
         BoxDev<T> e;
         memset(&e, 0, sizeof(e));
         e.a.phi = (const T *)x.phi_a;
@@ -161,31 +187,84 @@ static int build_table(cdi_batch *b, const cdi_box_desc *d, int nbox, std::vecto
         e.a.c.tol = sizeof(T) == 8 ? (T)DBL_EPSILON : (T)FLT_EPSILON;
         const int Df = (x.nx > 1) + (x.ny > 1) + (x.nz > 1);
         e.dV = pow(x.dx, (double)Df);
-        e.tiles_x = (x.nx + cdi::BBX - 1) / cdi::BBX;
-        e.ntiles = e.tiles_x * ((x.ny + cdi::BBY - 1) / cdi::BBY);
-        int nch = (x.nz + 16) / 32;  // about 32 planes per unit
+        e.tiles_x = (x.nx + bw - 1) / bw;
+        e.ntiles = e.tiles_x * ((x.ny + bh - 1) / bh);
+        int nch = zdepth > 0 ? (x.nz + zdepth / 2) / zdepth : 1;  // about zdepth planes per unit
         if (nch < 1) nch = 1;
         e.zc = (x.nz + nch - 1) / nch;
         e.unit0 = unit;
         e.nunits = e.ntiles * ((x.nz + e.zc - 1) / e.zc);
+        if ((long long)unit + e.nunits >= (1LL << 31)) return cdi::set_error(CDI_ERR_DIM, "too many work units");
         for (int k = 0; k < e.nunits; ++k) ub.push_back(i);
         unit += e.nunits;
-        b->cells += (long long)x.nx * x.ny * x.nz;
+        cells += (long long)x.nx * x.ny * x.nz;
         tab.push_back(e);
     }
+    int resident = 0;
+    cudaError_t e = batch_occ<T>(tile, &resident);
+    if (e != cudaSuccess) return cdi::set_error(CDI_ERR_CUDA, "batch occupancy: %s", cudaGetErrorString(e));
+    if (resident < 1) return cdi::set_error(CDI_ERR_CUDA, "batch kernel does not fit on an SM");
+    if (ub.size() > b->unit_cap) {
+        cudaFree(b->unit_box);
+        cudaFree(b->partials);
+        b->unit_box = nullptr;
+        b->partials = nullptr;
+        b->unit_cap = 0;
+        if ((e = cudaMalloc(&b->unit_box, sizeof(int) * ub.size())) != cudaSuccess ||
+            (e = cudaMalloc(&b->partials, sizeof(cdi::Partial) * ub.size())) != cudaSuccess)
+            return cdi::set_error(CDI_ERR_CUDA, "batch allocation: %s", cudaGetErrorString(e));
+        b->unit_cap = ub.size();
+    }
+    if (!b->boxes_dev && (e = cudaMalloc(&b->boxes_dev, sizeof(BoxDev<T>) * b->nbox)) != cudaSuccess)
+        return cdi::set_error(CDI_ERR_CUDA, "batch allocation: %s", cudaGetErrorString(e));
+    // The previous configuration's launches may still read the old tables.
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess ||
+        (e = cudaMemcpy(b->boxes_dev, tab.data(), sizeof(BoxDev<T>) * b->nbox, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b->unit_box, ub.data(), sizeof(int) * ub.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cdi::set_error(CDI_ERR_CUDA, "batch tables: %s", cudaGetErrorString(e));
+    long long nb = (long long)resident * b->sms;
+    if (nb > unit) nb = unit;
+    if (nb < 1) nb = 1;
+    drop_graphs(b);
+    b->tile = tile;
+    b->zdepth = zdepth;
     b->total_units = unit;
+    b->nblocks = (int)nb;
+    b->cells = cells;
     return CDI_OK;
+}
+
+static int rebuild(cdi_batch *b, int tile, int zdepth)
+{
+    return b->dtype == CDI_F64 ? build_units<double>(b, tile, zdepth) : build_units<float>(b, tile, zdepth);
+}
+
+template <typename T, int BX, int BY>
+static void batch_launch_one(cdi_batch *b, int parity, double vs, cudaStream_t s)
+{
+    cdi::batch_kernel<T, BX, BY><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
+        (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
+        b->box_done, b->recs);
 }
 
 template <typename T>
 static int batch_launch(cdi_batch *b, int parity, double vs, cudaStream_t s)
 {
-    cdi::batch_kernel<T><<<b->nblocks, dim3(cdi::BBX, cdi::BBY), batch_smem(b->dtype), s>>>(
-        (const BoxDev<T> *)b->boxes_dev, b->nbox, b->unit_box, b->total_units, parity, (T)vs,
-        b->partials, b->counter, b->recs);
+    switch (b->tile) {
+    case 0: batch_launch_one<T, 32, 8>(b, parity, vs, s); break;
+    case 1: batch_launch_one<T, 32, 16>(b, parity, vs, s); break;
+    case 2: batch_launch_one<T, 64, 8>(b, parity, vs, s); break;
+    case 3: batch_launch_one<T, 32, 4>(b, parity, vs, s); break;
+    default: return cdi::set_error(CDI_ERR_STATE, "bad batch tile");
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cdi::set_error(CDI_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
     return CDI_OK;
+}
+
+static int launch_any(cdi_batch *b, int parity, double vs, cudaStream_t s)
+{
+    return b->dtype == CDI_F64 ? batch_launch<double>(b, parity, vs, s) : batch_launch<float>(b, parity, vs, s);
 }
 
 static void reset_recs(std::vector<StatsRec> &h)
@@ -201,60 +280,36 @@ int cdi_batch_create(cdi_batch **out, const cdi_box_desc *boxes, int nbox, int d
     if (!out || !boxes || nbox < 1) return cdi::set_error(CDI_ERR_ARG, "bad batch arguments");
     *out = nullptr;
     if (dtype != CDI_F32 && dtype != CDI_F64) return cdi::set_error(CDI_ERR_ARG, "bad dtype");
+    for (int i = 0; i < nbox; ++i) {
+        const cdi_box_desc &x = boxes[i];
+        if (x.nx < 1 || x.ny < 1 || x.nz < 1 || (long long)x.nx * x.ny >= (1LL << 31))
+            return cdi::set_error(CDI_ERR_DIM, "box %d: bad extents", i);
+        if (!(x.dx > 0) || !(x.dt >= 0) || !(x.eps > 0) || !(x.gamma >= 0))
+            return cdi::set_error(CDI_ERR_ARG, "box %d: bad dx, dt, eps or gamma", i);
+        if (!x.phi_a || !x.phi_b || !x.u || (!x.v && !(x.ny == 1 && x.nz == 1)) || (!x.w && x.nz != 1))
+            return cdi::set_error(CDI_ERR_ARG, "box %d: NULL array", i);
+    }
     cdi_batch *b = new cdi_batch();
     b->nbox = nbox;
     b->dtype = dtype;
-    std::vector<int> ub;
-    std::vector<unsigned char> tab_bytes;
-    int rc;
-    size_t tab_size;
-    if (dtype == CDI_F64) {
-        std::vector<BoxDev<double>> tab;
-        rc = build_table<double>(b, boxes, nbox, tab, ub);
-        tab_size = tab.size() * sizeof(BoxDev<double>);
-        tab_bytes.assign((unsigned char *)tab.data(), (unsigned char *)tab.data() + tab_size);
-    } else {
-        std::vector<BoxDev<float>> tab;
-        rc = build_table<float>(b, boxes, nbox, tab, ub);
-        tab_size = tab.size() * sizeof(BoxDev<float>);
-        tab_bytes.assign((unsigned char *)tab.data(), (unsigned char *)tab.data() + tab_size);
-    }
-    if (rc) {
-        batch_free(b);
-        return rc;
-    }
+    b->desc.assign(boxes, boxes + nbox);
     cudaError_t e;
-    int dev = 0, sms = 0, resident = 0;
-    const size_t smem = batch_smem(dtype);
+    int dev = 0;
+    std::vector<StatsRec> hrec(nbox);
+    reset_recs(hrec);
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
-        (e = dtype == CDI_F64
-                 ? cudaFuncSetAttribute(cdi::batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                 : cudaFuncSetAttribute(cdi::batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess ||
-        (e = dtype == CDI_F64
-                 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cdi::batch_kernel<double>, cdi::BBX * cdi::BBY, smem)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, cdi::batch_kernel<float>, cdi::BBX * cdi::BBY, smem)) != cudaSuccess) {
+        (e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaMalloc(&b->box_done, sizeof(unsigned int) * nbox)) != cudaSuccess ||
+        (e = cudaMalloc(&b->recs, sizeof(StatsRec) * nbox)) != cudaSuccess ||
+        (e = cudaMemset(b->box_done, 0, sizeof(unsigned int) * nbox)) != cudaSuccess ||
+        (e = cudaMemcpy(b->recs, hrec.data(), sizeof(StatsRec) * nbox, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
         batch_free(b);
         return cdi::set_error(CDI_ERR_CUDA, "batch setup: %s", cudaGetErrorString(e));
     }
-    long long nb = (long long)resident * sms;
-    if (nb > b->total_units) nb = b->total_units;
-    if (nb < 1) nb = 1;
-    b->nblocks = (int)nb;
-    std::vector<StatsRec> hrec(nbox);
-    reset_recs(hrec);
-    if ((e = cudaMalloc(&b->boxes_dev, tab_size)) != cudaSuccess ||
-        (e = cudaMalloc(&b->unit_box, sizeof(int) * ub.size())) != cudaSuccess ||
-        (e = cudaMalloc(&b->partials, sizeof(cdi::Partial) * ub.size())) != cudaSuccess ||
-        (e = cudaMalloc(&b->counter, sizeof(unsigned int))) != cudaSuccess ||
-        (e = cudaMalloc(&b->recs, sizeof(StatsRec) * nbox)) != cudaSuccess ||
-        (e = cudaMemcpy(b->boxes_dev, tab_bytes.data(), tab_size, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->unit_box, ub.data(), sizeof(int) * ub.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(b->recs, hrec.data(), sizeof(StatsRec) * nbox, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemset(b->counter, 0, sizeof(unsigned int))) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+    if (int rc = rebuild(b, 0, CDI_BATCH_DEFAULT_ZDEPTH)) {
         batch_free(b);
-        return cdi::set_error(CDI_ERR_CUDA, "batch allocation: %s", cudaGetErrorString(e));
+        return rc;
     }
     *out = b;
     return CDI_OK;
@@ -277,8 +332,7 @@ int cdi_batch_step(cdi_batch *b, double vel_scale, void *stream)
     if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
     if (!isfinite(vel_scale)) return cdi::set_error(CDI_ERR_ARG, "vel_scale must be finite");
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = b->dtype == CDI_F64 ? batch_launch<double>(b, b->parity, vel_scale, s)
-                                 : batch_launch<float>(b, b->parity, vel_scale, s);
+    int rc = launch_any(b, b->parity, vel_scale, s);
     if (rc == CDI_OK) b->parity ^= 1;
     return rc;
 }
@@ -297,9 +351,7 @@ int cdi_batch_run(cdi_batch *b, int nsteps, void *stream)
             return cdi::set_error(CDI_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
         int rc = CDI_OK;
         for (int i = 0; i < nsteps && rc == CDI_OK; ++i) {
-            const int p = b->parity ^ (i & 1);
-            rc = b->dtype == CDI_F64 ? batch_launch<double>(b, p, 1.0, b->cap)
-                                     : batch_launch<float>(b, p, 1.0, b->cap);
+            rc = launch_any(b, b->parity ^ (i & 1), 1.0, b->cap);
         }
         e = cudaStreamEndCapture(b->cap, &graph);
         if (rc) return rc;
@@ -340,5 +392,79 @@ int cdi_batch_reset_run_stats(cdi_batch *b, void *stream)
     if ((e = cudaMemcpyAsync(b->recs, h.data(), sizeof(StatsRec) * b->nbox, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cdi::set_error(CDI_ERR_CUDA, "reset batch statistics: %s", cudaGetErrorString(e));
+    return CDI_OK;
+}
+
+int cdi_batch_set_launch(cdi_batch *b, int tile, int zdepth)
+{
+    if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
+    if (tile < -1 || tile >= cdi::BATCH_TILES) return cdi::set_error(CDI_ERR_ARG, "batch tile %d out of range", tile);
+    if (zdepth < -1) return cdi::set_error(CDI_ERR_ARG, "zdepth must be >= -1");
+    return rebuild(b, tile < 0 ? 0 : tile, zdepth < 0 ? CDI_BATCH_DEFAULT_ZDEPTH : zdepth);
+}
+
+int cdi_batch_get_launch(const cdi_batch *b, int *tile, int *zdepth, int *nblocks, int *total_units)
+{
+    if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
+    if (tile) *tile = b->tile;
+    if (zdepth) *zdepth = b->zdepth;
+    if (nblocks) *nblocks = b->nblocks;
+    if (total_units) *total_units = b->total_units;
+    return CDI_OK;
+}
+
+int cdi_batch_autotune(cdi_batch *b, int reps, float *best_ms, void *stream)
+{
+    if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
+    if (reps < 1) return cdi::set_error(CDI_ERR_ARG, "reps must be >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    // Trial launches all read the current state and write the other buffer (the
+    // next step overwrites it anyway); they do update the statistics records,
+    // which are saved here and put back afterwards.
+    std::vector<StatsRec> saved(b->nbox);
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess ||
+        (e = cudaMemcpy(saved.data(), b->recs, sizeof(StatsRec) * b->nbox, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cdi::set_error(CDI_ERR_CUDA, "batch autotune: %s", cudaGetErrorString(e));
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cdi::set_error(CDI_ERR_CUDA, "cudaEventCreate");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cdi::set_error(CDI_ERR_CUDA, "cudaEventCreate");
+    }
+    const int zopts[] = {8, 16, 32, 64, 0};
+    int best_tile = b->tile, best_z = b->zdepth, rc = CDI_OK;
+    float best_t = 1e30f;
+    for (int tile = 0; tile < cdi::BATCH_TILES && rc == CDI_OK; ++tile) {
+        for (int zi = 0; zi < (int)(sizeof(zopts) / sizeof(int)) && rc == CDI_OK; ++zi) {
+            if ((rc = rebuild(b, tile, zopts[zi])) != CDI_OK) break;
+            if ((rc = launch_any(b, b->parity, 1.0, s)) != CDI_OK) break;  // warm-up
+            if ((e = cudaEventRecord(e0, s)) != cudaSuccess) {
+                rc = cdi::set_error(CDI_ERR_CUDA, "event: %s", cudaGetErrorString(e));
+                break;
+            }
+            for (int i = 0; i < reps && rc == CDI_OK; ++i) rc = launch_any(b, b->parity, 1.0, s);
+            if (rc != CDI_OK) break;
+            if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+                rc = cdi::set_error(CDI_ERR_CUDA, "event: %s", cudaGetErrorString(e));
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (ms < best_t) {
+                best_t = ms;
+                best_tile = tile;
+                best_z = zopts[zi];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CDI_OK) return rc;
+    if ((rc = rebuild(b, best_tile, best_z)) != CDI_OK) return rc;
+    if ((e = cudaMemcpy(b->recs, saved.data(), sizeof(StatsRec) * b->nbox, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cdi::set_error(CDI_ERR_CUDA, "batch autotune: %s", cudaGetErrorString(e));
+    if (best_ms) *best_ms = best_t;
     return CDI_OK;
 }

@@ -66,3 +66,53 @@ def test_batch_graph_run_equals_steps():
     s1, s2 = b1.stats(), b2.stats()
     for a, c in zip(s1, s2):
         assert a["sum"] == c["sum"] and a["steps_run"] == c["steps_run"] == 5
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("zdepth", [0, 5, 32])
+def test_batch_every_launch_configuration(dtype, tile, zdepth):
+    """Each work-unit tile and z depth gives the oracle's steps (ragged tiles and chunks)."""
+    boxes = make_boxes(dtype, nbox=5, nmin=5, nmax=28, seed=20 + tile)
+    b = cdi.Batch(boxes)
+    b.set_launch(tile, zdepth)
+    cfg = b.get_launch()
+    assert cfg["tile"] == tile and cfg["zdepth"] == zdepth and cfg["units"] > 0
+    for _ in range(2):
+        b.step(1.0)
+    st = b.stats()
+    t = np.float64 if dtype == torch.float64 else np.float32
+    tol = 1e-12 if dtype == torch.float64 else 3e-6
+    for i, x in enumerate(boxes):
+        f = x["fields"]
+        rin = [np.asarray(a, t).astype(np.float64) for a in (f.phi, f.u, f.v, f.w)]
+        ref = oracle.run(*rin, f.h, x["dt"], x["eps"], x["gamma"], 2)
+        ours = b.current(i).double().cpu().numpy()
+        assert np.abs(ours - ref).max() <= tol, i
+        assert st[i]["steps_run"] == 2
+        assert st[i]["min"] == ours.min() and st[i]["max"] == ours.max()
+
+
+def test_batch_autotune_keeps_state_and_records():
+    boxes = make_boxes(torch.float32, nbox=6, nmin=8, nmax=40, seed=31)
+    b = cdi.Batch(boxes)
+    b.step(1.0)
+    state = [b.current(i).clone() for i in range(len(boxes))]
+    before = b.stats()
+    ms = b.autotune(reps=1)
+    assert ms > 0
+    cfg = b.get_launch()
+    assert 0 <= cfg["tile"] < 4 and cfg["units"] > 0
+    assert b.info()["parity"] == 1
+    for i in range(len(boxes)):
+        assert torch.equal(b.current(i), state[i])
+    after = b.stats()
+    for x, y in zip(before, after):
+        assert x == y
+    b.step(1.0)
+    for i, x in enumerate(boxes):
+        f = x["fields"]
+        rin = [np.asarray(a, np.float32).astype(np.float64) for a in (f.phi, f.u, f.v, f.w)]
+        ref = oracle.run(*rin, f.h, x["dt"], x["eps"], x["gamma"], 2)
+        assert np.abs(b.current(i).double().cpu().numpy() - ref).max() <= 3e-6, i
+    assert b.stats()[0]["steps_run"] == 2
