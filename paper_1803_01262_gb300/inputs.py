@@ -4,7 +4,10 @@ This module is shared by the CUDA path, its tests, the bench and the FP64
 oracle.  It holds none of the method's arithmetic (no normals, fluxes or
 updates): only initial phase fields, face velocities and their parameters.
 Everything is generated on the host in float64 with numpy; callers cast to
-float32 where the FP32 path is exercised.
+float32 where the FP32 path is exercised.  For boxes too large for host
+generation (512^3 and up) the ``*_torch`` variants evaluate the same
+definitions on a CUDA device in float64 (mode table from the same seeded
+PCG64 stream), chunked along z.
 
 Grid conventions (Section 2.2 of the paper: phi at cell centres, velocity
 components on faces, uniform isotropic spacing h):
@@ -32,6 +35,7 @@ __all__ = [
     "ellipsoid_distance", "staggered_curl", "single_vortex_2d",
     "deformation_3d", "fourier_potential", "random_velocity", "face_umax",
     "drop_2d_uniform", "random_boxes", "random_phi",
+    "spheres_phi_torch", "random_velocity_torch",
 ]
 
 
@@ -321,3 +325,86 @@ def random_boxes(nbox=64, nmin=32, nmax=160, seed=0, nmodes=32, kmax=4,
         boxes.append(dict(fields=Fields(phi, u, v, w, h, U), eps=eps, gamma=gamma,
                           eps_over_h=eoh))
     return boxes
+
+
+# ---------------------------------------------------------------------------
+# Device-side variants for large boxes (float64 on a CUDA device via torch).
+
+def spheres_phi_torch(shape, h, spheres, eps, device="cuda", zchunk=64):
+    """tanh profile of the union of spheres (max of the periodic signed
+    distances R - |x - c|), as ``sphere_distance`` + ``tanh_profile``.
+    ``spheres`` is a list of ((x, y, z), R); returns a float64 tensor."""
+    import torch
+    nz, ny, nx = shape
+    out = torch.empty(shape, dtype=torch.float64, device=device)
+    ax = [((torch.arange(n, dtype=torch.float64, device=device) + 0.5) * h) for n in (nx, ny, nz)]
+
+    def pd(x, c, L):
+        d = x - c
+        return d - L * torch.round(d / L)
+    for z0 in range(0, nz, zchunk):
+        z1 = min(nz, z0 + zchunk)
+        s = None
+        for (c, R) in spheres:
+            dx = pd(ax[0], c[0], nx * h).view(1, 1, nx)
+            dy = pd(ax[1], c[1], ny * h).view(1, ny, 1)
+            dz = pd(ax[2][z0:z1], c[2], nz * h).view(z1 - z0, 1, 1)
+            d = R - torch.sqrt(dx * dx + dy * dy + dz * dz)
+            s = d if s is None else torch.maximum(s, d)
+        out[z0:z1] = 0.5 * (1.0 + torch.tanh(s / (2.0 * eps)))
+    return out
+
+
+def _eval_modes_torch(shape, offsets, k, coef, theta, device, zchunk=32):
+    """``_eval_modes`` on the device: sum_m coef_m cos(2 pi k_m.(idx + off)/N + theta_m)."""
+    import torch
+    nz, ny, nx = shape
+
+    def axis_exp(n, kd, off):
+        idx = torch.arange(n, dtype=torch.int64, device=device)
+        kt = torch.as_tensor(kd, dtype=torch.int64, device=device)
+        ph = ((kt[:, None] * idx[None, :]) % n).to(torch.float64) / n + (kt[:, None].to(torch.float64) * off) / n
+        return torch.polar(torch.ones_like(ph), 2.0 * math.pi * ph)  # (M, n) complex128
+    ex = axis_exp(nx, k[:, 0], offsets[0])
+    ey = axis_exp(ny, k[:, 1], offsets[1])
+    ez = axis_exp(nz, k[:, 2], offsets[2])
+    c = torch.polar(torch.as_tensor(coef, dtype=torch.float64, device=device),
+                    torch.as_tensor(theta, dtype=torch.float64, device=device))
+    out = torch.empty(shape, dtype=torch.float64, device=device)
+    for z0 in range(0, nz, zchunk):
+        z1 = min(nz, z0 + zchunk)
+        yz = c[:, None, None] * ez[:, z0:z1, None] * ey[:, None, :]          # (M, zc, ny)
+        out[z0:z1] = (yz.reshape(len(coef), -1).T @ ex).real.reshape(z1 - z0, ny, nx)
+    return out
+
+
+def random_velocity_torch(shape, h, nmodes=32, kmax=4, seed=0, umax=1.0, device="cuda"):
+    """``random_velocity`` on the device (same seeded mode table): the discrete
+    staggered curl of the Fourier vector potential, rescaled so U = umax.
+    Returns float64 tensors (u, v, w)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    ndim = 3 if shape[0] > 1 else 2
+    k, amp, theta = _mode_table(rng, nmodes, kmax, ndim)
+    Az = _eval_modes_torch(shape, (1.0, 1.0, 0.5), k, amp[:, 2], theta, device)
+    if shape[0] == 1:  # 2D: only the streamfunction component acts in-plane
+        Ax = torch.zeros_like(Az)
+        Ay = torch.zeros_like(Az)
+    else:
+        Ax = _eval_modes_torch(shape, (0.5, 1.0, 1.0), k, amp[:, 0], theta, device)
+        Ay = _eval_modes_torch(shape, (1.0, 0.5, 1.0), k, amp[:, 1], theta, device)
+
+    def dm(a, axis):
+        return a - torch.roll(a, 1, dims=axis)
+    u = (dm(Az, 1) - dm(Ay, 0)) / h
+    v = (dm(Ax, 0) - dm(Az, 2)) / h
+    del Az
+    w = (dm(Ay, 2) - dm(Ax, 1)) / h
+    del Ax, Ay
+    U = float(max(u.abs().max(), v.abs().max(), w.abs().max()))
+    if U > 0.0:
+        sc = umax / U
+        u.mul_(sc)
+        v.mul_(sc)
+        w.mul_(sc)
+    return u, v, w
