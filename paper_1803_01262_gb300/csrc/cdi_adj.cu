@@ -12,35 +12,50 @@
 //               + sum_d ( gbar_d(c - e_d) - gbar_d(c + e_d) )
 //   lam_c       = lam'_c + phibar_c
 //   ubar_{c+1/2} += Fbar_{c+1/2} vs (phi_c + phi_{c+e_d}) / 2     (optional)
-// The structure mirrors the forward kernel: phi and lam' planes staged with a
-// halo of 2 in 4-slot shared rings, gbar_x / gbar_y on a one-cell ring in a
-// 2-slot shared buffer, gbar_z and the z-face term carried in registers.
+// The structure mirrors the scalar forward body: phi and lam' planes (halo 2)
+// and the face velocities (u from x0-1, v from y0-1, w) are staged by
+// element-wise cp.async into shared rings PF_A planes ahead of use (phi and
+// lam' plane j+2 travel with velocity plane j in one commit group); gbar_x /
+// gbar_y of a plane go to a double-buffered shared array (written one plane
+// ahead), gbar_z and the z-face term are carried in registers; one barrier
+// per plane.
 #include "cdi_internal.cuh"
+#include "cdi_async.cuh"
 
 namespace cdi {
 
 __device__ __forceinline__ float rsqrt_a(float q) { return rsqrtf(q); }
 __device__ __forceinline__ double rsqrt_a(double q) { return rsqrt(q); }
 
+constexpr int PF_A = 3;    // prefetch distance (planes)
+constexpr int NSLOT_A = 8; // phi / lam' ring: power of two >= PF_A + 3 live planes
+constexpr int NVS_A = 4;   // velocity ring: power of two >= PF_A + 1
+
 template <typename T, int BX, int BY>
 struct AdjSmem {
     static constexpr int PX = BX + 4, PY = BY + 4;
-    static constexpr size_t bytes =
-        sizeof(T) * (2 * 4 * PY * PX + 2 * BY * (BX + 2) + 2 * (BY + 2) * BX);
+    static constexpr int NU = BY * (BX + 1), NV = (BY + 1) * BX, NW = BY * BX;
+    static constexpr int VPL = NU + NV + NW;
+    static constexpr size_t bytes = sizeof(T) * (2 * NSLOT_A * PY * PX + 2 * BY * (BX + 2) +
+                                                 2 * (BY + 2) * BX + NVS_A * VPL);
 };
 
 template <typename T, int BX, int BY>
 __global__ void __launch_bounds__(BX * BY)
 adj_kernel(const AdjArgs<T> a)
 {
+    using S = AdjSmem<T, BX, BY>;
     constexpr int PX = BX + 4, PY = BY + 4, PLANE = PX * PY;
     constexpr int NT = BX * BY;
     constexpr int NLOAD = (PLANE + NT - 1) / NT;
+    constexpr int NU = S::NU, NV = S::NV, NW = S::NW;
+    constexpr int RU = (NU + NT - 1) / NT, RV = (NV + NT - 1) / NT, RW = (NW + NT - 1) / NT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T(*sp)[PY][PX] = reinterpret_cast<T(*)[PY][PX]>(smem_raw);          // phi ring [4]
-    T(*sl)[PY][PX] = sp + 4;                                            // lam' ring [4]
-    T(*gxs)[BY][BX + 2] = reinterpret_cast<T(*)[BY][BX + 2]>(sl + 4);   // gbar_x [2]
-    T(*gys)[BY + 2][BX] = reinterpret_cast<T(*)[BY + 2][BX]>(gxs + 2);  // gbar_y [2]
+    T(*sp)[PY][PX] = reinterpret_cast<T(*)[PY][PX]>(smem_raw);          // phi ring [NSLOT_A]
+    T(*sl)[PY][PX] = sp + NSLOT_A;                                      // lam' ring [NSLOT_A]
+    T(*gxs)[BY][BX + 2] = reinterpret_cast<T(*)[BY][BX + 2]>(sl + NSLOT_A);  // gbar_x [2]
+    T(*gys)[BY + 2][BX] = reinterpret_cast<T(*)[BY + 2][BX]>(gxs + 2);       // gbar_y [2]
+    T *const sv = reinterpret_cast<T *>(gys + 2);                            // velocities [NVS_A][VPL]
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -56,11 +71,25 @@ adj_kernel(const AdjArgs<T> a)
         const int ey = e / PX, ex = e - ey * PX;
         loff[r] = (e < PLANE) ? wrapi(y0 + ey - 2, ny) * nx + wrapi(x0 + ex - 2, nx) : 0;
     }
+    int uoff[RU], voff[RV], woff[RW];
+#pragma unroll
+    for (int r = 0; r < RU; ++r) {
+        const int e = tid + r * NT, ey = e / (BX + 1), ex = e - ey * (BX + 1);
+        uoff[r] = (e < NU) ? wrapi(y0 + ey, ny) * nx + wrapi(x0 - 1 + ex, nx) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < RV; ++r) {
+        const int e = tid + r * NT, ey = e / BX, ex = e - ey * BX;
+        voff[r] = (e < NV) ? wrapi(y0 - 1 + ey, ny) * nx + wrapi(x0 + ex, nx) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r) {
+        const int e = tid + r * NT, ey = e / BX, ex = e - ey * BX;
+        woff[r] = (e < NW) ? wrapi(y0 + ey, ny) * nx + wrapi(x0 + ex, nx) : 0;
+    }
     const int gx = wrapi(x0 + tx, nx), gy = wrapi(y0 + ty, ny);
     const bool own = (x0 + tx < nx) && (y0 + ty < ny);
     const int oc = gy * nx + gx;
-    const int oxm = gy * nx + wrapi(gx - 1, nx);
-    const int oym = wrapi(gy - 1, ny) * nx + gx;
 
     int rkind = 0, rx = 0, ry = 0;
     if (tid < 2 * BX) {
@@ -78,26 +107,46 @@ adj_kernel(const AdjArgs<T> a)
     const T c_vel = a.c_vel;
     const bool want_vel = a.gu != nullptr;
 
-    auto load_plane = [&](int z) {
+    auto issue_plane = [&](int z) {
         const long long zo = (long long)wrapi(z, nz) * plane;
-        T *dp = &sp[z & 3][0][0];
-        T *dl = &sl[z & 3][0][0];
+        T *dp = &sp[z & (NSLOT_A - 1)][0][0];
+        T *dl = &sl[z & (NSLOT_A - 1)][0][0];
 #pragma unroll
         for (int r = 0; r < NLOAD; ++r) {
             const int e = tid + r * NT;
             if (e < PLANE) {
-                dp[e] = __ldg(a.phi + zo + loff[r]);
-                dl[e] = __ldg(a.lam + zo + loff[r]);
+                cp_async<sizeof(T)>(dp + e, a.phi + zo + loff[r]);
+                cp_async<sizeof(T)>(dl + e, a.lam + zo + loff[r]);
             }
         }
     };
+    auto issue_vel = [&](int z) {  // 0 <= z < nz
+        const long long zo = (long long)z * plane;
+        T *dst = sv + (z & (NVS_A - 1)) * S::VPL;
+#pragma unroll
+        for (int r = 0; r < RU; ++r) {
+            const int e = tid + r * NT;
+            if (e < NU) cp_async<sizeof(T)>(dst + e, a.u + zo + uoff[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < RV; ++r) {
+            const int e = tid + r * NT;
+            if (e < NV) cp_async<sizeof(T)>(dst + NU + e, a.v + zo + voff[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const int e = tid + r * NT;
+            if (e < NW) cp_async<sizeof(T)>(dst + NU + NV + e, a.w + zo + woff[r]);
+        }
+    };
+
     // gbar (3-vector) and the local term (1 - 2 phi)(sbar . n) at cell (lx, ly) of plane z.
     // The projection (I - n n^T) sbar is formed as n x (sbar x n), which is
     // exactly zero when sbar and n lie along one axis (the 1D case) and avoids
     // the cancellation of sbar - n (n . sbar) when |n| is off 1 by rounding.
     auto gbar = [&](int z, int lx, int ly, T &b0, T &b1, T &b2, T &tloc) {
         const int X = lx + 2, Y = ly + 2;
-        const int m = z & 3, mm = (z - 1) & 3, mp = (z + 1) & 3;
+        const int m = z & (NSLOT_A - 1), mm = (z - 1) & (NSLOT_A - 1), mp = (z + 1) & (NSLOT_A - 1);
         const T p = sp[m][Y][X];
         const T g0 = sp[m][Y][X + 1] - sp[m][Y][X - 1];
         const T g1 = sp[m][Y + 1][X] - sp[m][Y - 1][X];
@@ -135,10 +184,23 @@ adj_kernel(const AdjArgs<T> a)
         }
     };
 
-    load_plane(z0 - 2);
-    load_plane(z0 - 1);
-    load_plane(z0);
-    load_plane(z0 + 1);
+    // Commit groups: planes z0-2 .. z0+1; then PF_A prologue groups, the d-th
+    // with planes z0+2+d and velocity plane z0+d; then one group per iteration j
+    // with plane j+2+PF_A and velocity plane j+PF_A.  Waiting at iteration k
+    // until at most PF_A-1 groups are pending lands plane k+2 and velocity k.
+    issue_plane(z0 - 2);
+    issue_plane(z0 - 1);
+    issue_plane(z0);
+    issue_plane(z0 + 1);
+    cp_async_commit();
+#pragma unroll
+    for (int d = 0; d < PF_A; ++d) {
+        if (z0 + 2 + d <= z1 + 1) issue_plane(z0 + 2 + d);
+        if (z0 + d < z1) issue_vel(z0 + d);
+        cp_async_commit();
+    }
+    const T wlo = __ldg(a.w + (long long)wrapi(z0 - 1, nz) * plane + oc);
+    cp_async_wait<PF_A>();
     __syncthreads();
     T gz_m, gz_c, t_c;
     {
@@ -148,23 +210,28 @@ adj_kernel(const AdjArgs<T> a)
     gbar_plane(z0, gz_c, t_c);
     T Tzm;
     {
-        const T wlo = __ldg(a.w + (long long)wrapi(z0 - 1, nz) * plane + oc);
-        const T Fb = c_upd * (sl[z0 & 3][ty + 2][tx + 2] - sl[(z0 - 1) & 3][ty + 2][tx + 2]);
+        const T Fb = c_upd * (sl[z0 & (NSLOT_A - 1)][ty + 2][tx + 2] - sl[(z0 - 1) & (NSLOT_A - 1)][ty + 2][tx + 2]);
         Tzm = Fb * (c_adv * wlo - c_dif);
     }
-    __syncthreads();
 
     for (int k = z0; k < z1; ++k) {
-        load_plane(k + 2);
-        const long long zb = (long long)k * plane;
-        const T uc = __ldg(a.u + zb + oc), um = __ldg(a.u + zb + oxm);
-        const T vc = __ldg(a.v + zb + oc), vm = __ldg(a.v + zb + oym);
-        const T wc = __ldg(a.w + zb + oc);
+        // S1: plane k+2 and velocity plane k have landed; every thread has left
+        // iteration k-1 (its reads of the slots written below, and of the gbar
+        // buffer gbar_plane(k+1) writes).
+        cp_async_wait<PF_A - 1>();
         __syncthreads();
+        if (k + 2 + PF_A <= z1 + 1) issue_plane(k + 2 + PF_A);
+        if (k + PF_A < z1) issue_vel(k + PF_A);
+        cp_async_commit();
+
         T gz_p, t_p;
-        gbar_plane(k + 1, gz_p, t_p);
-        __syncthreads();
-        const int m = k & 3, b = k & 1, mp = (k + 1) & 3;
+        gbar_plane(k + 1, gz_p, t_p);  // buffer (k+1)&1; phase C reads buffer k&1
+        const long long zb = (long long)k * plane;
+        const int m = k & (NSLOT_A - 1), b = k & 1, mp = (k + 1) & (NSLOT_A - 1);
+        const T *vel = sv + (k & (NVS_A - 1)) * S::VPL;
+        const T uc = vel[ty * (BX + 1) + tx + 1], um = vel[ty * (BX + 1) + tx];
+        const T vc = vel[NU + (ty + 1) * BX + tx], vm = vel[NU + ty * BX + tx];
+        const T wc = vel[NU + NV + ty * BX + tx];
         const T lc = sl[m][ty + 2][tx + 2];
         const T Fxp = c_upd * (sl[m][ty + 2][tx + 3] - lc);
         const T Fxm = c_upd * (lc - sl[m][ty + 2][tx + 1]);
@@ -191,6 +258,7 @@ adj_kernel(const AdjArgs<T> a)
         gz_c = gz_p;
         t_c = t_p;
     }
+    cp_async_wait<0>();
 }
 
 struct TileDimA { int bx, by; };

@@ -6,6 +6,10 @@ gamma = U, dt = 0.1 dx / U), with the forward (or adjoint) kernel's launch
 configuration set explicitly so that a profiler capture is deterministic:
 
     python -m paper_1803_01262_gb300.profile_step --n 256 --dtype f32 --tile 4 --nchunks 9 --steps 3
+
+``--kernel batch`` runs the 64-box batch workload of the benchmark instead
+(edges U{32..160}, seed 0), with ``--tile`` / ``--zdepth`` as its work-unit
+tile and planes per unit (``--tile -1``: the autotuner's choice).
 """
 from __future__ import annotations
 
@@ -22,12 +26,15 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
-    ap.add_argument("--kernel", choices=["forward", "adjoint"], default="forward")
+    ap.add_argument("--kernel", choices=["forward", "adjoint", "batch"], default="forward")
+    ap.add_argument("--zdepth", type=int, default=64)
     ap.add_argument("--tile", type=int, default=-1)
     ap.add_argument("--nchunks", type=int, default=0)
     ap.add_argument("--steps", type=int, default=3)
     args = ap.parse_args()
     dtype = torch.float32 if args.dtype == "f32" else torch.float64
+    if args.kernel == "batch":
+        return run_batch(args, dtype)
     n = args.n
     f = I.deformation_3d(n)
     g = cdi.Grid(n, n, n, f.h, dtype)
@@ -48,6 +55,27 @@ def main():
             g.step_adjoint(a, lam, b, dt, eps, gamma, vs)
     torch.cuda.synchronize()
     print("launch", g.get_launch(which))
+
+
+def run_batch(args, dtype):
+    import numpy as np
+    boxes = []
+    for r in I.random_boxes(64, 32, 160, seed=0):
+        f = r["fields"]
+        Df = sum(1 for q in f.phi.shape if q > 1)
+        dt = 0.9 * f.h * f.h / (2 * Df * r["gamma"] * r["eps"])
+        d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+        boxes.append(dict(dx=f.h, dt=dt, eps=r["eps"], gamma=r["gamma"], u=d(f.u), v=d(f.v), w=d(f.w),
+                          phi_a=d(f.phi), phi_b=torch.empty(f.phi.shape, dtype=dtype, device="cuda")))
+    b = cdi.Batch(boxes)
+    if args.tile < 0:
+        b.autotune(reps=2)
+    else:
+        b.set_launch(args.tile, args.zdepth)
+    for _ in range(args.steps):
+        b.step(1.0)
+    torch.cuda.synchronize()
+    print("launch", b.get_launch(), b.info())
 
 
 if __name__ == "__main__":
