@@ -58,6 +58,8 @@ adj_kernel(const AdjArgs<T> a)
     T *const sv = reinterpret_cast<T *>(gys + 2);                            // velocities [NVS_A][VPL]
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    // The block is BX x BY: lets the compiler drop the bound checks of full copy rounds.
+    __builtin_assume(tx >= 0 && tx < BX && ty >= 0 && ty < BY);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
     const long long plane = (long long)nx * ny;
@@ -107,8 +109,8 @@ adj_kernel(const AdjArgs<T> a)
     const T c_vel = a.c_vel;
     const bool want_vel = a.gu != nullptr;
 
-    auto issue_plane = [&](int z) {
-        const long long zo = (long long)wrapi(z, nz) * plane;
+    // Stage phi and lam' plane z (ring slot z & (NSLOT_A-1)) from wrapped plane offset zo.
+    auto issue_plane_at = [&](int z, long long zo) {
         T *dp = &sp[z & (NSLOT_A - 1)][0][0];
         T *dl = &sl[z & (NSLOT_A - 1)][0][0];
 #pragma unroll
@@ -120,8 +122,9 @@ adj_kernel(const AdjArgs<T> a)
             }
         }
     };
-    auto issue_vel = [&](int z) {  // 0 <= z < nz
-        const long long zo = (long long)z * plane;
+    auto issue_plane = [&](int z) { issue_plane_at(z, (long long)wrapi(z, nz) * plane); };
+    // Stage velocity plane z (0 <= z < nz) from plane offset zo = z * plane.
+    auto issue_vel_at = [&](int z, long long zo) {
         T *dst = sv + (z & (NVS_A - 1)) * S::VPL;
 #pragma unroll
         for (int r = 0; r < RU; ++r) {
@@ -139,6 +142,7 @@ adj_kernel(const AdjArgs<T> a)
             if (e < NW) cp_async<sizeof(T)>(dst + NU + NV + e, a.w + zo + woff[r]);
         }
     };
+    auto issue_vel = [&](int z) { issue_vel_at(z, (long long)z * plane); };
 
     // gbar (3-vector) and the local term (1 - 2 phi)(sbar . n) at cell (lx, ly) of plane z.
     // The projection (I - n n^T) sbar is formed as n x (sbar x n), which is
@@ -214,15 +218,26 @@ adj_kernel(const AdjArgs<T> a)
         Tzm = Fb * (c_adv * wlo - c_dif);
     }
 
+    // Wrapped offset of the plane issued next (k+2+PF_A) and of the next
+    // velocity plane (k+PF_A), advanced by one plane per iteration.
+    int zq = wrapi(z0 + 2 + PF_A, nz);
+    long long oq = (long long)zq * plane, ov = (long long)(z0 + PF_A) * plane;
     for (int k = z0; k < z1; ++k) {
         // S1: plane k+2 and velocity plane k have landed; every thread has left
         // iteration k-1 (its reads of the slots written below, and of the gbar
         // buffer gbar_plane(k+1) writes).
         cp_async_wait<PF_A - 1>();
         __syncthreads();
-        if (k + 2 + PF_A <= z1 + 1) issue_plane(k + 2 + PF_A);
-        if (k + PF_A < z1) issue_vel(k + PF_A);
+        if (k + 2 + PF_A <= z1 + 1) issue_plane_at(k + 2 + PF_A, oq);
+        if (k + PF_A < z1) issue_vel_at(k + PF_A, ov);
         cp_async_commit();
+        if (++zq == nz) {
+            zq = 0;
+            oq = 0;
+        } else {
+            oq += plane;
+        }
+        ov += plane;
 
         T gz_p, t_p;
         gbar_plane(k + 1, gz_p, t_p);  // buffer (k+1)&1; phase C reads buffer k&1

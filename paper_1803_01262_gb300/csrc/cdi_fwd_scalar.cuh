@@ -52,6 +52,8 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
     T *const sv = reinterpret_cast<T *>(sy + 2);                          // velocity ring [NVS][VPL]
 
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    // The block is BX x BY: lets the compiler drop the bound checks of full copy rounds.
+    __builtin_assume(tx >= 0 && tx < BX && ty >= 0 && ty < BY);
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const long long plane = (long long)nx * ny;
     const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
@@ -108,8 +110,9 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
     const bool own = (x0 + tx < nx) && (y0 + ty < ny);
     const int oc = gy * nx + gx;
 
-    auto issue_plane = [&](int z) {
-        const T *src = a.phi + (long long)wrapi(z, nz) * plane;
+    // Stage phi plane z (ring slot z & (NSLOT-1)) from wrapped plane offset zo.
+    auto issue_plane_at = [&](int z, long long zo) {
+        const T *src = a.phi + zo;
         T *dst = &sp[z & (NSLOT - 1)][0][0];
 #pragma unroll
         for (int r = 0; r < NLOAD; ++r) {
@@ -135,8 +138,9 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
         const int e = tid + r * NT, ey = e / BX, ex = e - ey * BX;
         woff[r] = (e < NW) ? wrapi(y0 + ey, ny) * nx + wrapi(x0 + ex, nx) : 0;
     }
-    auto issue_vel = [&](int z) {  // 0 <= z < nz
-        const long long zo = (long long)z * plane;
+    auto issue_plane = [&](int z) { issue_plane_at(z, (long long)wrapi(z, nz) * plane); };
+    // Stage velocity plane z (0 <= z < nz) from plane offset zo = z * plane.
+    auto issue_vel_at = [&](int z, long long zo) {
         T *dst = sv + (z & (NVS - 1)) * S::VPL;
 #pragma unroll
         for (int r = 0; r < RU; ++r) {
@@ -154,6 +158,7 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
             if (e < NW) cp_async<sizeof(T)>(dst + NU + NV + e, a.w + zo + woff[r]);
         }
     };
+    auto issue_vel = [&](int z) { issue_vel_at(z, (long long)z * plane); };
 
     // Commit groups: first phi planes z0-2 .. z0+1; then PF prologue groups,
     // the d-th holding phi plane z0+2+d and velocity plane z0+d; then one group
@@ -188,14 +193,25 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
         Fzm = flux(c_adv * wlo, c_dif, c_shp, pm, pc, szm, szc);
     }
 
+    // Wrapped offset of the phi plane issued next (k+2+PF) and of the next
+    // velocity plane (k+PF), advanced by one plane per iteration.
+    int zq = wrapi(z0 + 2 + PF, nz);
+    long long oq = (long long)zq * plane, ov = (long long)(z0 + PF) * plane;
     for (int k = z0; k < z1; ++k) {
         // S1: phi plane k+2 and velocity plane k have landed, and every thread
         // has left iteration k-1 (so the slots written below are free).
         cp_async_wait<PF - 1>();
         __syncthreads();
-        if (k + 2 + PF <= z1 + 1) issue_plane(k + 2 + PF);
-        if (k + PF < z1) issue_vel(k + PF);
+        if (k + 2 + PF <= z1 + 1) issue_plane_at(k + 2 + PF, oq);
+        if (k + PF < z1) issue_vel_at(k + PF, ov);
         cp_async_commit();
+        if (++zq == nz) {
+            zq = 0;
+            oq = 0;
+        } else {
+            oq += plane;
+        }
+        ov += plane;
         T rb = T(0), rq = T(0);
         if constexpr (RK) {
             if (own) {
