@@ -66,8 +66,12 @@ struct Acc<float> {
         s = t;
         mn = fminf(mn, p);
         mx = fmaxf(mx, p);
-        ns += (p < 0.f) | (p > 1.f);
-        nt += (p < -tol) | (p > 1.f + tol);
+        // A tolerant violation is also a strict one; both are rare, so one test
+        // guards the counting (NaN fails every comparison and is not counted).
+        if (p < 0.f || p > 1.f) {
+            ++ns;
+            nt += (p < -tol) | (p > 1.f + tol);
+        }
     }
     // N values at once: their pairwise sum is added with compensation (the
     // uncompensated pairwise rounding is random and of relative size ~1e-9 on
@@ -125,8 +129,10 @@ struct Acc<double> {
         s += p;
         mn = fmin(mn, p);
         mx = fmax(mx, p);
-        ns += (p < 0.0) | (p > 1.0);
-        nt += (p < -tol) | (p > 1.0 + tol);
+        if (p < 0.0 || p > 1.0) {
+            ++ns;
+            nt += (p < -tol) | (p > 1.0 + tol);
+        }
     }
     template <int N>
     __device__ __forceinline__ void add_group(const double *o, double tol)
