@@ -25,7 +25,7 @@ CDI_EULER, CDI_RK2, CDI_RK3, CDI_RK4 = 0, 1, 2, 3
 CDI_CHECK_CONDITION = 1
 CDI_KERNEL_FORWARD, CDI_KERNEL_ADJOINT = 0, 1
 FWD_TILES = 7
-ADJ_TILES = 3
+ADJ_TILES = 4
 
 _ERRNAMES = {-1: "CDI_ERR_ARG", -2: "CDI_ERR_DIM", -3: "CDI_ERR_CUDA", -4: "CDI_ERR_CONDITION",
              -5: "CDI_ERR_NAN", -6: "CDI_ERR_TIMEOUT", -7: "CDI_ERR_STATE"}

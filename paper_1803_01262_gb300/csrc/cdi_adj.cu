@@ -21,6 +21,7 @@
 // per plane.
 #include "cdi_internal.cuh"
 #include "cdi_async.cuh"
+#include "cdi_fwd_common.cuh"
 
 namespace cdi {
 
@@ -276,16 +277,425 @@ adj_kernel(const AdjArgs<T> a)
     cp_async_wait<0>();
 }
 
+// ===========================================================================
+// Vector adjoint (nx a multiple of 16 / sizeof(T), 16-byte aligned arrays):
+// the structure of the vector forward kernel.  Each of the TX x TY own threads
+// holds a 16-byte vector of VX x-cells; two extra warps compute gbar on the
+// one-cell ring (gbar_y for the rows y0-1 and y0+H, gbar_x for the columns
+// x0-1 and x0+W) and issue every 16-byte copy of phi, lam' (5-slot rings, halo
+// 2 in y, one vector in x) and u, v, w (3-slot ring) two planes ahead of use.
+// Units are (z chunk, tile) pairs taken round-robin in chunk-major order by a
+// persistent grid; one barrier per plane (gbar_x / gbar_y double-buffered,
+// written one plane ahead; gbar_z, the local term and the z-face term carried).
+
+template <typename T, int TX, int TY>
+struct AdjVecCfg {
+    static constexpr int VX = 16 / sizeof(T);
+    static constexpr int W = TX * VX, H = TY;
+    static constexpr int NOWN = TX * TY;
+    static constexpr int NT = NOWN + 64;     // + one y-ring warp + one x-ring warp
+    static constexpr int PP = W + 2 * VX;    // row pitch of phi / lam': x0-VX .. x0+W+VX-1
+    static constexpr int PR = H + 4;         // rows y0-2 .. y0+H+1
+    static constexpr int PHI = PR * PP;
+    static constexpr int UP = W + VX;        // u row pitch: x0-VX .. x0+W-1
+    static constexpr int USZ = H * UP;
+    static constexpr int VSZ = (H + 1) * W;  // v rows: y0-1 .. y0+H-1
+    static constexpr int WSZ = H * W;
+    static constexpr int VEL = USZ + VSZ + WSZ;
+    static constexpr int SXP = W + 2 * VX;   // gbar_x pitch: x0-1 at VX-1, x0+W at VX+W
+    static constexpr int SXS = H * SXP;
+    static constexpr int SYS = (H + 2) * W;  // gbar_y rows: y0-1 .. y0+H
+    static constexpr int NSP = 5, NSV = 3;
+    static constexpr int CPHI = PHI / VX, CU = USZ / VX, CV = VSZ / VX, CW = WSZ / VX;
+    static constexpr size_t bytes =
+        sizeof(T) * (size_t)(2 * NSP * PHI + NSV * VEL + 2 * SXS + 2 * SYS);
+    static_assert(2 * TX <= 32 && 2 * TY <= 32, "ring warps hold 2*TX groups and 2*TY cells");
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(AdjVecCfg<T, TX, TY>::NT, 2)
+adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
+{
+    using C = AdjVecCfg<T, TX, TY>;
+    using VV = V16<T>;
+    constexpr int VX = C::VX, W = C::W, H = C::H, PP = C::PP, UP = C::UP, SXP = C::SXP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sphi = reinterpret_cast<T *>(smem_raw);      // [NSP][PHI]
+    T *const slam = sphi + C::NSP * C::PHI;                // [NSP][PHI]
+    T *const svel = slam + C::NSP * C::PHI;                // [NSV][VEL] = u | v | w
+    T *const sgx = svel + C::NSV * C::VEL;                 // [2][SXS]
+    T *const sgy = sgx + 2 * C::SXS;                       // [2][SYS]
+
+    const int tid = threadIdx.x;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long plane = (long long)nx * ny;
+    const int tiles_x = (nx + W - 1) / W;
+    const int ntiles = tiles_x * ((ny + H - 1) / H);
+    const int zc = (nz + nchunks - 1) / nchunks;
+    const int units = ntiles * ((nz + zc - 1) / zc);
+    const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_upd = a.c.c_upd, c_sb = a.c_shp_adj;
+    const T c_vel = a.c_vel;
+    const bool want_vel = a.gu != nullptr;
+
+    const bool is_own = tid < C::NOWN;
+    const int tx = tid % TX, ty = tid / TX;
+    const int rr = tid - C::NOWN;  // 0..63 for ring threads
+    const bool is_yring = !is_own && rr < 32 && rr < 2 * TX;
+    const bool is_xring = !is_own && rr >= 32 && rr - 32 < 2 * TY;
+    const int ry_row = (rr < TX) ? -1 : H, ry_col = rr % TX;  // y-ring group
+    const int rx_row = (rr - 32) % TY;                         // x-ring cell
+    const int rx_col = ((rr - 32) < TY) ? -1 : W;
+
+    // gbar and the local term (1 - 2 phi)(sbar . n) of the VX cells of group
+    // (gc, ly) at the plane of slot Pm (Pmm / Pmp: planes below / above; the
+    // same slots of the lam' ring).  n = g / |g| (0 where g = 0); the
+    // projection uses n x (sbar x n) (see the per-cell kernel above).
+    auto gbar_group = [&](int sm, int smm, int smp, int gc, int ly, T *b0, T *b1, T *b2, T *tl) {
+        const int off = (ly + 2) * PP + VX + gc * VX;
+        const T *Pm = sphi + sm * C::PHI, *Pmm = sphi + smm * C::PHI, *Pmp = sphi + smp * C::PHI;
+        const T *Lm = slam + sm * C::PHI, *Lmm = slam + smm * C::PHI, *Lmp = slam + smp * C::PHI;
+        T c[VX], yn[VX], yp[VX], zn[VX], zp[VX];
+        VV::ld(c, Pm + off);
+        VV::ld(yn, Pm + off - PP);
+        VV::ld(yp, Pm + off + PP);
+        VV::ld(zn, Pmm + off);
+        VV::ld(zp, Pmp + off);
+        const T L = Pm[off - 1], R = Pm[off + VX];
+        T lc[VX], lyn[VX], lyp[VX], lzn[VX], lzp[VX];
+        VV::ld(lc, Lm + off);
+        VV::ld(lyn, Lm + off - PP);
+        VV::ld(lyp, Lm + off + PP);
+        VV::ld(lzn, Lmm + off);
+        VV::ld(lzp, Lmp + off);
+        const T lL = Lm[off - 1], lR = Lm[off + VX];
+#pragma unroll
+        for (int i = 0; i < VX; ++i) {
+            const T g0 = (i + 1 < VX ? c[i + 1] : R) - (i > 0 ? c[i - 1] : L);
+            const T g1 = yp[i] - yn[i];
+            const T g2 = zp[i] - zn[i];
+            const T q = g0 * g0 + g1 * g1 + g2 * g2;
+            const T inv = q > T(0) ? rsqrt_a(q) : T(0);
+            const T sb0 = c_sb * ((i + 1 < VX ? lc[i + 1] : lR) - (i > 0 ? lc[i - 1] : lL));
+            const T sb1 = c_sb * (lyp[i] - lyn[i]);
+            const T sb2 = c_sb * (lzp[i] - lzn[i]);
+            const T n0 = g0 * inv, n1 = g1 * inv, n2 = g2 * inv;
+            const T p = c[i];
+            tl[i] = (T(1) - T(2) * p) * (sb0 * n0 + sb1 * n1 + sb2 * n2);
+            const T x0_ = sb1 * n2 - sb2 * n1;
+            const T x1_ = sb2 * n0 - sb0 * n2;
+            const T x2_ = sb0 * n1 - sb1 * n0;
+            const T wgt = p * (T(1) - p) * inv;
+            b0[i] = wgt * (n1 * x2_ - n2 * x1_);
+            b1[i] = wgt * (n2 * x0_ - n0 * x2_);
+            b2[i] = wgt * (n0 * x1_ - n1 * x0_);
+        }
+    };
+    // gbar_x only, of cell (lx, ly) (the x-ring).
+    auto gbar_x_cell = [&](int sm, int smm, int smp, int lx, int ly) {
+        const int off = (ly + 2) * PP + VX + lx;
+        const T *Pm = sphi + sm * C::PHI, *Pmm = sphi + smm * C::PHI, *Pmp = sphi + smp * C::PHI;
+        const T *Lm = slam + sm * C::PHI, *Lmm = slam + smm * C::PHI, *Lmp = slam + smp * C::PHI;
+        const T p = Pm[off];
+        const T g0 = Pm[off + 1] - Pm[off - 1];
+        const T g1 = Pm[off + PP] - Pm[off - PP];
+        const T g2 = Pmp[off] - Pmm[off];
+        const T q = g0 * g0 + g1 * g1 + g2 * g2;
+        const T inv = q > T(0) ? rsqrt_a(q) : T(0);
+        const T sb0 = c_sb * (Lm[off + 1] - Lm[off - 1]);
+        const T sb1 = c_sb * (Lm[off + PP] - Lm[off - PP]);
+        const T sb2 = c_sb * (Lmp[off] - Lmm[off]);
+        const T n0 = g0 * inv, n1 = g1 * inv, n2 = g2 * inv;
+        const T x1_ = sb2 * n0 - sb0 * n2;
+        const T x2_ = sb0 * n1 - sb1 * n0;
+        return p * (T(1) - p) * inv * (n1 * x2_ - n2 * x1_);
+    };
+
+    for (int u = blockIdx.x; u < units; u += gridDim.x) {
+        const Unit un = unit_of(u, ntiles, tiles_x, W, H, zc, nz);
+        const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
+
+        // The 64 ring threads issue every 16-byte copy; global in-plane
+        // offsets of their chunks (phi and lam' share one layout):
+        constexpr int NC = 64;
+        constexpr int RPHI = (C::CPHI + NC - 1) / NC, RU = (C::CU + NC - 1) / NC;
+        constexpr int RV = (C::CV + NC - 1) / NC, RW = (C::CW + NC - 1) / NC;
+        const int ct = tid - C::NOWN;
+        int gphi[RPHI], gu_[RU], gv_[RV], gw_[RW];
+        if (!is_own) {
+#pragma unroll
+            for (int r = 0; r < RPHI; ++r) {
+                const int e = ct + r * NC, row = e / (PP / VX), col = e - row * (PP / VX);
+                gphi[r] = wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+            }
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                const int e = ct + r * NC, row = e / (UP / VX), col = e - row * (UP / VX);
+                gu_[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+            }
+#pragma unroll
+            for (int r = 0; r < RV; ++r) {
+                const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
+                gv_[r] = wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+            }
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
+                gw_[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+            }
+        }
+        auto issue_pl = [&](int z, int slot) {
+            if (is_own) return;
+            const long long zo = (long long)wrapi(z, nz) * plane;
+            T *dp = sphi + slot * C::PHI;
+            T *dl = slam + slot * C::PHI;
+#pragma unroll
+            for (int r = 0; r < RPHI; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CPHI) {
+                    cp_async<16>(dp + e * VX, a.phi + zo + gphi[r]);
+                    cp_async<16>(dl + e * VX, a.lam + zo + gphi[r]);
+                }
+            }
+        };
+        auto issue_vel = [&](int z, int slot) {
+            if (is_own) return;
+            const long long zo = (long long)z * plane;
+            T *dst = svel + slot * C::VEL;
+#pragma unroll
+            for (int r = 0; r < RU; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CU) cp_async<16>(dst + e * VX, a.u + zo + gu_[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RV; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CV) cp_async<16>(dst + C::USZ + e * VX, a.v + zo + gv_[r]);
+            }
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                const int e = ct + r * NC;
+                if (e < C::CW) cp_async<16>(dst + C::USZ + C::VSZ + e * VX, a.w + zo + gw_[r]);
+            }
+        };
+
+        // Ring slot of plane z: (z - z0 + 2) mod 5; velocity slot: (z - z0) mod 3.
+        __syncthreads();  // the previous unit's readers are done with every slot
+        for (int d = 0; d < 5; ++d) issue_pl(z0 - 2 + d, d);  // planes z0-2 .. z0+2
+        issue_vel(z0, 0);
+        cp_async_commit();
+
+        const int own_x = x0 + tx * VX, own_y = y0 + ty;
+        const bool writes = is_own && own_x < nx && own_y < ny;
+        const long long own_off = (long long)wrapi(own_y, ny) * nx + wrapi(own_x, nx);
+        T wlo[VX];  // w on the face below plane z0 (own cells)
+        if (is_own) {
+            const T *src = a.w + (long long)wrapi(z0 - 1, nz) * plane + own_off;
+#pragma unroll
+            for (int i = 0; i < VX; ++i) wlo[i] = __ldg(src + i);
+        }
+        cp_async_wait<0>();
+        __syncthreads();
+
+        // Prologue: gbar_z at plane z0-1 (own); gbar, local term at z0 (own + ring);
+        // z-face term at z0-1/2.
+        T gzm[VX], gzc[VX], tc[VX], Tzm[VX];
+        if (is_own) {
+            T d0[VX], d1[VX], dt[VX], b0[VX], b1[VX];
+            gbar_group(1, 0, 2, tx, ty, d0, d1, gzm, dt);
+            gbar_group(2, 1, 3, tx, ty, b0, b1, gzc, tc);
+            VV::st(sgx + (z0 & 1) * C::SXS + ty * SXP + VX + tx * VX, b0);
+            VV::st(sgy + (z0 & 1) * C::SYS + (ty + 1) * W + tx * VX, b1);
+            T lm[VX], lcv[VX];
+            const int po = (ty + 2) * PP + VX + tx * VX;
+            VV::ld(lm, slam + 1 * C::PHI + po);
+            VV::ld(lcv, slam + 2 * C::PHI + po);
+#pragma unroll
+            for (int i = 0; i < VX; ++i) Tzm[i] = c_upd * (lcv[i] - lm[i]) * (c_adv * wlo[i] - c_dif);
+        } else if (is_yring) {
+            T b0[VX], b1[VX], b2[VX], t_[VX];
+            gbar_group(2, 1, 3, ry_col, ry_row, b0, b1, b2, t_);
+            VV::st(sgy + (z0 & 1) * C::SYS + (ry_row + 1) * W + ry_col * VX, b1);
+        } else if (is_xring) {
+            sgx[(z0 & 1) * C::SXS + rx_row * SXP + VX + rx_col] = gbar_x_cell(2, 1, 3, rx_col, rx_row);
+        }
+        // Plane z0+3 reuses the slot of plane z0-2, which the prologue just read.
+        __syncthreads();
+        if (z0 + 3 <= z1 + 1) issue_pl(z0 + 3, 0);
+        if (z0 + 1 < z1) issue_vel(z0 + 1, 1);
+        cp_async_commit();
+
+        int pk = 2;  // ring slot of plane k
+        int vk = 0;  // velocity slot of plane k
+        for (int k = z0; k < z1; ++k) {
+            const int pk1 = pk == 4 ? 0 : pk + 1;
+            const int pk2 = pk1 == 4 ? 0 : pk1 + 1;
+            const int pkm = pk == 0 ? 4 : pk - 1;   // also the slot of plane k+4
+            const int vk2 = vk == 0 ? 2 : vk - 1;   // slot of plane k+2
+            // S1: planes k+2 and the velocities of plane k have landed, and
+            // every thread has left iteration k-1.
+            cp_async_wait<1>();
+            __syncthreads();
+            if (k + 4 <= z1 + 1) issue_pl(k + 4, pkm);
+            if (k + 2 < z1) issue_vel(k + 2, vk2);
+            cp_async_commit();
+
+            // B: gbar at plane k+1 (buffer (k+1)&1; phase C reads buffer k&1).
+            const int b1 = (k + 1) & 1;
+            T gzp[VX], tp[VX];
+            if (is_own) {
+                T b0[VX], bb1[VX];
+                gbar_group(pk1, pk, pk2, tx, ty, b0, bb1, gzp, tp);
+                VV::st(sgx + b1 * C::SXS + ty * SXP + VX + tx * VX, b0);
+                VV::st(sgy + b1 * C::SYS + (ty + 1) * W + tx * VX, bb1);
+            } else if (is_yring) {
+                T b0[VX], bb1[VX], b2[VX], t_[VX];
+                gbar_group(pk1, pk, pk2, ry_col, ry_row, b0, bb1, b2, t_);
+                VV::st(sgy + b1 * C::SYS + (ry_row + 1) * W + ry_col * VX, bb1);
+            } else if (is_xring) {
+                sgx[b1 * C::SXS + rx_row * SXP + VX + rx_col] = gbar_x_cell(pk1, pk, pk2, rx_col, rx_row);
+            }
+
+            // C: lam at plane k.
+            if (is_own) {
+                const int b = k & 1;
+                const int po = (ty + 2) * PP + VX + tx * VX;
+                const T *Lk = slam + pk * C::PHI, *Lk1 = slam + pk1 * C::PHI;
+                T lc[VX], lyn[VX], lyp[VX], lzp[VX];
+                VV::ld(lc, Lk + po);
+                VV::ld(lyn, Lk + po - PP);
+                VV::ld(lyp, Lk + po + PP);
+                VV::ld(lzp, Lk1 + po);
+                const T lL = Lk[po - 1], lR = Lk[po + VX];
+                const T *gxr = sgx + b * C::SXS + ty * SXP + VX + tx * VX;
+                const T *gyr = sgy + b * C::SYS + (ty + 1) * W + tx * VX;
+                T gx[VX], gyn[VX], gyp[VX];
+                VV::ld(gx, gxr);
+                VV::ld(gyn, gyr - W);
+                VV::ld(gyp, gyr + W);
+                const T gxL = gxr[-1], gxR = gxr[VX];
+                const T *vel = svel + vk * C::VEL;
+                const T *ur = vel + ty * UP + VX + tx * VX;
+                const T *vr = vel + C::USZ + (ty + 1) * W + tx * VX;
+                const T *wr = vel + C::USZ + C::VSZ + ty * W + tx * VX;
+                T uc[VX], vc[VX], vn[VX], wc[VX];
+                VV::ld(uc, ur);
+                VV::ld(vc, vr);
+                VV::ld(vn, vr - W);
+                VV::ld(wc, wr);
+                const T uL = ur[-1];
+                T o[VX], fxp[VX], fyp[VX], fzp[VX];
+#pragma unroll
+                for (int i = 0; i < VX; ++i) {
+                    const T xl = i > 0 ? lc[i - 1] : lL, xr = i + 1 < VX ? lc[i + 1] : lR;
+                    const T ul = i > 0 ? uc[i - 1] : uL;
+                    const T Fxp = c_upd * (xr - lc[i]);
+                    const T Fxm = c_upd * (lc[i] - xl);
+                    const T Fyp = c_upd * (lyp[i] - lc[i]);
+                    const T Fym = c_upd * (lc[i] - lyn[i]);
+                    const T Fzp = c_upd * (lzp[i] - lc[i]);
+                    T pb = Fxp * (c_adv * uc[i] + c_dif) + Fxm * (c_adv * ul - c_dif);
+                    pb += Fyp * (c_adv * vc[i] + c_dif) + Fym * (c_adv * vn[i] - c_dif);
+                    pb += Fzp * (c_adv * wc[i] + c_dif) + Tzm[i];
+                    pb += tc[i];
+                    const T gl = i > 0 ? gx[i - 1] : gxL, gr = i + 1 < VX ? gx[i + 1] : gxR;
+                    pb += (gl - gr) + (gyn[i] - gyp[i]) + (gzm[i] - gzp[i]);
+                    o[i] = lc[i] + pb;
+                    fxp[i] = Fxp;
+                    fyp[i] = Fyp;
+                    fzp[i] = Fzp;
+                    Tzm[i] = Fzp * (c_adv * wc[i] - c_dif);
+                    gzm[i] = gzc[i];
+                    gzc[i] = gzp[i];
+                    tc[i] = tp[i];
+                }
+                if (writes) {
+                    const long long ko = (long long)k * plane + own_off;
+                    VV::st(a.out + ko, o);
+                    if (want_vel) {
+                        const T *Pk = sphi + pk * C::PHI, *Pk1 = sphi + pk1 * C::PHI;
+                        T pc[VX], pyp[VX], pzp[VX], gu0[VX], gv0[VX], gw0[VX];
+                        VV::ld(pc, Pk + po);
+                        VV::ld(pyp, Pk + po + PP);
+                        VV::ld(pzp, Pk1 + po);
+                        const T pR = Pk[po + VX];
+                        VV::ld(gu0, a.gu + ko);
+                        VV::ld(gv0, a.gv + ko);
+                        VV::ld(gw0, a.gw + ko);
+#pragma unroll
+                        for (int i = 0; i < VX; ++i) {
+                            const T pxr = i + 1 < VX ? pc[i + 1] : pR;
+                            gu0[i] += fxp[i] * c_vel * (pc[i] + pxr);
+                            gv0[i] += fyp[i] * c_vel * (pc[i] + pyp[i]);
+                            gw0[i] += fzp[i] * c_vel * (pc[i] + pzp[i]);
+                        }
+                        VV::st(a.gu + ko, gu0);
+                        VV::st(a.gv + ko, gv0);
+                        VV::st(a.gw + ko, gw0);
+                    }
+                }
+            }
+            pk = pk1;
+            vk = vk == 2 ? 0 : vk + 1;
+        }
+        cp_async_wait<0>();
+    }
+}
+
+// Adjoint tiles: 0..2 one cell per thread (32x8, 32x16, 32x4 cells, one block per tile
+// and z chunk); 3 the vector kernel (16x8 threads, persistent grid).
 struct TileDimA { int bx, by; };
 static const TileDimA kATiles[] = {{32, 8}, {32, 16}, {32, 4}};
-static const int kNumATiles = sizeof(kATiles) / sizeof(kATiles[0]);
+static const int kNumATiles = 4;
 
 int adj_num_tiles() { return kNumATiles; }
 
+bool adj_tile_is_vec(int tile) { return tile == 3; }
+
 int adj_blocks(int tile, int zchunk, int nx, int ny, int nz)
 {
+    if (adj_tile_is_vec(tile)) return 0;  // persistent grid, no scratch
     const TileDimA t = kATiles[tile];
     return ((nx + t.bx - 1) / t.bx) * ((ny + t.by - 1) / t.by) * ((nz + zchunk - 1) / zchunk);
+}
+
+void adj_vec_tile_dims(int esize, int *bw, int *bh)
+{
+    *bw = 16 * (16 / esize);
+    *bh = 8;
+}
+
+template <typename T>
+cudaError_t adj_vec_resident(int *resident)
+{
+    using C = AdjVecCfg<T, 16, 8>;
+    cudaError_t e = cudaFuncSetAttribute(adj_vec_kernel<T, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)C::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, adj_vec_kernel<T, 16, 8>, C::NT, C::bytes);
+}
+template cudaError_t adj_vec_resident<float>(int *);
+template cudaError_t adj_vec_resident<double>(int *);
+
+// Persistent grid of the vector adjoint: every resident block, at most one per unit.
+template <typename T>
+static cudaError_t launch_adj_vec(const AdjArgs<T> &a, cudaStream_t s)
+{
+    using C = AdjVecCfg<T, 16, 8>;
+    int resident = 0, dev = 0, sms = 0;
+    cudaError_t e;
+    if ((e = adj_vec_resident<T>(&resident)) != cudaSuccess) return e;
+    if (resident < 1) return cudaErrorInvalidConfiguration;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const int nchunks = (a.nz + a.zchunk - 1) / a.zchunk;
+    const int zc = (a.nz + nchunks - 1) / nchunks;
+    const long long units = (long long)((a.nx + C::W - 1) / C::W) * ((a.ny + C::H - 1) / C::H) *
+                            ((a.nz + zc - 1) / zc);
+    long long nb = (long long)resident * sms;
+    if (nb > units) nb = units;
+    adj_vec_kernel<T, 16, 8><<<(int)nb, C::NT, C::bytes, s>>>(a, nchunks);
+    return cudaGetLastError();
 }
 
 template <typename T, int BX, int BY>
@@ -312,6 +722,7 @@ cudaError_t launch_adj(const AdjArgs<T> &a, int tile, cudaStream_t s)
     case 0: return launch_adj_t<T, 32, 8>(a, s);
     case 1: return launch_adj_t<T, 32, 16>(a, s);
     case 2: return launch_adj_t<T, 32, 4>(a, s);
+    case 3: return launch_adj_vec<T>(a, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -164,10 +164,50 @@ static int default_fwd_tile(const cdi_grid *g)
     return (g->nx >= 32 && g->ny >= 16) ? 1 : 3;
 }
 
-// Adjoint launch: z chunk giving about eight blocks per SM.
+// Vector adjoint: z chunking from the forward cost model (rounds of the
+// persistent grid against per-unit prologues).
+static int adj_vec_zchunk(const cdi_grid *g)
+{
+    int resident = 0;
+    cudaError_t e = g->dtype == CDI_F64 ? cdi::adj_vec_resident<double>(&resident)
+                                        : cdi::adj_vec_resident<float>(&resident);
+    if (e != cudaSuccess || resident < 1) resident = 1;
+    int bw, bh;
+    cdi::adj_vec_tile_dims((int)esize(g), &bw, &bh);
+    const long long G = (long long)resident * g->sm_count;
+    const long long tiles = (long long)((g->nx + bw - 1) / bw) * ((g->ny + bh - 1) / bh);
+    const int nz = g->nz;
+    double best = 1e300;
+    int nch = 1;
+    for (int nc = 1; nc <= nz; ++nc) {
+        const int zc = (nz + nc - 1) / nc;
+        if (nc > 1 && zc == (nz + nc - 2) / (nc - 1)) continue;
+        const long long units = tiles * ((nz + zc - 1) / zc);
+        const double rounds = (double)((units + G - 1) / G);
+        const double cost = fmax(rounds * (zc + 3.0), (double)units * (zc + 1.0) / (double)G);
+        if (cost < best * (1.0 - 1e-9)) {
+            best = cost;
+            nch = nc;
+        }
+    }
+    return (nz + nch - 1) / nch;
+}
+
+static bool adj_vec_eligible(const cdi_grid *g) { return g->nx % (16 / (int)esize(g)) == 0; }
+
+// Adjoint launch: the vector kernel where nx allows it (and the box is wide enough
+// for its 16-byte tiles); else a one-cell-per-thread tile with a z chunk giving
+// about eight blocks per SM.
 static LaunchCfg adj_default(const cdi_grid *g)
 {
     LaunchCfg c;
+    if (adj_vec_eligible(g) && g->nx >= 48) {
+        c.tile = 3;
+        c.zchunk = adj_vec_zchunk(g);
+        c.nblocks = 0;
+        c.nchunks = 0;
+        return c;
+    }
     c.tile = (g->nx >= 32 && g->ny >= 16) ? 1 : 2;
     const int bx = 32, by = c.tile == 1 ? 16 : 4;
     long long tiles = (long long)((g->nx + bx - 1) / bx) * ((g->ny + by - 1) / by);
@@ -733,7 +773,10 @@ int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchu
             return CDI_OK;
         }
         if (tile >= cdi::adj_num_tiles()) return fail(CDI_ERR_ARG, "adjoint tile %d out of range", tile);
+        if (cdi::adj_tile_is_vec(tile) && !adj_vec_eligible(g))
+            return fail(CDI_ERR_ARG, "vector adjoint tile needs nx %% %d == 0", 16 / (int)esize(g));
         LaunchCfg c = adj_default(g);
+        if (cdi::adj_tile_is_vec(tile) && !cdi::adj_tile_is_vec(c.tile)) c.zchunk = adj_vec_zchunk(g);
         c.tile = tile;
         if (nchunks > 0) c.zchunk = (g->nz + nchunks - 1) / nchunks;
         if (cdi::adj_blocks(c.tile, c.zchunk, g->nx, g->ny, g->nz) > g->capacity)

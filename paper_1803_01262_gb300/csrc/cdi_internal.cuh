@@ -126,6 +126,11 @@ cudaError_t launch_adj(const AdjArgs<T> &a, int tile, cudaStream_t s);
 
 int adj_num_tiles();
 int adj_blocks(int tile, int zchunk, int nx, int ny, int nz);
+// Tile 3: vector adjoint (nx % (16/sizeof(T)) == 0), tile W x H cells, persistent grid.
+bool adj_tile_is_vec(int tile);
+void adj_vec_tile_dims(int esize, int *bw, int *bh);
+template <typename T>
+cudaError_t adj_vec_resident(int *resident);
 
 // Record a message for cdi_last_error_string() and return code (cdi_api.cu).
 int set_error(int code, const char *fmt, ...);

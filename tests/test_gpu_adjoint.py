@@ -54,6 +54,42 @@ def test_adjoint_parity(dtype, shape, with_vel):
             assert np.abs(gd.double().cpu().numpy() - (base + rg)).max() <= tol * s2 * 4
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("tile", range(cdi.ADJ_TILES))
+@pytest.mark.parametrize("shape,nchunks", [((9, 21, 68), 0), ((1, 40, 128), 1), ((3, 10, 8), 2),
+                                           ((6, 13, 96), 3), ((20, 9, 64), 7), ((2, 17, 132), 0)])
+@pytest.mark.parametrize("with_vel", [False, True])
+def test_adjoint_every_tile(dtype, tile, shape, nchunks, with_vel):
+    """Each adjoint kernel (one cell per thread, and the vector kernel where nx allows)
+    and z chunking gives the oracle's adjoint step, ragged tiles and chunks included."""
+    phi, u, v, w, lam, h = case(shape, 11 + shape[2], dtype == torch.float32)
+    t = np.float64 if dtype == torch.float64 else np.float32
+    phi, u, v, w, lam = (np.asarray(x, t).astype(np.float64) for x in (phi, u, v, w, lam))
+    dt, eps, gamma, vs = 0.15 * h * h / (1.3 * 1.1 * h), 1.1 * h, 1.3, 0.7
+    nz, ny, nx = shape
+    g = cdi.Grid(nx, ny, nz, h, dtype)
+    g.set_velocity(*[dev(x, dtype) for x in (u, v, w)])
+    g.set_launch(cdi.CDI_KERNEL_ADJOINT, tile, 0, nchunks)
+    assert g.get_launch(cdi.CDI_KERNEL_ADJOINT)["tile"] == tile
+    out = torch.empty(shape, dtype=dtype, device="cuda")
+    grads = None
+    if with_vel:
+        g0 = np.random.default_rng(5).standard_normal((3,) + shape)
+        grads = [dev(x, dtype) for x in g0]
+    g.step_adjoint(dev(phi, dtype), dev(lam, dtype), out, dt, eps, gamma, vs, grads=grads)
+    ref = oracle.adjoint(phi, u, v, w, lam, h, dt, eps, gamma, vs, want_vel=with_vel)
+    if with_vel:
+        ref, rgu, rgv, rgw = ref
+    scale = max(1.0, np.abs(ref).max())
+    tol = 1e-12 if dtype == torch.float64 else 2e-6
+    assert np.abs(out.double().cpu().numpy() - ref).max() <= tol * scale
+    if with_vel:
+        for gd, rg, base in zip(grads, (rgu, rgv, rgw), g0):
+            base = np.asarray(base, t).astype(np.float64)
+            s2 = max(1.0, np.abs(rg).max())
+            assert np.abs(gd.double().cpu().numpy() - (base + rg)).max() <= tol * s2 * 4
+
+
 def test_adjoint_constant_lambda_gpu():
     """lam' = const gives lam = lam' exactly (J^T 1 = 1 from conservation)."""
     shape = (6, 10, 40)
