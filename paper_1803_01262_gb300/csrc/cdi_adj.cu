@@ -312,8 +312,10 @@ struct AdjVecCfg {
     static_assert(2 * TX <= 32 && 2 * TY <= 32, "ring warps hold 2*TX groups and 2*TY cells");
 };
 
+// Three FP32 blocks per SM (113 registers) measured 8% faster than two; FP64
+// keeps two (it would spill at three).
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(AdjVecCfg<T, TX, TY>::NT, 2)
+__global__ void __launch_bounds__(AdjVecCfg<T, TX, TY>::NT, sizeof(T) == 4 ? 3 : 2)
 adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
 {
     using C = AdjVecCfg<T, TX, TY>;
