@@ -45,11 +45,11 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             i, d = ctypes.c_int, ctypes.c_double
-            lib.oracle_rhs.argtypes = [i, i, i, d, _D, _D, _D, _D, d, d, d, _D]
-            lib.oracle_step.argtypes = [i, i, i, d, _D, _D, _D, _D, d, d, d, d, _D]
+            lib.oracle_rhs.argtypes = [i, i, i, d, _D, _D, _D, _D, d, d, d, d, _D]
+            lib.oracle_step.argtypes = [i, i, i, d, _D, _D, _D, _D, d, d, d, d, d, _D]
             lib.oracle_stats.argtypes = [ctypes.c_long, _D, d, d, _D,
                                          ctypes.POINTER(ctypes.c_longlong)]
-            lib.oracle_adjoint.argtypes = [i, i, i, d, _D, _D, _D, _D, _D, d, d, d, d,
+            lib.oracle_adjoint.argtypes = [i, i, i, d, _D, _D, _D, _D, _D, d, d, d, d, d,
                                            _D, _D, _D, _D]
             for f in (lib.oracle_rhs, lib.oracle_step, lib.oracle_stats, lib.oracle_adjoint):
                 f.restype = ctypes.c_int
@@ -72,37 +72,44 @@ def _check(phi, u, v, w):
     return phi, u, v, w
 
 
-def rhs(phi, u, v, w, dx, eps, gamma, vel_scale=1.0):
-    """d phi/dt of Eq. 1 discretised by the five steps of Section 2.2."""
+def floor_of(dtype) -> float:
+    """The floor under |g|^2 of a step computed in ``dtype``: its smallest
+    normal number (FLT_MIN, DBL_MIN).  0 gives the paper's unit normal."""
+    return float(np.finfo(dtype).tiny)
+
+
+def rhs(phi, u, v, w, dx, eps, gamma, vel_scale=1.0, tiny=0.0):
+    """d phi/dt of Eq. 1 discretised by the five steps of Section 2.2; the
+    normal is g / sqrt(|g|^2 + tiny) (0 where g = 0)."""
     phi, u, v, w = _check(phi, u, v, w)
     nz, ny, nx = phi.shape
     out = np.empty_like(phi)
     rc = _load().oracle_rhs(nx, ny, nz, dx, _p(phi), _p(u), _p(v), _p(w), eps, gamma,
-                            vel_scale, _p(out))
+                            vel_scale, tiny, _p(out))
     if rc:
         raise ValueError("oracle_rhs: bad arguments")
     return out
 
 
-def step(phi, u, v, w, dx, dt, eps, gamma, vel_scale=1.0):
+def step(phi, u, v, w, dx, dt, eps, gamma, vel_scale=1.0, tiny=0.0):
     """One explicit Euler step of the CDI equation (Eq. 11 generalised to 3D)."""
     phi, u, v, w = _check(phi, u, v, w)
     nz, ny, nx = phi.shape
     out = np.empty_like(phi)
     rc = _load().oracle_step(nx, ny, nz, dx, _p(phi), _p(u), _p(v), _p(w), dt, eps,
-                             gamma, vel_scale, _p(out))
+                             gamma, vel_scale, tiny, _p(out))
     if rc:
         raise ValueError("oracle_step: bad arguments")
     return out
 
 
-def run(phi, u, v, w, dx, dt, eps, gamma, nsteps, period=0.0, t0=0.0):
+def run(phi, u, v, w, dx, dt, eps, gamma, nsteps, period=0.0, t0=0.0, tiny=0.0):
     """nsteps Euler steps; velocity scaled by cos(pi t / period) when period > 0."""
     p = _f64(phi)
     t = t0
     for _ in range(nsteps):
         s = np.cos(np.pi * t / period) if period > 0 else 1.0
-        p = step(p, u, v, w, dx, dt, eps, gamma, s)
+        p = step(p, u, v, w, dx, dt, eps, gamma, s, tiny)
         t += dt
     return p
 
@@ -140,20 +147,20 @@ def rk_advance(f, phi, t, dt, scheme):
     raise ValueError(scheme)
 
 
-def rk_step(phi, u, v, w, dx, dt, eps, gamma, scheme, t=0.0, period=0.0):
+def rk_step(phi, u, v, w, dx, dt, eps, gamma, scheme, t=0.0, period=0.0, tiny=0.0):
     """One RK step of the CDI equation; velocity scaled by cos(pi t/period) at each stage time."""
     phi, u, v, w = _check(phi, u, v, w)
 
     def f(p, tt):
         s = np.cos(np.pi * tt / period) if period > 0 else 1.0
-        return rhs(p, u, v, w, dx, eps, gamma, s)
+        return rhs(p, u, v, w, dx, eps, gamma, s, tiny)
     return rk_advance(f, phi, t, dt, scheme)
 
 
-def rk_run(phi, u, v, w, dx, dt, eps, gamma, nsteps, scheme, period=0.0, t0=0.0):
+def rk_run(phi, u, v, w, dx, dt, eps, gamma, nsteps, scheme, period=0.0, t0=0.0, tiny=0.0):
     p = _f64(phi)
     for i in range(nsteps):
-        p = rk_step(p, u, v, w, dx, dt, eps, gamma, scheme, t0 + i * dt, period)
+        p = rk_step(p, u, v, w, dx, dt, eps, gamma, scheme, t0 + i * dt, period, tiny)
     return p
 
 
@@ -167,15 +174,18 @@ def stats(phi, dV, tol):
     return dict(mass=o[0], sum=o[1], min=o[2], max=o[3], n_strict=int(c[0]), n_tol=int(c[1]))
 
 
-def adjoint(phi, u, v, w, lam_next, dx, dt, eps, gamma, vel_scale=1.0, want_vel=False):
-    """Discrete adjoint of one Euler step: returns lam (and velocity gradients)."""
+def adjoint(phi, u, v, w, lam_next, dx, dt, eps, gamma, vel_scale=1.0, want_vel=False,
+            tiny=0.0):
+    """Discrete adjoint of one Euler step (of :func:`step` with the same
+    ``tiny``): returns lam (and velocity gradients)."""
     phi, u, v, w = _check(phi, u, v, w)
     lam_next = _f64(lam_next)
     nz, ny, nx = phi.shape
     lam = np.empty_like(phi)
     g = [np.zeros_like(phi) for _ in range(3)] if want_vel else [None] * 3
     rc = _load().oracle_adjoint(nx, ny, nz, dx, _p(phi), _p(u), _p(v), _p(w), _p(lam_next),
-                                dt, eps, gamma, vel_scale, _p(lam), _p(g[0]), _p(g[1]), _p(g[2]))
+                                dt, eps, gamma, vel_scale, tiny, _p(lam), _p(g[0]), _p(g[1]),
+                                _p(g[2]))
     if rc:
         raise ValueError("oracle_adjoint: bad arguments")
     return (lam, *g) if want_vel else lam

@@ -23,6 +23,11 @@
  *     ((phi_{i-1})^2 - phi_{i-1}) n_{i-1}, as Eq. 13 and Eq. 16 require;
  *   - the normal is 0 where the central-difference gradient is exactly 0
  *     (the paper divides by |grad phi| without a guard);
+ *   - every entry point takes a floor tiny >= 0 under the root,
+ *     n = g / sqrt(|g|^2 + tiny) for g != 0: tiny = 0 is the paper's
+ *     unit normal, tiny = the smallest normal number of a working precision
+ *     is the regularised normal a finite-precision step divides by (it only
+ *     matters where |g|^2 falls to that number);
  *   - the 1/(2dx) of the central gradient cancels in n = g/|g|, so g is the
  *     plain difference phi_{c+e} - phi_{c-e};
  *   - velocities are face values u[k][j][i] = u_{i+1/2,j,k} (right face),
@@ -54,9 +59,10 @@ static long nb(long i, long j, long k, int d, long s, long nx, long ny, long nz)
     return at(i, j, k + s, nx, ny, nz);
 }
 
-/* Step 1: cell-centre normals n = g/|g|, g_d = phi_{c+e_d} - phi_{c-e_d};
- * n = 0 where |g| = 0.  Also returns |g| (needed by the adjoint). */
-static void normals(long nx, long ny, long nz, const double *phi,
+/* Step 1: cell-centre normals n = g/m, m = sqrt(|g|^2 + tiny),
+ * g_d = phi_{c+e_d} - phi_{c-e_d}; n = 0 where g = 0.  Also returns m (needed
+ * by the adjoint; 0 where g = 0). */
+static void normals(long nx, long ny, long nz, const double *phi, double tiny,
                     double *n0, double *n1, double *n2, double *gmag)
 {
     for (long k = 0; k < nz; k++)
@@ -69,7 +75,7 @@ static void normals(long nx, long ny, long nz, const double *phi,
                 double g2 = g[0] * g[0];
                 g2 = g2 + g[1] * g[1];
                 g2 = g2 + g[2] * g[2];
-                double m = sqrt(g2);
+                double m = g2 > 0.0 ? sqrt(g2 + tiny) : 0.0;
                 gmag[c] = m;
                 if (m > 0.0) {
                     n0[c] = g[0] / m; n1[c] = g[1] / m; n2[c] = g[2] / m;
@@ -82,7 +88,7 @@ static void normals(long nx, long ny, long nz, const double *phi,
 /* Steps 1-4: face fluxes F_d[c] on the face c + 1/2 e_d for every cell c. */
 static void face_fluxes(long nx, long ny, long nz, double dx, const double *phi,
                         const double *u, const double *v, const double *w,
-                        double eps, double gamma, double vel_scale,
+                        double eps, double gamma, double vel_scale, double tiny,
                         double *F0, double *F1, double *F2)
 {
     long n = nx * ny * nz;
@@ -92,7 +98,7 @@ static void face_fluxes(long nx, long ny, long nz, double dx, const double *phi,
         s[d] = (double *)malloc(sizeof(double) * n);
     }
     gm = (double *)malloc(sizeof(double) * n);
-    normals(nx, ny, nz, phi, nrm[0], nrm[1], nrm[2], gm);
+    normals(nx, ny, nz, phi, tiny, nrm[0], nrm[1], nrm[2], gm);
 
     /* Step 2a: sharpening term at cell centres. */
     for (long c = 0; c < n; c++)
@@ -124,13 +130,14 @@ static void face_fluxes(long nx, long ny, long nz, double dx, const double *phi,
 /* d phi / dt = -(1/dx) sum_d (F_{c+1/2 e_d} - F_{c-1/2 e_d})  (Step 5, divergence). */
 ORACLE_API int oracle_rhs(int nx, int ny, int nz, double dx, const double *phi,
                           const double *u, const double *v, const double *w,
-                          double eps, double gamma, double vel_scale, double *rhs)
+                          double eps, double gamma, double vel_scale, double tiny,
+                          double *rhs)
 {
-    if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0.0)) return -1;
+    if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0.0) || !(tiny >= 0.0)) return -1;
     long n = (long)nx * ny * nz;
     double *F[3];
     for (int d = 0; d < 3; d++) F[d] = (double *)malloc(sizeof(double) * n);
-    face_fluxes(nx, ny, nz, dx, phi, u, v, w, eps, gamma, vel_scale, F[0], F[1], F[2]);
+    face_fluxes(nx, ny, nz, dx, phi, u, v, w, eps, gamma, vel_scale, tiny, F[0], F[1], F[2]);
     for (long k = 0; k < nz; k++)
         for (long j = 0; j < ny; j++)
             for (long i = 0; i < nx; i++) {
@@ -148,12 +155,12 @@ ORACLE_API int oracle_rhs(int nx, int ny, int nz, double dx, const double *phi,
 ORACLE_API int oracle_step(int nx, int ny, int nz, double dx, const double *phi,
                            const double *u, const double *v, const double *w,
                            double dt, double eps, double gamma, double vel_scale,
-                           double *phi_out)
+                           double tiny, double *phi_out)
 {
     long n = (long)nx * ny * nz;
     if (nx < 1 || ny < 1 || nz < 1) return -1;
     double *r = (double *)malloc(sizeof(double) * n);
-    int rc = oracle_rhs(nx, ny, nz, dx, phi, u, v, w, eps, gamma, vel_scale, r);
+    int rc = oracle_rhs(nx, ny, nz, dx, phi, u, v, w, eps, gamma, vel_scale, tiny, r);
     if (rc == 0)
         for (long c = 0; c < n; c++) phi_out[c] = phi[c] + dt * r[c];
     free(r);
@@ -193,17 +200,18 @@ ORACLE_API int oracle_stats(long n, const double *phi, double dV, double tol,
  *   ubar_f += Fbar vel_scale (phi_L + phi_R)/2
  *   phibar_c += sum_d sbar_d (1 - 2 phi_c) n_d                 (Step 2a)
  *   nbar_d = sbar_d phi_c (1 - phi_c)
- *   gbar = (nbar - n (n . nbar)) / |g|   (0 where |g| = 0)      (Step 1)
+ *   gbar = (nbar - n (n . nbar)) / m   (0 where g = 0)          (Step 1)
+ *     the derivative of n = g / m, m = sqrt(|g|^2 + tiny): dn/dg = (I - n n^T)/m
  *   phibar_{c+e_d} += gbar_d, phibar_{c-e_d} -= gbar_d
  *   lam_out = lam_next + phibar.
  */
 ORACLE_API int oracle_adjoint(int nx, int ny, int nz, double dx, const double *phi,
                               const double *u, const double *v, const double *w,
                               const double *lam_next, double dt, double eps,
-                              double gamma, double vel_scale, double *lam_out,
+                              double gamma, double vel_scale, double tiny, double *lam_out,
                               double *gu, double *gv, double *gw)
 {
-    if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0.0)) return -1;
+    if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0.0) || !(tiny >= 0.0)) return -1;
     long n = (long)nx * ny * nz;
     double *nrm[3], *sbar[3], *gm, *pbar;
     for (int d = 0; d < 3; d++) {
@@ -212,7 +220,7 @@ ORACLE_API int oracle_adjoint(int nx, int ny, int nz, double dx, const double *p
     }
     gm = (double *)malloc(sizeof(double) * n);
     pbar = (double *)calloc(n, sizeof(double));
-    normals(nx, ny, nz, phi, nrm[0], nrm[1], nrm[2], gm);
+    normals(nx, ny, nz, phi, tiny, nrm[0], nrm[1], nrm[2], gm);
 
     const double *vel[3] = {u, v, w};
     double *gvel[3] = {gu, gv, gw};

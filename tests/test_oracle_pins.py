@@ -21,7 +21,7 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 AX = (2, 1, 0)  # array axis of x, y, z
 
 
-def coefficient_form_step(phi, u, v, w, dx, dt, eps, gamma):
+def coefficient_form_step(phi, u, v, w, dx, dt, eps, gamma, sharpen=True):
     """Eq. 18-22 (and Eq. 13 in 1D), written for 3D: phi' = sum C phi.
 
     C_c = 1 - 2 D A - (B A / gamma) sum_d (u^d_{c+1/2} - u^d_{c-1/2})   (Eq. 19, D = 3
@@ -34,7 +34,7 @@ def coefficient_form_step(phi, u, v, w, dx, dt, eps, gamma):
     g = [np.roll(phi, -1, a) - np.roll(phi, 1, a) for a in AX]
     m = np.sqrt(g[0] ** 2 + g[1] ** 2 + g[2] ** 2)
     safe = np.where(m > 0, m, 1.0)
-    n = [np.where(m > 0, gd / safe, 0.0) for gd in g]
+    n = [np.where((m > 0) & sharpen, gd / safe, 0.0) for gd in g]
     vel = (u, v, w)
     Cc = 1 - 6 * A - (B * A / gamma) * sum(vel[d] - np.roll(vel[d], 1, AX[d]) for d in range(3))
     out = Cc * phi
@@ -79,6 +79,38 @@ def test_coefficient_form(shape, solenoidal):
     assert np.abs(a - b).max() < 2e-15
 
 
+F32_TINY, F64_TINY = 1.17549435e-38, 2.2250738585072014e-308
+
+
+@pytest.mark.parametrize("shape", [(1, 9, 11), (5, 6, 7)])
+def test_floor_invisible_at_working_scale(shape):
+    """The floor under |g|^2 is invisible wherever |g|^2 is far above it: DBL_MIN
+    changes no bit of a step or an adjoint on O(1) fields, FLT_MIN changes no
+    value by more than a few ulps."""
+    phi, u, v, w, h = rand_case(shape, 12)
+    lam = np.random.default_rng(2).standard_normal(shape)
+    args = dict(dx=h, dt=0.2 * h * h, eps=h, gamma=1.1, vel_scale=0.9)
+    base = oracle.step(phi, u, v, w, **args)
+    assert np.array_equal(oracle.step(phi, u, v, w, tiny=F64_TINY, **args), base)
+    assert np.abs(oracle.step(phi, u, v, w, tiny=F32_TINY, **args) - base).max() < 1e-15
+    abase = oracle.adjoint(phi, u, v, w, lam, **args)
+    assert np.array_equal(oracle.adjoint(phi, u, v, w, lam, tiny=F64_TINY, **args), abase)
+    assert np.abs(oracle.adjoint(phi, u, v, w, lam, tiny=F32_TINY, **args) - abase).max() < 1e-14
+
+
+@pytest.mark.parametrize("solenoidal", [True, False])
+def test_floor_above_gradient_removes_sharpening(solenoidal):
+    """A floor far above |g|^2 shrinks the normal to ~g/sqrt(tiny) -> 0: the step becomes
+    the sharpening-free advection-diffusion step of Eq. 18-22 (all n = 0); a floor
+    placed anywhere but under the root (e.g. on the numerator) fails this."""
+    phi, u, v, w, h = rand_case((4, 5, 6), 13, solenoidal)
+    dt, eps, gamma = 0.3 * h * h, 1.2 * h, 0.8
+    a = oracle.step(phi, u, v, w, h, dt, eps, gamma, tiny=1e40)
+    b = coefficient_form_step(phi, u, v, w, h, dt, eps, gamma, sharpen=False)
+    assert np.abs(a - b).max() < 2e-15
+    assert np.abs(a - coefficient_form_step(phi, u, v, w, h, dt, eps, gamma)).max() > 1e-4
+
+
 def test_eq11_1d():
     """ny = nz = 1 reduces exactly to the printed 1D scheme (Eq. 11)."""
     n, h = 40, 1.0 / 40
@@ -112,6 +144,10 @@ def test_symmetry_eq16(shape):
     args = (u, v, w, h, 0.2 * h * h, h, 1.0)
     a = oracle.step(1 - phi, *args)
     b = 1 - oracle.step(phi, *args)
+    assert np.abs(a - b).max() < 1e-15
+    # the floor keeps the symmetry (|g| is even under phi -> 1 - phi)
+    a = oracle.step(1 - phi, *args, tiny=1e-3)
+    b = 1 - oracle.step(phi, *args, tiny=1e-3)
     assert np.abs(a - b).max() < 1e-15
 
 
@@ -348,6 +384,27 @@ def test_adjoint_dot_product(shape):
     jt = oracle.adjoint(phi, u, v, w, lam, **args)
     lhs, rhs = (jv * lam).sum(), (dphi * jt).sum()
     assert abs(lhs - rhs) <= 1e-7 * (abs(lhs) + abs(rhs))
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 12), (4, 5, 6)])
+def test_adjoint_dot_product_with_floor(shape):
+    """With the floor of the same size as |g|^2 (so that n = g/sqrt(|g|^2 + tiny) is far
+    from a unit vector) the adjoint is still the transpose of the step's Jacobian."""
+    rng = np.random.default_rng(17)
+    phi, u, v, w, h = rand_case(shape, 22)
+    phi = 0.1 + 0.8 * I.random_phi(shape, 5, smooth=True)
+    g2 = sum((np.roll(phi, -1, a) - np.roll(phi, 1, a)) ** 2 for a in AX)
+    tiny = float(np.median(g2))
+    args = dict(dx=h, dt=0.2 * h * h, eps=1.2 * h, gamma=1.3, vel_scale=0.8, tiny=tiny)
+    lam = rng.standard_normal(shape)
+    dphi = rng.standard_normal(shape)
+    jv = _fd_jvp(phi, u, v, w, dphi, args)
+    jt = oracle.adjoint(phi, u, v, w, lam, **args)
+    lhs, rhs = (jv * lam).sum(), (dphi * jt).sum()
+    assert abs(lhs - rhs) <= 1e-7 * (abs(lhs) + abs(rhs))
+    # and the floor matters here: the unit-normal adjoint differs
+    jt0 = oracle.adjoint(phi, u, v, w, lam, **{**args, "tiny": 0.0})
+    assert abs((dphi * jt0).sum() - rhs) > 1e-4 * abs(rhs)
 
 
 def test_adjoint_brute_force_transpose():
