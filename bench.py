@@ -197,6 +197,62 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def inverse_512(dev, iters=3):
+    """Sphere-parameter inverse problem at 512^3, FP32: 200 steps, checkpoint every 16.
+
+    Velocity: 32-mode random divergence-free field (kmax 4, seed 7), eps = dx,
+    gamma = U, dt = 0.1 dx / U.  Target: the rollout of the sphere (0.5, 0.5,
+    0.5, R 0.2); start: (0.52, 0.485, 0.51, R 0.18).  One untimed gradient, then
+    ``iters`` timed Adam iterations (each: 200 forward steps, the checkpoint
+    recompute, 200 adjoint steps).  dL/dR is checked against a central
+    difference of the FP32 rollout.
+    """
+    import torch
+    from paper_1803_01262_gb300 import autograd as AG
+    from paper_1803_01262_gb300 import cdi
+    from paper_1803_01262_gb300 import inputs as I
+    n, nst, ck = 512, 200, 16
+    h = 1.0 / n
+    vel = [x.to(torch.float32).contiguous() for x in I.random_velocity_torch((n, n, n), h, 32, 4, 7, device=dev)]
+    g = cdi.Grid(n, n, n, h, torch.float32)
+    g.set_velocity(*vel)
+    eps, gamma = h, g.U
+    dt = 0.1 * h / g.U
+    true = torch.tensor([0.5, 0.5, 0.5, 0.2], dtype=torch.float64, device=dev)
+    init = torch.tensor([0.52, 0.485, 0.51, 0.18], dtype=torch.float64, device=dev)
+
+    def roll(th):
+        return AG.rollout(AG.sphere_phi(th, g.shape, h, eps).float().contiguous(), *vel, g, nst, dt, eps,
+                          gamma, ckpt_every=ck)
+    with torch.no_grad():
+        target = roll(true).detach()
+
+    def loss(th):
+        return ((roll(th).double() - target.double()) ** 2).sum() * h ** 3
+    th = init.clone().requires_grad_(True)
+    loss(th).backward()   # untimed: allocator warm-up
+    grad = th.grad.detach().cpu().tolist()
+    with torch.no_grad():
+        dR = 2e-3
+        e = torch.tensor([0, 0, 0, dR], dtype=torch.float64, device=dev)
+        fd = (float(loss(init + e)) - float(loss(init - e))) / (2 * dR)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    theta, losses = AG.inverse_problem(target, *vel, g, nst, dt, eps, gamma, init, iters=iters, lr=5e-3,
+                                       ckpt_every=ck)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    out = {"workload": "sphere inverse problem 512^3 FP32, 32-mode random velocity, 200 steps, "
+                       "checkpoint every 16, Adam on (cx, cy, cz, R)",
+           "ms_per_gradient": el / iters * 1e3, "iters": iters,
+           "steps_per_gradient": {"forward": nst, "adjoint": nst,
+                                  "recompute": sum(min(s + ck, nst) - s - 1 for s in range(0, nst, ck))},
+           "losses": losses, "theta": theta.cpu().tolist(),
+           "grad_at_start": grad, "fd_dL_dR": fd, "grad_rel_err_R": abs(grad[3] - fd) / abs(fd)}
+    del g, vel, target
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -409,6 +465,11 @@ def main():
                "frac": BYTES_F32 * 512 ** 3 / (avg_big * 1e-3) / 1e9 / peak}
         del gb, vb, ab, bb, buf
 
+    # ---- inverse problem through the adjoint, 512^3 ----
+    inverse = None
+    if not args.no_extra:
+        inverse = inverse_512(dev)
+
     line = None
     if rank == 0:
         cpu = None
@@ -448,6 +509,7 @@ def main():
                         "achieved_gbs": BYTES_ADJ_F32 * cells / (avg_adj * 1e-3) / 1e9},
             "batch": batch,
             "size_512": big,
+            "inverse_512": inverse,
             "stats_last_step": {"mass": st["mass"], "min": st["min"], "max": st["max"],
                                 "n_tol": st["n_tol"]},
             "clocks": clocks,

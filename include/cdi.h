@@ -193,6 +193,17 @@ CDI_API int cdi_step_host(cdi_grid *g, const void *phi_in_host, void *phi_out_ho
  * them (accumulated over steps by the caller).  phi_k is the forward input
  * of the step (recomputed by the caller from a checkpoint).  lam_k must not
  * overlap lam_next or phi_k.  Same dt/eps/gamma/vel_scale as the forward.
+ *
+ * J is taken with the interface normal n = g / sqrt(|g|^2 + delta^2)
+ * (g the central difference of phi; n = 0 where g = 0), delta = 8 machine
+ * epsilons of the working precision (2^-20 in FP32, 2^-49 in FP64, i.e.
+ * 16 units in the last place of values just below 1).  Where |g| is far
+ * above delta -- every interface cell -- this is the derivative of the
+ * forward step.  Where |g| falls to the rounding level of phi (the flat
+ * bulk next to phi = 1 or 0, where neighbours differ by a unit or two in the
+ * last place) the unit normal is rounding noise and its derivative
+ * phi (1 - phi)/|g| is unbounded; the floor caps it, which keeps the
+ * backward recursion of long rollouts from amplifying that noise.
  */
 CDI_API int cdi_step_adjoint(cdi_grid *g, const void *phi_k, const void *lam_next, void *lam_k,
                      void *gu, void *gv, void *gw, double dt, double eps, double gamma,

@@ -78,6 +78,17 @@ def floor_of(dtype) -> float:
     return float(np.finfo(dtype).tiny)
 
 
+def adjoint_floor_of(dtype) -> float:
+    """The floor under |g|^2 that the backward pass of a ``dtype`` step takes:
+    (8 machine epsilons)^2, i.e. delta = 16 units in the last place of values
+    just below 1.  The forward step divides by |g| (its floor, ``floor_of``,
+    is invisible); the adjoint differentiates n = g / sqrt(|g|^2 + delta^2),
+    which is the same wherever |g| >> delta and caps the normal's derivative
+    phi (1 - phi)/|g| where g is at the rounding level of phi.  (The paper
+    has no adjoint; this is the reading taken for it.)"""
+    return float((8.0 * np.finfo(dtype).eps) ** 2)
+
+
 def rhs(phi, u, v, w, dx, eps, gamma, vel_scale=1.0, tiny=0.0):
     """d phi/dt of Eq. 1 discretised by the five steps of Section 2.2; the
     normal is g / sqrt(|g|^2 + tiny) (0 where g = 0)."""

@@ -120,5 +120,5 @@ def inverse_problem(target, u, v, w, grid: Grid, nsteps, dt, eps, gamma, init, i
         loss = ((out.double() - target.double()) ** 2).sum() * dV
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     return theta.detach(), losses

@@ -5,7 +5,15 @@
 //   Fbar_f      = (dt/dx) (lam'_R - lam'_L)
 //   sbar_d(c)   = (gamma dt / 2dx) (lam'_{c+e_d} - lam'_{c-e_d})
 //   nbar(c)     = sbar(c) phi_c (1 - phi_c)
-//   gbar(c)     = (nbar - n (n . nbar)) / |g|         (0 where g = 0)
+//   gbar(c)     = (nbar - n (n . nbar)) / m           (0 where g = 0)
+// with the normal n = g / m, m = sqrt(|g|^2 + delta^2), delta = 8 machine
+// epsilons of T.  In every interface cell |g| >> delta and this is the
+// derivative of the forward step.  In the flat bulk next to phi = 1 (or 0)
+// neighbours differ by a unit or two in the last place, the unit normal is
+// rounding noise, and its derivative p (1 - p)/|g| (a few, there) makes the
+// linearised sharpening anti-diffusive: over a 200-step backward recursion
+// that noise grows by many orders of magnitude.  The floor caps the
+// derivative at p (1 - p)/delta.
 //   phibar_c    = sum_d [ Fbar_{c+1/2}(vs u_{c+1/2}/2 + gamma eps/dx)
 //                       + Fbar_{c-1/2}(vs u_{c-1/2}/2 - gamma eps/dx) ]
 //               + (1 - 2 phi_c) (sbar(c) . n_c)
@@ -27,6 +35,22 @@ namespace cdi {
 
 __device__ __forceinline__ float rsqrt_a(float q) { return rsqrtf(q); }
 __device__ __forceinline__ double rsqrt_a(double q) { return rsqrt(q); }
+
+// 1/m, m = sqrt(|g|^2 + delta^2), or 0 where g = 0 (no normal there, so no
+// derivative either).
+template <typename T>
+__device__ __forceinline__ T inv_norm(T g0, T g1, T g2)
+{
+    const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, NumLim<T>::adj_floor())));
+    const bool nz = (g0 != T(0)) | (g1 != T(0)) | (g2 != T(0));
+    return nz ? rsqrt_a(q) : T(0);
+}
+
+// 1 - |n|^2 = delta^2 / m^2 for n = g / m: the part of sbar that the
+// projection sbar - n (n . sbar) keeps along n when n is shorter than a unit
+// vector.
+template <typename T>
+__device__ __forceinline__ T floor_part(T inv) { return NumLim<T>::adj_floor() * inv * inv; }
 
 constexpr int PF_A = 3;    // prefetch distance (planes)
 constexpr int NSLOT_A = 8; // phi / lam' ring: power of two >= PF_A + 3 live planes
@@ -156,21 +180,22 @@ adj_kernel(const AdjArgs<T> a)
         const T g0 = sp[m][Y][X + 1] - sp[m][Y][X - 1];
         const T g1 = sp[m][Y + 1][X] - sp[m][Y - 1][X];
         const T g2 = sp[mp][Y][X] - sp[mm][Y][X];
-        const T q = g0 * g0 + g1 * g1 + g2 * g2;
-        const T inv = q > T(0) ? rsqrt_a(q) : T(0);
+        const T inv = inv_norm(g0, g1, g2);
         const T sb0 = c_sb * (sl[m][Y][X + 1] - sl[m][Y][X - 1]);
         const T sb1 = c_sb * (sl[m][Y + 1][X] - sl[m][Y - 1][X]);
         const T sb2 = c_sb * (sl[mp][Y][X] - sl[mm][Y][X]);
         const T n0 = g0 * inv, n1 = g1 * inv, n2 = g2 * inv;
         tloc = (T(1) - T(2) * p) * (sb0 * n0 + sb1 * n1 + sb2 * n2);
-        // c = sbar x n ; d = n x c = sbar - n (n . sbar) for a unit n
+        // c = sbar x n ; d = n x c + sbar (1 - |n|^2) = sbar - n (n . sbar).  The
+        // cross-product form keeps d exactly 0 for sbar parallel to n (1D).
         const T c0 = sb1 * n2 - sb2 * n1;
         const T c1 = sb2 * n0 - sb0 * n2;
         const T c2 = sb0 * n1 - sb1 * n0;
-        const T d0 = n1 * c2 - n2 * c1;
-        const T d1 = n2 * c0 - n0 * c2;
-        const T d2 = n0 * c1 - n1 * c0;
-        // nbar = sbar p (1 - p);  gbar = (nbar - n (n . nbar)) / |g| = p (1 - p) d / |g|
+        const T fl = floor_part(inv);
+        const T d0 = fma(sb0, fl, n1 * c2 - n2 * c1);
+        const T d1 = fma(sb1, fl, n2 * c0 - n0 * c2);
+        const T d2 = fma(sb2, fl, n0 * c1 - n1 * c0);
+        // nbar = sbar p (1 - p);  gbar = (nbar - n (n . nbar)) / m = p (1 - p) d / m
         const T wgt = p * (T(1) - p) * inv;
         b0 = wgt * d0;
         b1 = wgt * d1;
@@ -350,8 +375,8 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
 
     // gbar and the local term (1 - 2 phi)(sbar . n) of the VX cells of group
     // (gc, ly) at the plane of slot Pm (Pmm / Pmp: planes below / above; the
-    // same slots of the lam' ring).  n = g / |g| (0 where g = 0); the
-    // projection uses n x (sbar x n) (see the per-cell kernel above).
+    // same slots of the lam' ring).  n = g / m (0 where g = 0); the
+    // projection uses n x (sbar x n) + sbar tiny/m^2 (see the per-cell kernel above).
     auto gbar_group = [&](int sm, int smm, int smp, int gc, int ly, T *b0, T *b1, T *b2, T *tl) {
         const int off = (ly + 2) * PP + VX + gc * VX;
         const T *Pm = sphi + sm * C::PHI, *Pmm = sphi + smm * C::PHI, *Pmp = sphi + smp * C::PHI;
@@ -375,8 +400,7 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
             const T g0 = (i + 1 < VX ? c[i + 1] : R) - (i > 0 ? c[i - 1] : L);
             const T g1 = yp[i] - yn[i];
             const T g2 = zp[i] - zn[i];
-            const T q = g0 * g0 + g1 * g1 + g2 * g2;
-            const T inv = q > T(0) ? rsqrt_a(q) : T(0);
+            const T inv = inv_norm(g0, g1, g2);
             const T sb0 = c_sb * ((i + 1 < VX ? lc[i + 1] : lR) - (i > 0 ? lc[i - 1] : lL));
             const T sb1 = c_sb * (lyp[i] - lyn[i]);
             const T sb2 = c_sb * (lzp[i] - lzn[i]);
@@ -387,9 +411,10 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
             const T x1_ = sb2 * n0 - sb0 * n2;
             const T x2_ = sb0 * n1 - sb1 * n0;
             const T wgt = p * (T(1) - p) * inv;
-            b0[i] = wgt * (n1 * x2_ - n2 * x1_);
-            b1[i] = wgt * (n2 * x0_ - n0 * x2_);
-            b2[i] = wgt * (n0 * x1_ - n1 * x0_);
+            const T fl = floor_part(inv);
+            b0[i] = wgt * fma(sb0, fl, n1 * x2_ - n2 * x1_);
+            b1[i] = wgt * fma(sb1, fl, n2 * x0_ - n0 * x2_);
+            b2[i] = wgt * fma(sb2, fl, n0 * x1_ - n1 * x0_);
         }
     };
     // gbar_x only, of cell (lx, ly) (the x-ring).
@@ -401,15 +426,14 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
         const T g0 = Pm[off + 1] - Pm[off - 1];
         const T g1 = Pm[off + PP] - Pm[off - PP];
         const T g2 = Pmp[off] - Pmm[off];
-        const T q = g0 * g0 + g1 * g1 + g2 * g2;
-        const T inv = q > T(0) ? rsqrt_a(q) : T(0);
+        const T inv = inv_norm(g0, g1, g2);
         const T sb0 = c_sb * (Lm[off + 1] - Lm[off - 1]);
         const T sb1 = c_sb * (Lm[off + PP] - Lm[off - PP]);
         const T sb2 = c_sb * (Lmp[off] - Lmm[off]);
         const T n0 = g0 * inv, n1 = g1 * inv, n2 = g2 * inv;
         const T x1_ = sb2 * n0 - sb0 * n2;
         const T x2_ = sb0 * n1 - sb1 * n0;
-        return p * (T(1) - p) * inv * (n1 * x2_ - n2 * x1_);
+        return p * (T(1) - p) * inv * fma(sb0, floor_part(inv), n1 * x2_ - n2 * x1_);
     };
 
     for (int u = blockIdx.x; u < units; u += gridDim.x) {

@@ -41,7 +41,8 @@ def test_adjoint_parity(dtype, shape, with_vel):
         g0 = np.random.default_rng(1).standard_normal((3,) + shape)
         grads = [dev(x, dtype) for x in g0]
     g.step_adjoint(dev(phi, dtype), dev(lam, dtype), out, dt, eps, gamma, vs, grads=grads)
-    ref = oracle.adjoint(phi, u, v, w, lam, h, dt, eps, gamma, vs, want_vel=with_vel)
+    ref = oracle.adjoint(phi, u, v, w, lam, h, dt, eps, gamma, vs, want_vel=with_vel,
+                         tiny=oracle.adjoint_floor_of(t))
     if with_vel:
         ref, rgu, rgv, rgw = ref
     scale = max(1.0, np.abs(ref).max())
@@ -77,7 +78,8 @@ def test_adjoint_every_tile(dtype, tile, shape, nchunks, with_vel):
         g0 = np.random.default_rng(5).standard_normal((3,) + shape)
         grads = [dev(x, dtype) for x in g0]
     g.step_adjoint(dev(phi, dtype), dev(lam, dtype), out, dt, eps, gamma, vs, grads=grads)
-    ref = oracle.adjoint(phi, u, v, w, lam, h, dt, eps, gamma, vs, want_vel=with_vel)
+    ref = oracle.adjoint(phi, u, v, w, lam, h, dt, eps, gamma, vs, want_vel=with_vel,
+                         tiny=oracle.adjoint_floor_of(t))
     if with_vel:
         ref, rgu, rgv, rgw = ref
     scale = max(1.0, np.abs(ref).max())
@@ -88,6 +90,49 @@ def test_adjoint_every_tile(dtype, tile, shape, nchunks, with_vel):
             base = np.asarray(base, t).astype(np.float64)
             s2 = max(1.0, np.abs(rg).max())
             assert np.abs(gd.double().cpu().numpy() - (base + rg)).max() <= tol * s2 * 4
+
+
+def tail_case(shape, eps_cells, seed):
+    """A tanh sphere whose far tails fall through 1e-19 (|g|^2 ~ FLT_MIN) to ~1e-26."""
+    nz, ny, nx = shape
+    h = 1.0 / nx
+    c = (0.5 * nx * h, 0.45 * ny * h, 0.55 * nz * h)
+    d = I.sphere_distance(shape, h, c, 6 * h)
+    phi = 1.0 / (1.0 + np.exp(-d / (eps_cells * h)))  # = (1 + tanh(d / 2 eps)) / 2, no cancellation
+    u, v, w = I.random_velocity(shape, h, 8, 3, seed)
+    lam = np.random.default_rng(seed + 1).standard_normal(shape)
+    return phi, u, v, w, lam, h
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("tile", range(cdi.ADJ_TILES))
+def test_adjoint_floor_regime(dtype, tile):
+    """Where |g| falls to the adjoint's floor delta (the tails of a sharp sphere, and its
+    bulk next to phi = 1 where FP32 neighbours differ by units in the last place) the
+    adjoint differentiates n = g / sqrt(|g|^2 + delta^2): it matches the oracle adjoint with
+    that floor on every kernel, and (so that the case means something) in FP32 not the
+    oracle's unit-normal adjoint."""
+    shape = (24, 20, 64)
+    t = np.float32 if dtype == torch.float32 else np.float64
+    phi, u, v, w, lam, h = tail_case(shape, 0.5, 3)
+    phi, u, v, w, lam = (np.asarray(x, t).astype(np.float64) for x in (phi, u, v, w, lam))
+    g2 = sum((np.roll(phi, -1, a) - np.roll(phi, 1, a)) ** 2 for a in (0, 1, 2))
+    fl = oracle.adjoint_floor_of(t)
+    assert ((g2 > 0) & (g2 < fl)).sum() > 100   # the regime is present
+    dt, eps, gamma, vs = 0.1 * h, 0.5 * h, 1.0, 1.0
+    g = cdi.Grid(shape[2], shape[1], shape[0], h, dtype)
+    g.set_velocity(*[dev(x, dtype) for x in (u, v, w)])
+    g.set_launch(cdi.CDI_KERNEL_ADJOINT, tile, 0, 0)
+    out = torch.empty(shape, dtype=dtype, device="cuda")
+    g.step_adjoint(dev(phi, dtype), dev(lam, dtype), out, dt, eps, gamma, vs)
+    ref = oracle.adjoint(phi, u, v, w, lam, h, dt, eps, gamma, vs, tiny=fl)
+    unit = oracle.adjoint(phi, u, v, w, lam, h, dt, eps, gamma, vs)
+    tol = 2e-6 if dtype == torch.float32 else 1e-12
+    scale = max(1.0, np.abs(ref).max())
+    got = out.double().cpu().numpy()
+    assert np.abs(got - ref).max() <= tol * scale
+    if dtype == torch.float32:
+        assert np.abs(unit - ref).max() > 1e-4 * scale
 
 
 def test_adjoint_constant_lambda_gpu():

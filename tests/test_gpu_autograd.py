@@ -133,3 +133,40 @@ def test_inverse_problem_recovers_sphere():
     theta, losses = AG.inverse_problem(target, *vel, g, 40, dt, eps, gamma, init, iters=60, lr=4e-3)
     assert losses[-1] < 0.05 * losses[0]
     assert (theta - true).abs().max().item() < 0.5 * (init - true).abs().max().item()
+
+
+@pytest.mark.parametrize("n", [128, 512])
+def test_long_fp32_rollout_gradient(n):
+    """The inverse problem's configuration (512^3; 128^3 as the small case): 200 FP32 steps,
+    checkpoint every 16, 32-mode random velocity.  dL/dtheta of the sphere parameters from
+    the adjoint matches central differences of the FP32 rollout.  The far tails of phi reach
+    |g|^2 ~ FLT_MIN here; an adjoint of the unit normal instead of the step's regularised
+    normal grows there without bound over the 200 steps."""
+    h = 1.0 / n
+    vel = [x.to(torch.float32).contiguous() for x in I.random_velocity_torch((n, n, n), h, 32, 4, 7)]
+    g = cdi.Grid(n, n, n, h, torch.float32)
+    g.set_velocity(*vel)
+    eps, gamma, dt = h, g.U, 0.1 * h / g.U
+    true = torch.tensor([0.5, 0.5, 0.5, 0.2], dtype=torch.float64, device="cuda")
+    init = torch.tensor([0.52, 0.485, 0.51, 0.18], dtype=torch.float64, device="cuda")
+
+    def roll(th):
+        return AG.rollout(AG.sphere_phi(th, g.shape, h, eps).float().contiguous(), *vel, g, 200, dt, eps,
+                          gamma, ckpt_every=16)
+    with torch.no_grad():
+        target = roll(true)
+
+    def loss(th):
+        return ((roll(th).double() - target.double()) ** 2).sum() * h ** 3
+    th = init.clone().requires_grad_(True)
+    loss(th).backward()
+    grad = th.grad.cpu().numpy()
+    fd = np.empty(4)
+    with torch.no_grad():
+        for c in range(4):
+            e = torch.zeros(4, dtype=torch.float64, device="cuda")
+            e[c] = 2e-3
+            fd[c] = (float(loss(init + e)) - float(loss(init - e))) / 4e-3
+    assert np.all(np.isfinite(grad))
+    assert np.abs(grad - fd).max() <= 0.02 * np.abs(fd).max(), (grad, fd)
+    assert abs(grad[3] - fd[3]) <= 0.01 * abs(fd[3]), (grad, fd)

@@ -514,3 +514,10 @@ def test_rk_conservation_and_boundedness(scheme):
             p = oracle.rk_step(p, u, v, w, h, dt, eps, gamma, scheme)
             assert ((p < -tol) | (p > 1 + tol)).sum() == 0
         assert abs(p.sum() - phi.sum()) <= 1e-13 * phi.sum()
+
+
+def test_adjoint_floor_values():
+    """delta = 8 machine epsilons = 16 units in the last place just below 1."""
+    assert oracle.adjoint_floor_of(np.float32) == 2.0 ** -40
+    assert oracle.adjoint_floor_of(np.float64) == 2.0 ** -98
+    assert np.sqrt(oracle.adjoint_floor_of(np.float32)) == 16 * (1.0 - float(np.nextafter(np.float32(1), 0)))
