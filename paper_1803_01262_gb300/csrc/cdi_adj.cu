@@ -36,12 +36,21 @@ namespace cdi {
 __device__ __forceinline__ float rsqrt_a(float q) { return rsqrtf(q); }
 __device__ __forceinline__ double rsqrt_a(double q) { return rsqrt(q); }
 
+// delta^2 = (8 machine epsilons)^2: (2^-20)^2 in FP32, (2^-49)^2 in FP64.
+template <typename T> struct AdjFloor;
+template <> struct AdjFloor<float> {
+    __device__ __forceinline__ static float sq() { return 9.094947017729282e-13f; }
+};
+template <> struct AdjFloor<double> {
+    __device__ __forceinline__ static double sq() { return 3.1554436208840472e-30; }
+};
+
 // 1/m, m = sqrt(|g|^2 + delta^2), or 0 where g = 0 (no normal there, so no
 // derivative either).
 template <typename T>
 __device__ __forceinline__ T inv_norm(T g0, T g1, T g2)
 {
-    const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, NumLim<T>::adj_floor())));
+    const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, AdjFloor<T>::sq())));
     const bool nz = (g0 != T(0)) | (g1 != T(0)) | (g2 != T(0));
     return nz ? rsqrt_a(q) : T(0);
 }
@@ -50,7 +59,7 @@ __device__ __forceinline__ T inv_norm(T g0, T g1, T g2)
 // projection sbar - n (n . sbar) keeps along n when n is shorter than a unit
 // vector.
 template <typename T>
-__device__ __forceinline__ T floor_part(T inv) { return NumLim<T>::adj_floor() * inv * inv; }
+__device__ __forceinline__ T floor_part(T inv) { return AdjFloor<T>::sq() * inv * inv; }
 
 constexpr int PF_A = 3;    // prefetch distance (planes)
 constexpr int NSLOT_A = 8; // phi / lam' ring: power of two >= PF_A + 3 live planes

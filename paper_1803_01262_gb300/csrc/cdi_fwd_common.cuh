@@ -11,13 +11,9 @@ __device__ __forceinline__ double rsqrt_t(double q) { return rsqrt(q); }
 template <typename T> struct NumLim;
 template <> struct NumLim<float> {
     __device__ __forceinline__ static float tiny() { return 1.17549435e-38f; }  // FLT_MIN
-    // (8 FLT_EPSILON)^2 = (2^-20)^2, the adjoint's floor under |g|^2
-    __device__ __forceinline__ static float adj_floor() { return 9.094947017729282e-13f; }
 };
 template <> struct NumLim<double> {
     __device__ __forceinline__ static double tiny() { return 2.2250738585072014e-308; }  // DBL_MIN
-    // (8 DBL_EPSILON)^2 = (2^-49)^2
-    __device__ __forceinline__ static double adj_floor() { return 3.1554436208840472e-30; }
 };
 
 template <typename T>
