@@ -253,6 +253,83 @@ def inverse_512(dev, iters=3):
     return out
 
 
+def size_1024(dev, peak, nst=500, ck=32, inner=8):
+    """1024^3 FP32: 64-mode random velocity (kmax 4, seed 11, U = 1), four spheres, eps = dx,
+    gamma = U, dt = 0.1 dx / U.  500 timed forward steps (one native run, CUDA events):
+    Gcell-updates/s, HBM fraction, FP64-reduced mass drift and tolerant bound violations over
+    the run.  Then one gradient of L = sum(w phi_500) dV (w = phi_0) through the 500 steps,
+    checkpoint every 32 (recomputed in sub-segments of 8), timed, and its directional
+    derivative along phi_0 (1 - phi_0) against a central difference of two FP32 rollouts."""
+    import torch
+    from paper_1803_01262_gb300 import autograd as AG
+    from paper_1803_01262_gb300 import cdi
+    from paper_1803_01262_gb300 import inputs as I
+    n = 1024
+    h = 1.0 / n
+    shape = (n, n, n)
+    sph = [((0.3, 0.3, 0.3), 0.12), ((0.7, 0.35, 0.6), 0.15), ((0.45, 0.75, 0.25), 0.1),
+           ((0.8, 0.8, 0.8), 0.13)]
+    vel = [t.float() for t in I.random_velocity_torch(shape, h, 64, 4, 11, device=dev)]
+    phi0 = I.spheres_phi_torch(shape, h, sph, h, device=dev).float()
+    g = cdi.Grid(n, n, n, h, torch.float32)
+    g.set_velocity(*vel)
+    eps, gamma = h, g.U
+    dt = 0.1 * h / g.U
+    s1, s2 = phi0.clone(), torch.empty_like(phi0)
+    g.autotune(s1, s2, dt, eps, gamma, reps=2)
+    del s1, s2
+    launch = g.get_launch()
+    a, b = phi0.clone(), torch.empty_like(phi0)
+    g.run(a, b, 3, dt, eps, gamma)      # warm-up
+    a.copy_(phi0)
+    g.reset_run_stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    out = g.run(a, b, nst, dt, eps, gamma)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = g.stats()
+    m0 = phi0.double().sum().item()
+    del a, b, out
+    gbs = BYTES_F32 * n ** 3 / (ms / nst * 1e-3) / 1e9
+    res = {"workload": "cdi_step_random64_4spheres_1024^3", "steps": nst,
+           "value": n ** 3 * nst / (ms * 1e-3) / 1e9, "unit": "Gcell-updates/s",
+           "ms_per_step": ms / nst, "achieved_gbs": gbs, "frac": gbs / peak, "launch": launch,
+           "mass_drift_rel": abs(st["sum"] - m0) / m0, "n_tol_run": int(st["n_tol_run"]),
+           "n_strict_run": int(st["n_strict_run"]), "steps_run": int(st["steps_run"]),
+           "min_run": st["min_run"], "max_run": st["max_run"]}
+
+    w64 = phi0.double()
+
+    def lossval(pT):
+        return float(torch.sum(pT.double() * w64)) * h ** 3
+
+    def roll(p0):
+        x, y = p0.clone(), torch.empty_like(p0)
+        return g.run(x, y, nst, dt, eps, gamma)
+    x = phi0.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    outT = AG.rollout(x, *vel, g, nst, dt, eps, gamma, ckpt_every=ck, inner_every=inner)
+    outT.backward((phi0 * h ** 3).contiguous())
+    torch.cuda.synchronize()
+    tg = time.perf_counter() - t0
+    delta = phi0 * (1 - phi0)
+    dd = float(torch.sum(x.grad.double() * delta.double()))
+    del x, outT
+    alpha = 1e-2
+    with torch.no_grad():
+        fd = (lossval(roll(phi0 + alpha * delta)) - lossval(roll(phi0 - alpha * delta))) / (2 * alpha)
+    res["gradient"] = {"ms_per_gradient": tg * 1e3, "checkpoint_every": ck, "inner_every": inner,
+                       "loss": "sum(phi_0 phi_500) dV", "direction": "phi_0 (1 - phi_0)",
+                       "adjoint_dir_deriv": dd, "fd_dir_deriv": fd, "rel_err": abs(dd - fd) / abs(fd)}
+    del g, vel, phi0, w64, delta
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -469,6 +546,12 @@ def main():
     inverse = None
     if not args.no_extra:
         inverse = inverse_512(dev)
+        torch.cuda.empty_cache()
+
+    # ---- 1024^3: 500 forward steps and a gradient through them ----
+    big1024 = None
+    if not args.no_extra:
+        big1024 = size_1024(dev, peak)
 
     line = None
     if rank == 0:
@@ -510,6 +593,7 @@ def main():
             "batch": batch,
             "size_512": big,
             "inverse_512": inverse,
+            "size_1024": big1024,
             "stats_last_step": {"mass": st["mass"], "min": st["min"], "max": st["max"],
                                 "n_tol": st["n_tol"]},
             "clocks": clocks,

@@ -5,8 +5,15 @@ explicit CDI steps (``cdi_step``) and, on backward, applies the discrete
 adjoint step (``cdi_step_adjoint``) in reverse with recompute from
 checkpoints: the forward keeps phi every ``ckpt_every`` steps; the backward
 recomputes one segment at a time (ckpt_every - 1 extra forward steps per
-segment) and walks it backwards.  If the face velocities require grad, their
-gradients are accumulated by the adjoint kernel on the same pass.
+segment) and walks it backwards.  With ``inner_every`` < ``ckpt_every`` a
+segment is itself recomputed in sub-segments of ``inner_every`` steps: one
+pass over the segment keeps only the sub-segment starts, then each
+sub-segment (last first) is recomputed in full and walked backwards, so the
+backward holds ckpt_every / inner_every + inner_every states instead of
+ckpt_every (at 1024^3 FP32, 32 steps per checkpoint: 48 GB instead of
+124 GB) for about ckpt_every more forward steps per segment.  If the face
+velocities require grad, their gradients are accumulated by the adjoint
+kernel on the same pass.
 
 The velocity of step i is vel_scale_i * (u, v, w) with
 vel_scale_i = cos(pi t_i / period) (1 when period <= 0), t_i = t0 + i dt.
@@ -26,7 +33,7 @@ def _scale(i, t0, dt, period):
 
 class _Rollout(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, phi0, u, v, w, grid, nsteps, dt, eps, gamma, period, t0, ckpt_every):
+    def forward(ctx, phi0, u, v, w, grid, nsteps, dt, eps, gamma, period, t0, ckpt_every, inner_every):
         grid.set_velocity(u, v, w, umax=0.0)
         ckpts = {0: phi0.detach().clone()}
         a = phi0.detach().clone()
@@ -37,7 +44,7 @@ class _Rollout(torch.autograd.Function):
             if (i + 1) % ckpt_every == 0 and i + 1 < nsteps:
                 ckpts[i + 1] = a.clone()
         ctx.grid = grid
-        ctx.args = (nsteps, dt, eps, gamma, period, t0, ckpt_every)
+        ctx.args = (nsteps, dt, eps, gamma, period, t0, ckpt_every, inner_every)
         ctx.ckpts = ckpts
         ctx.save_for_backward(u, v, w)
         return a
@@ -46,39 +53,56 @@ class _Rollout(torch.autograd.Function):
     def backward(ctx, grad_out):
         u, v, w = ctx.saved_tensors
         grid = ctx.grid
-        nsteps, dt, eps, gamma, period, t0, k = ctx.args
+        nsteps, dt, eps, gamma, period, t0, k, inner = ctx.args
         grid.set_velocity(u, v, w, umax=0.0)
         want_vel = any(ctx.needs_input_grad[1:4])
         grads = [torch.zeros_like(u), torch.zeros_like(v), torch.zeros_like(w)] if want_vel else None
         lam = grad_out.contiguous().clone()
         lam_b = torch.empty_like(lam)
-        starts = sorted(ctx.ckpts)
-        for s in reversed(starts):
+
+        def fwd(p, i):
+            nxt = torch.empty_like(p)
+            grid.step(p, nxt, dt, eps, gamma, _scale(i, t0, dt, period))
+            return nxt
+
+        for s in reversed(sorted(ctx.ckpts)):
             e = min(s + k, nsteps)
-            # recompute states s .. e-1 from the checkpoint
-            states = [ctx.ckpts[s]]
-            for i in range(s, e - 1):
-                nxt = torch.empty_like(states[-1])
-                grid.step(states[-1], nxt, dt, eps, gamma, _scale(i, t0, dt, period))
-                states.append(nxt)
-            for i in range(e - 1, s - 1, -1):
-                grid.step_adjoint(states[i - s], lam, lam_b, dt, eps, gamma,
-                                  _scale(i, t0, dt, period), grads=grads)
-                lam, lam_b = lam_b, lam
-            del states
+            # sub-segment starts s, s + inner, ... (< e), recomputed from the checkpoint
+            subs = {s: ctx.ckpts[s]}
+            p = ctx.ckpts[s]
+            last = s + ((e - 1 - s) // inner) * inner
+            for i in range(s, last):
+                p = fwd(p, i)
+                if (i + 1 - s) % inner == 0:
+                    subs[i + 1] = p
+            del p
+            for ss in reversed(sorted(subs)):
+                ee = min(ss + inner, e)
+                states = [subs.pop(ss)]     # states ss .. ee-1
+                for i in range(ss, ee - 1):
+                    states.append(fwd(states[-1], i))
+                for i in range(ee - 1, ss - 1, -1):
+                    grid.step_adjoint(states[i - ss], lam, lam_b, dt, eps, gamma,
+                                      _scale(i, t0, dt, period), grads=grads)
+                    lam, lam_b = lam_b, lam
+                del states
         ctx.ckpts = None
         gu = gv = gw = None
         if want_vel:
             gu, gv, gw = grads
-        return lam, gu, gv, gw, None, None, None, None, None, None, None, None
+        return lam, gu, gv, gw, None, None, None, None, None, None, None, None, None
 
 
-def rollout(phi0, u, v, w, grid: Grid, nsteps, dt, eps, gamma, period=0.0, t0=0.0, ckpt_every=16):
+def rollout(phi0, u, v, w, grid: Grid, nsteps, dt, eps, gamma, period=0.0, t0=0.0, ckpt_every=16,
+            inner_every=None):
     """Differentiable nsteps-step CDI rollout (see module docstring)."""
     if ckpt_every < 1:
         raise ValueError("ckpt_every must be >= 1")
+    inner = ckpt_every if inner_every is None else int(inner_every)
+    if inner < 1:
+        raise ValueError("inner_every must be >= 1")
     return _Rollout.apply(phi0, u, v, w, grid, int(nsteps), float(dt), float(eps), float(gamma),
-                          float(period), float(t0), int(ckpt_every))
+                          float(period), float(t0), int(ckpt_every), min(inner, int(ckpt_every)))
 
 
 def sphere_phi(params, shape, h, eps):

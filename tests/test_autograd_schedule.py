@@ -1,0 +1,84 @@
+"""Host logic of the checkpoint-recompute rollout, on the CPU.
+
+A stand-in grid whose step is an elementwise nonlinear map (and whose adjoint
+is that map's exact transpose) checks that the backward applies the adjoint
+at the right recomputed state, in the right order, for every checkpoint and
+sub-segment layout: the gradient must equal torch autograd through the same
+map, and must not depend on the layout.
+"""
+import math
+
+import pytest
+import torch
+
+from paper_1803_01262_gb300 import autograd as AG
+
+
+class FakeGrid:
+    """phi' = phi + dt vs (sin(phi) + u phi); its adjoint lam = lam' (1 + dt vs (cos(phi) + u))."""
+
+    def __init__(self):
+        self.steps = 0
+        self.adjoints = 0
+
+    def set_velocity(self, u, v, w, umax=-1.0):
+        self.u = u
+
+    def step(self, a, b, dt, eps, gamma, vs=1.0):
+        self.steps += 1
+        b.copy_(a + dt * vs * (torch.sin(a) + self.u * a))
+
+    def step_adjoint(self, phi, lam, out, dt, eps, gamma, vs=1.0, grads=None):
+        self.adjoints += 1
+        out.copy_(lam * (1 + dt * vs * (torch.cos(phi) + self.u)))
+
+
+def reference(phi0, u, nsteps, dt, period):
+    p = phi0
+    for i in range(nsteps):
+        vs = math.cos(math.pi * i * dt / period) if period > 0 else 1.0
+        p = p + dt * vs * (torch.sin(p) + u * p)
+    return p
+
+
+@pytest.mark.parametrize("nsteps,ckpt,inner", [(1, 16, None), (7, 16, None), (16, 16, None),
+                                               (37, 16, None), (37, 16, 4), (37, 16, 5), (37, 16, 1),
+                                               (50, 8, 3), (33, 32, 8), (200, 16, 16), (41, 1, None)])
+@pytest.mark.parametrize("period", [0.0, 0.37])
+def test_gradient_matches_autograd_for_every_layout(nsteps, ckpt, inner, period):
+    g = torch.Generator().manual_seed(nsteps)
+    phi0 = torch.rand(5, 4, 6, dtype=torch.float64, generator=g)
+    u = torch.rand(5, 4, 6, dtype=torch.float64, generator=g) - 0.5
+    w = torch.randn(5, 4, 6, dtype=torch.float64, generator=g)
+    dt = 0.05
+    x = phi0.clone().requires_grad_(True)
+    (reference(x, u, nsteps, dt, period) * w).sum().backward()
+    want = x.grad.clone()
+
+    grid = FakeGrid()
+    y = phi0.clone().requires_grad_(True)
+    out = AG.rollout(y, u, u, u, grid, nsteps, dt, 1.0, 1.0, period=period, ckpt_every=ckpt,
+                     inner_every=inner)
+    assert torch.allclose(out, reference(phi0, u, nsteps, dt, period), rtol=0, atol=1e-14)
+    fwd_steps = grid.steps
+    (out * w).sum().backward()
+    assert torch.allclose(y.grad, want, rtol=1e-13, atol=1e-14)
+    assert grid.adjoints == nsteps
+    # recompute count: each segment [s, e) reaches its last sub-start, then each sub-segment
+    # recomputes its own states
+    inn = min(inner or ckpt, ckpt)
+    expect = 0
+    for s in range(0, nsteps, ckpt):
+        e = min(s + ckpt, nsteps)
+        last = s + ((e - 1 - s) // inn) * inn
+        expect += last - s + sum(min(ss + inn, e) - ss - 1 for ss in range(s, e, inn))
+    assert grid.steps - fwd_steps == expect
+
+
+def test_rejects_bad_intervals():
+    grid = FakeGrid()
+    p = torch.zeros(2, 2, 2, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        AG.rollout(p, p, p, p, grid, 3, 0.1, 1.0, 1.0, ckpt_every=0)
+    with pytest.raises(ValueError):
+        AG.rollout(p, p, p, p, grid, 3, 0.1, 1.0, 1.0, ckpt_every=4, inner_every=0)
