@@ -280,12 +280,18 @@ CDI_API int cdi_batch_autotune(cdi_batch *b, int reps, float *best_ms, void *str
 /* Kernels with a tunable launch configuration. */
 enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
 
+/* Forward work split of cdi_set_launch: equal contiguous shares per block. */
+#define CDI_NCHUNKS_BALANCED (-1)
+
 /* Choose the launch configuration of a kernel of this grid (not part of the
  * paper: a performance control).  Forward tiles: 0..3 one cell per thread
  * (32x8, 32x16, 64x8, 32x4 cells), 4 and 5 sixteen-byte vectors per thread
  * (16x16 and 16x8 threads; need nx % (16/sizeof(element)) == 0); tile < 0
- * restores the default.  blocks_per_sm <= 0 fills the GPU; nchunks <= 0
- * picks the number of z chunks per tile column from a cost model.  Adjoint
+ * restores the default.  blocks_per_sm <= 0 fills the GPU.  Forward work
+ * split: nchunks >= 1 cuts every tile column into that many z chunks, taken
+ * round-robin by the persistent blocks; CDI_NCHUNKS_BALANCED gives every block
+ * an equal contiguous share of the tile-planes (tile-major, cut at column
+ * ends); 0 picks one of these from a cost model.  Adjoint
  * tiles: 0..2 (32x8, 32x16, 32x4 cells), nchunks sets its z chunking.  Every
  * configuration computes the same result up to the order of the reduction
  * partials. */

@@ -24,6 +24,7 @@ CDI_F32, CDI_F64 = 0, 1
 CDI_EULER, CDI_RK2, CDI_RK3, CDI_RK4 = 0, 1, 2, 3
 CDI_CHECK_CONDITION = 1
 CDI_KERNEL_FORWARD, CDI_KERNEL_ADJOINT = 0, 1
+CDI_NCHUNKS_BALANCED = -1   # forward work split: equal contiguous shares per block
 FWD_TILES = 7
 ADJ_TILES = 4
 

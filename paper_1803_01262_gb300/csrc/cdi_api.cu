@@ -104,11 +104,12 @@ static void reset_run_host(StatsRec *r)
 }
 
 // Forward launch: a tile shape, as many blocks as fit on the GPU at once, and
-// the number of z chunks per tile column.  Blocks take (chunk, tile) units
-// round-robin; with nchunks <= 0 the count minimises
-//   max(rounds * (planes per unit + 3), units * (planes per unit + 1) / blocks),
-// a per-block critical path (3 planes of prologue per unit) against the
-// average load (1 plane of re-read per unit).
+// the work split.  nchunks >= 1: z chunks per tile column, (chunk, tile) units
+// taken round-robin; CDI_NCHUNKS_BALANCED: equal contiguous shares of the
+// tile-planes per block; 0: the split minimising the per-block critical path
+// in planes, 3 planes of prologue per unit:
+//   chunks: max(rounds * (planes per unit + 3), units * (planes per unit + 1) / blocks)
+//   balanced: P + 3 (ceil(P / nz) + 1), P = ceil(tiles * nz / blocks).
 static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, LaunchCfg *c,
                    bool rk = false)
 {
@@ -129,7 +130,8 @@ static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, 
     const long long G = (long long)resident * g->sm_count;
     const long long tiles = cdi::fwd_tiles_xy(tile, es, g->nx, g->ny);
     const int nz = g->nz;
-    if (nchunks <= 0) {
+    if (nchunks < 0 && nchunks != CDI_NCHUNKS_BALANCED) return fail(CDI_ERR_ARG, "nchunks %d", nchunks);
+    if (nchunks == 0) {
         double best = 1e300;
         for (int nc = 1; nc <= nz; ++nc) {
             const int zc = (nz + nc - 1) / nc;
@@ -142,11 +144,21 @@ static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, 
                 nchunks = nc;
             }
         }
+        const long long P = (tiles * nz + G - 1) / G;
+        const double bal = (double)P + 3.0 * (double)((P + nz - 1) / nz + 1);
+        if (bal < best * (1.0 - 1e-9) && tiles * nz < (1LL << 31)) nchunks = CDI_NCHUNKS_BALANCED;
     }
-    if (nchunks > nz) nchunks = nz;
-    const int zc = (nz + nchunks - 1) / nchunks;
-    const long long units = tiles * ((nz + zc - 1) / zc);
-    long long nb = G < units ? G : units;
+    long long nb;
+    if (nchunks == CDI_NCHUNKS_BALANCED) {
+        const long long T = tiles * nz;
+        if (T >= (1LL << 31)) return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
+        nb = G < T ? G : T;
+    } else {
+        if (nchunks > nz) nchunks = nz;
+        const int zc = (nz + nchunks - 1) / nchunks;
+        const long long units = tiles * ((nz + zc - 1) / zc);
+        nb = G < units ? G : units;
+    }
     if (nb > g->capacity) nb = g->capacity;
     c->tile = tile;
     c->zchunk = 0;
@@ -815,7 +827,7 @@ int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps, d
     LaunchCfg best = saved;
     float best_t = 1e30f;
     int rc = CDI_OK;
-    const int chunk_opts[] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32};
+    const int chunk_opts[] = {CDI_NCHUNKS_BALANCED, 0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32};
     for (int tile = 0; tile < cdi::fwd_num_tiles() && rc == CDI_OK; ++tile) {
         if (cdi::fwd_tile_is_vec(tile) && g->nx % (16 / (int)esize(g)) != 0) continue;
         for (int oi = 0; oi < (int)(sizeof(chunk_opts) / sizeof(int)); ++oi) {

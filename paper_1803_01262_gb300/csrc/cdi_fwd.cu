@@ -19,7 +19,8 @@
 //                      register-prefetched velocities; any extents.
 // Work units are (z chunk, tile) pairs taken round-robin in chunk-major
 // order, so blocks resident together work on neighbouring tiles at the same
-// planes and the halo rows they share are served from L2.
+// planes and the halo rows they share are served from L2; or (balanced) each
+// block takes an equal contiguous share of the tile-planes (UnitIter).
 // Every block folds its outputs into mass / min / max / violation partials,
 // finished by the last block (cdi_reduce.cuh).
 // All indices wrap periodically; tiles may overhang the grid (ragged edges):
@@ -78,8 +79,6 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
     const long long plane = (long long)nx * ny;
     const int tiles_x = (nx + W - 1) / W;
     const int ntiles = tiles_x * ((ny + H - 1) / H);
-    const int zc = (nz + nchunks - 1) / nchunks;
-    const int units = ntiles * ((nz + zc - 1) / zc);
     const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_shp = a.c.c_shp, c_upd = a.c.c_upd;
 
     // Role: own vector of cells (tx, ty), a y-ring group, or an x-ring cell.
@@ -134,8 +133,9 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
     Acc<T> acc;
     acc.init();
 
-    for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        const Unit un = unit_of(u, ntiles, tiles_x, W, H, zc, nz);
+    UnitIter<W, H> units(ntiles, nz, nchunks);
+    Unit un;
+    while (units.next(un, ntiles, tiles_x, nz, nchunks)) {
         const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
 
         // The 64 ring threads issue every 16-byte copy (they are idle while the
@@ -378,14 +378,11 @@ fwd_kernel(const FwdArgs<T> a, const int nchunks)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tiles_x = (a.nx + BX - 1) / BX;
     const int ntiles = tiles_x * ((a.ny + BY - 1) / BY);
-    const int zc = (a.nz + nchunks - 1) / nchunks;
-    const int units = ntiles * ((a.nz + zc - 1) / zc);
     Acc<T> acc;
     acc.init();
-    for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        const Unit un = unit_of(u, ntiles, tiles_x, BX, BY, zc, a.nz);
-        scalar_unit<T, BX, BY, RK>(a, un, acc, smem_raw);
-    }
+    UnitIter<BX, BY> units(ntiles, a.nz, nchunks);
+    Unit un;
+    while (units.next(un, ntiles, tiles_x, a.nz, nchunks)) scalar_unit<T, BX, BY, RK>(a, un, acc, smem_raw);
     reduce_and_finish(acc.partial(), a.red);
 }
 

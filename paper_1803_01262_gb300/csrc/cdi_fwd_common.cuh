@@ -71,4 +71,46 @@ __device__ __forceinline__ Unit unit_of(int u, int ntiles, int tiles_x, int bw, 
     return r;
 }
 
+// The work units of one block of a persistent grid, tiles of BW x BH cells.
+//   nchunks >= 1: units u = blockIdx.x, blockIdx.x + gridDim.x, ... of the
+//     (z chunk, tile) list in chunk-major order, chunks of ceil(nz / nchunks)
+//     planes: blocks resident together work on neighbouring tiles at the same
+//     planes.
+//   nchunks <= 0 (balanced): block b takes the contiguous share
+//     [b T / B, (b + 1) T / B) of the T = ntiles * nz tile-planes in
+//     tile-major order (T < 2^31, checked by the host), cut where a tile's
+//     column ends: every block gets the same number of planes (+-1) in one or
+//     two units (more only when a share exceeds a column).
+template <int BW, int BH>
+struct UnitIter {
+    int p;  // next unit, or next tile-plane (the only state: the rest is recomputed
+            // from the launch parameters, which keeps it out of the registers)
+    __device__ __forceinline__ UnitIter(int ntiles, int nz, int nchunks)
+    {
+        p = nchunks >= 1 ? (int)blockIdx.x
+                         : (int)((long long)ntiles * nz * blockIdx.x / gridDim.x);
+    }
+    __device__ __forceinline__ bool next(Unit &r, int ntiles, int tiles_x, int nz, int nchunks)
+    {
+        if (nchunks >= 1) {
+            const int zc = (nz + nchunks - 1) / nchunks;
+            if (p >= ntiles * ((nz + zc - 1) / zc)) return false;
+            r = unit_of(p, ntiles, tiles_x, BW, BH, zc, nz);
+            p += gridDim.x;
+            return true;
+        }
+        const int q = (int)((long long)ntiles * nz * (blockIdx.x + 1) / gridDim.x);
+        if (p >= q) return false;
+        const int tile = p / nz;
+        const int z0 = p - tile * nz;
+        const int z1 = min(nz, z0 + (q - p));
+        r.x0 = (tile % tiles_x) * BW;
+        r.y0 = (tile / tiles_x) * BH;
+        r.z0 = z0;
+        r.z1 = z1;
+        p += z1 - z0;
+        return true;
+    }
+};
+
 }  // namespace cdi

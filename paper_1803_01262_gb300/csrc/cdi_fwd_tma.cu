@@ -84,8 +84,6 @@ fwd_tma_kernel(const FwdArgs<T> a, const __grid_constant__ TmaMaps maps, const i
     const long long plane = (long long)nx * ny;
     const int tiles_x = nx / W;
     const int ntiles = tiles_x * (ny / H);
-    const int zc = (nz + nchunks - 1) / nchunks;
-    const int units = ntiles * ((nz + zc - 1) / zc);
     const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_shp = a.c.c_shp, c_upd = a.c.c_upd;
 
     const bool is_own = tid < C::NOWN;
@@ -150,10 +148,10 @@ fwd_tma_kernel(const FwdArgs<T> a, const __grid_constant__ TmaMaps maps, const i
     Acc<T> acc;
     acc.init();
 
-    for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        const int chunk = u / ntiles, tile = u - chunk * ntiles;
-        const int x0 = (tile % tiles_x) * W, y0 = (tile / tiles_x) * H;
-        const int z0 = chunk * zc, z1 = min(nz, z0 + zc);
+    UnitIter<W, H> units(ntiles, nz, nchunks);
+    Unit un;
+    while (units.next(un, ntiles, tiles_x, nz, nchunks)) {
+        const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
         const int ym2 = wrapi(y0 - 2, ny), yph = wrapi(y0 + H, ny), ym1 = wrapi(y0 - 1, ny);
         const int xl = wrapi(x0 - VX, nx), xr = wrapi(x0 + W, nx);
 

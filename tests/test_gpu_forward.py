@@ -245,6 +245,32 @@ def test_every_launch_configuration(dtype, tile, shape, nchunks):
     assert abs(st["sum"] - ours.sum()) <= 1e-7 * abs(ours.sum())  # compensated FP32 partials
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("shape,tile,bps", [((64, 64, 256), 4, 1), ((64, 64, 256), 0, 1),
+                                            ((2, 512, 512), 4, 1), ((2, 512, 512), 1, 1),
+                                            ((9, 21, 68), 4, 0), ((9, 21, 68), 3, 0),
+                                            ((5, 7, 4), 0, 0), ((16, 32, 128), 6, 1)])
+def test_balanced_split(dtype, shape, tile, bps):
+    """Equal contiguous shares of the tile-planes per block (CDI_NCHUNKS_BALANCED): shares
+    cut inside a tile column, shares spanning many short columns, one-plane shares."""
+    f = random_fields(shape, 17 + shape[0], True, smooth=True)
+    eps, gamma = 1.1 * f.h, 0.9
+    dt = 0.12 * f.h * f.h / (gamma * eps)
+    g, vel = make_grid(f, dtype)
+    g.set_launch(cdi.CDI_KERNEL_FORWARD, tile, bps, cdi.CDI_NCHUNKS_BALANCED)
+    assert g.get_launch()["nchunks"] == cdi.CDI_NCHUNKS_BALANCED
+    a = dev(f.phi, dtype)
+    b = torch.empty_like(a)
+    g.step(a, b, dt, eps, gamma, 0.8)
+    st = g.stats()
+    phi, u, v, w = rounded(f, dtype)
+    ref = oracle.step(phi, u, v, w, f.h, dt, eps, gamma, 0.8)
+    ours = b.double().cpu().numpy()
+    assert np.abs(ours - ref).max() <= TOL[dtype]
+    assert st["min"] == ours.min() and st["max"] == ours.max()
+    assert abs(st["sum"] - ours.sum()) <= (1e-12 * ours.size if dtype == torch.float64 else 1e-7 * abs(ours.sum()))
+
+
 def test_autotune_keeps_result():
     f = I.deformation_3d(64)
     g, vel = make_grid(f, torch.float32)
