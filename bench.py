@@ -559,11 +559,11 @@ def main():
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and ws == 1:
-            planes = max(1, int(round(4 * 6e6 * 3 / (n * n))))  # about 4 s per step-sample set
+            planes = max(1, int(round(4 * 6e6 * 3 / (n * n))))  # the whole box up to 256^3
             planes = min(planes, n)
-            rate, el = cpu_oracle_rate(f, dt, eps, gamma, planes, 4)
+            rate, el = cpu_oracle_rate(f, dt, eps, gamma, planes, 12)   # ~10 s of CPU work
             cpu = {"value": rate, "unit": "Gcell-updates/s", "cores": 1, "kind": "oracle",
-                   "sample": f"4 FP64 oracle steps on {planes} of {n} z-planes of the {n}^3 box "
+                   "sample": f"12 FP64 oracle steps on {planes} of {n} z-planes of the {n}^3 box "
                              f"({n}x{n}x{planes} cells, periodic wrap), {el:.1f} s, single thread"}
         clocks = clk.summary()
         line = {
