@@ -332,6 +332,29 @@ def size_1024(dev, peak, nst=500, ck=32, inner=8):
     return res
 
 
+def phase_line(dev):
+    """Phase diagram of the (eps/dx, gamma/|u|) plane: 16 x 16 Table 2 drop boxes (50 x 50,
+    FP64) advanced by one batched launch per step for at least one advection period each."""
+    import numpy as np
+    import torch
+    from paper_1803_01262_gb300 import phase as P
+    pts = [(float(a), float(b)) for a in np.linspace(0.55, 2.0, 16) for b in np.linspace(0.3, 3.0, 16)]
+    P.phase_diagram(pts[:4], nsteps=10, autotune=False)       # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rows, info = P.phase_diagram(pts)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"workload": "phase diagram: 256 periodic 50x50 drop boxes (Table 2 setup), eps/dx 0.55..2,"
+                        " gamma/|u| 0.3..3, FP64 Euler, one batched launch per step",
+            "boxes": len(rows), "cells": info["cells"], "steps": info["nsteps"],
+            "run_ms": info["run_ms"], "value": info["cells"] * info["nsteps"] / (info["run_ms"] * 1e-3) / 1e9,
+            "unit": "Gcell-updates/s", "seconds_total_incl_setup_and_autotune": el,
+            "bounded": sum(r["bounded"] for r in rows), "sufficient": sum(r["sufficient"] for r in rows),
+            "sufficient_and_unbounded": sum(r["sufficient"] and not r["bounded"] for r in rows),
+            "launch": info["launch"]}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -550,6 +573,11 @@ def main():
         inverse = inverse_512(dev)
         torch.cuda.empty_cache()
 
+    # ---- phase diagram as one batched workload ----
+    phase = None
+    if not args.no_extra:
+        phase = phase_line(dev)
+
     # ---- 1024^3: 500 forward steps and a gradient through them ----
     big1024 = None
     if not args.no_extra:
@@ -596,6 +624,7 @@ def main():
             "size_512": big,
             "inverse_512": inverse,
             "size_1024": big1024,
+            "phase_diagram": phase,
             "stats_last_step": {"mass": st["mass"], "min": st["min"], "max": st["max"],
                                 "n_tol": st["n_tol"]},
             "clocks": clocks,
