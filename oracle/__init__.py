@@ -47,11 +47,14 @@ def _load():
             i, d = ctypes.c_int, ctypes.c_double
             lib.oracle_rhs.argtypes = [i, i, i, d, _D, _D, _D, _D, d, d, d, d, _D]
             lib.oracle_step.argtypes = [i, i, i, d, _D, _D, _D, _D, d, d, d, d, d, _D]
+            lib.oracle_rhs_face.argtypes = lib.oracle_rhs.argtypes
+            lib.oracle_step_face.argtypes = lib.oracle_step.argtypes
             lib.oracle_stats.argtypes = [ctypes.c_long, _D, d, d, _D,
                                          ctypes.POINTER(ctypes.c_longlong)]
             lib.oracle_adjoint.argtypes = [i, i, i, d, _D, _D, _D, _D, _D, d, d, d, d, d,
                                            _D, _D, _D, _D]
-            for f in (lib.oracle_rhs, lib.oracle_step, lib.oracle_stats, lib.oracle_adjoint):
+            for f in (lib.oracle_rhs, lib.oracle_step, lib.oracle_stats, lib.oracle_adjoint,
+                      lib.oracle_rhs_face, lib.oracle_step_face):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -89,38 +92,43 @@ def adjoint_floor_of(dtype) -> float:
     return float((8.0 * np.finfo(dtype).eps) ** 2)
 
 
-def rhs(phi, u, v, w, dx, eps, gamma, vel_scale=1.0, tiny=0.0):
+SHARPEN = ("centre", "face")
+
+
+def rhs(phi, u, v, w, dx, eps, gamma, vel_scale=1.0, tiny=0.0, sharpen="centre"):
     """d phi/dt of Eq. 1 discretised by the five steps of Section 2.2; the
-    normal is g / sqrt(|g|^2 + tiny) (0 where g = 0)."""
+    normal is g / sqrt(|g|^2 + tiny) (0 where g = 0).  ``sharpen="face"``
+    takes the non-default face-product sharpening phi_f (1 - phi_f) n_f."""
     phi, u, v, w = _check(phi, u, v, w)
     nz, ny, nx = phi.shape
     out = np.empty_like(phi)
-    rc = _load().oracle_rhs(nx, ny, nz, dx, _p(phi), _p(u), _p(v), _p(w), eps, gamma,
-                            vel_scale, tiny, _p(out))
+    f = {"centre": _load().oracle_rhs, "face": _load().oracle_rhs_face}[sharpen]
+    rc = f(nx, ny, nz, dx, _p(phi), _p(u), _p(v), _p(w), eps, gamma, vel_scale, tiny, _p(out))
     if rc:
         raise ValueError("oracle_rhs: bad arguments")
     return out
 
 
-def step(phi, u, v, w, dx, dt, eps, gamma, vel_scale=1.0, tiny=0.0):
-    """One explicit Euler step of the CDI equation (Eq. 11 generalised to 3D)."""
+def step(phi, u, v, w, dx, dt, eps, gamma, vel_scale=1.0, tiny=0.0, sharpen="centre"):
+    """One explicit Euler step of the CDI equation (Eq. 11 generalised to 3D);
+    ``sharpen`` as in :func:`rhs`."""
     phi, u, v, w = _check(phi, u, v, w)
     nz, ny, nx = phi.shape
     out = np.empty_like(phi)
-    rc = _load().oracle_step(nx, ny, nz, dx, _p(phi), _p(u), _p(v), _p(w), dt, eps,
-                             gamma, vel_scale, tiny, _p(out))
+    f = {"centre": _load().oracle_step, "face": _load().oracle_step_face}[sharpen]
+    rc = f(nx, ny, nz, dx, _p(phi), _p(u), _p(v), _p(w), dt, eps, gamma, vel_scale, tiny, _p(out))
     if rc:
         raise ValueError("oracle_step: bad arguments")
     return out
 
 
-def run(phi, u, v, w, dx, dt, eps, gamma, nsteps, period=0.0, t0=0.0, tiny=0.0):
+def run(phi, u, v, w, dx, dt, eps, gamma, nsteps, period=0.0, t0=0.0, tiny=0.0, sharpen="centre"):
     """nsteps Euler steps; velocity scaled by cos(pi t / period) when period > 0."""
     p = _f64(phi)
     t = t0
     for _ in range(nsteps):
         s = np.cos(np.pi * t / period) if period > 0 else 1.0
-        p = step(p, u, v, w, dx, dt, eps, gamma, s, tiny)
+        p = step(p, u, v, w, dx, dt, eps, gamma, s, tiny, sharpen)
         t += dt
     return p
 

@@ -23,6 +23,11 @@
  *     ((phi_{i-1})^2 - phi_{i-1}) n_{i-1}, as Eq. 13 and Eq. 16 require;
  *   - the normal is 0 where the central-difference gradient is exactly 0
  *     (the paper divides by |grad phi| without a guard);
+ *   - a non-default face-product sharpening (oracle_rhs_face / oracle_step_face):
+ *     the flux term gamma phi_f (1 - phi_f) n_f with phi_f = (phi_L + phi_R)/2
+ *     and n_f = (n_L + n_R)/2, the cell-centre normals interpolated to the
+ *     face; Eq. 13 and Eq. 19 do not hold for it (Section 2.2 forms the
+ *     product at cell centres), and the boundedness proof does not cover it;
  *   - every entry point takes a floor tiny >= 0 under the root,
  *     n = g / sqrt(|g|^2 + tiny) for g != 0: tiny = 0 is the paper's
  *     unit normal, tiny = the smallest normal number of a working precision
@@ -88,7 +93,7 @@ static void normals(long nx, long ny, long nz, const double *phi, double tiny,
 /* Steps 1-4: face fluxes F_d[c] on the face c + 1/2 e_d for every cell c. */
 static void face_fluxes(long nx, long ny, long nz, double dx, const double *phi,
                         const double *u, const double *v, const double *w,
-                        double eps, double gamma, double vel_scale, double tiny,
+                        double eps, double gamma, double vel_scale, double tiny, int face,
                         double *F0, double *F1, double *F2)
 {
     long n = nx * ny * nz;
@@ -113,8 +118,15 @@ static void face_fluxes(long nx, long ny, long nz, double dx, const double *phi,
                 long L = at(i, j, k, nx, ny, nz);
                 for (int d = 0; d < 3; d++) {
                     long R = nb(i, j, k, d, +1, nx, ny, nz);
-                    /* Step 2b: sharpening interpolated (averaged) to the face. */
-                    double sharp_f = 0.5 * (s[d][L] + s[d][R]);
+                    /* Step 2b: sharpening interpolated (averaged) to the face; or, in
+                     * the face-product form, phi_f (1 - phi_f) times the averaged normal. */
+                    double sharp_f;
+                    if (face) {
+                        double pf = 0.5 * (phi[L] + phi[R]);
+                        sharp_f = pf * (1.0 - pf) * 0.5 * (nrm[d][L] + nrm[d][R]);
+                    } else {
+                        sharp_f = 0.5 * (s[d][L] + s[d][R]);
+                    }
                     /* Step 3: diffusive flux, eps * dphi/dx on the face. */
                     double diff_f = eps * (phi[R] - phi[L]) / dx;
                     /* Step 4: advective flux, u_f times phi averaged to the face. */
@@ -128,16 +140,16 @@ static void face_fluxes(long nx, long ny, long nz, double dx, const double *phi,
 }
 
 /* d phi / dt = -(1/dx) sum_d (F_{c+1/2 e_d} - F_{c-1/2 e_d})  (Step 5, divergence). */
-ORACLE_API int oracle_rhs(int nx, int ny, int nz, double dx, const double *phi,
-                          const double *u, const double *v, const double *w,
-                          double eps, double gamma, double vel_scale, double tiny,
-                          double *rhs)
+static int rhs_impl(int nx, int ny, int nz, double dx, const double *phi,
+                    const double *u, const double *v, const double *w,
+                    double eps, double gamma, double vel_scale, double tiny, int face,
+                    double *rhs)
 {
     if (nx < 1 || ny < 1 || nz < 1 || !(dx > 0.0) || !(tiny >= 0.0)) return -1;
     long n = (long)nx * ny * nz;
     double *F[3];
     for (int d = 0; d < 3; d++) F[d] = (double *)malloc(sizeof(double) * n);
-    face_fluxes(nx, ny, nz, dx, phi, u, v, w, eps, gamma, vel_scale, tiny, F[0], F[1], F[2]);
+    face_fluxes(nx, ny, nz, dx, phi, u, v, w, eps, gamma, vel_scale, tiny, face, F[0], F[1], F[2]);
     for (long k = 0; k < nz; k++)
         for (long j = 0; j < ny; j++)
             for (long i = 0; i < nx; i++) {
@@ -151,20 +163,52 @@ ORACLE_API int oracle_rhs(int nx, int ny, int nz, double dx, const double *phi,
     return 0;
 }
 
+ORACLE_API int oracle_rhs(int nx, int ny, int nz, double dx, const double *phi,
+                          const double *u, const double *v, const double *w,
+                          double eps, double gamma, double vel_scale, double tiny,
+                          double *rhs)
+{
+    return rhs_impl(nx, ny, nz, dx, phi, u, v, w, eps, gamma, vel_scale, tiny, 0, rhs);
+}
+
+ORACLE_API int oracle_rhs_face(int nx, int ny, int nz, double dx, const double *phi,
+                               const double *u, const double *v, const double *w,
+                               double eps, double gamma, double vel_scale, double tiny,
+                               double *rhs)
+{
+    return rhs_impl(nx, ny, nz, dx, phi, u, v, w, eps, gamma, vel_scale, tiny, 1, rhs);
+}
+
 /* One explicit Euler step phi_out = phi + dt * rhs(phi)  (Eq. 11, Step 5). */
+static int step_impl(int nx, int ny, int nz, double dx, const double *phi,
+                     const double *u, const double *v, const double *w,
+                     double dt, double eps, double gamma, double vel_scale,
+                     double tiny, int face, double *phi_out)
+{
+    long n = (long)nx * ny * nz;
+    if (nx < 1 || ny < 1 || nz < 1) return -1;
+    double *r = (double *)malloc(sizeof(double) * n);
+    int rc = rhs_impl(nx, ny, nz, dx, phi, u, v, w, eps, gamma, vel_scale, tiny, face, r);
+    if (rc == 0)
+        for (long c = 0; c < n; c++) phi_out[c] = phi[c] + dt * r[c];
+    free(r);
+    return rc;
+}
+
 ORACLE_API int oracle_step(int nx, int ny, int nz, double dx, const double *phi,
                            const double *u, const double *v, const double *w,
                            double dt, double eps, double gamma, double vel_scale,
                            double tiny, double *phi_out)
 {
-    long n = (long)nx * ny * nz;
-    if (nx < 1 || ny < 1 || nz < 1) return -1;
-    double *r = (double *)malloc(sizeof(double) * n);
-    int rc = oracle_rhs(nx, ny, nz, dx, phi, u, v, w, eps, gamma, vel_scale, tiny, r);
-    if (rc == 0)
-        for (long c = 0; c < n; c++) phi_out[c] = phi[c] + dt * r[c];
-    free(r);
-    return rc;
+    return step_impl(nx, ny, nz, dx, phi, u, v, w, dt, eps, gamma, vel_scale, tiny, 0, phi_out);
+}
+
+ORACLE_API int oracle_step_face(int nx, int ny, int nz, double dx, const double *phi,
+                                const double *u, const double *v, const double *w,
+                                double dt, double eps, double gamma, double vel_scale,
+                                double tiny, double *phi_out)
+{
+    return step_impl(nx, ny, nz, dx, phi, u, v, w, dt, eps, gamma, vel_scale, tiny, 1, phi_out);
 }
 
 /* Mass and bounds of a field: out = {mass, sum, min, max, n_strict, n_tol}

@@ -242,6 +242,54 @@ def test_face_product_variant_is_not_stationary():
     assert np.abs(F - np.roll(F, 1)).max() > 1e-4
 
 
+def test_face_form_not_stationary_in_the_oracle():
+    """The oracle's face-product form moves the discrete equilibrium that its default
+    (centre-product) form leaves unchanged."""
+    n, h = 240, 1.0 / 240
+    p = discrete_equilibrium_1d(n, 1.0).reshape(1, 1, n)
+    z = np.zeros_like(p)
+    args = (z, z, z, h, 0.2 * h * h, h, 1.0)
+    assert np.abs(oracle.step(p, *args) - p).max() < 1e-15
+    assert np.abs(oracle.step(p, *args, sharpen="face") - p).max() > 1e-6
+
+
+def test_face_form_1d_closed_form():
+    """Where a face's two cells have equal normals n, the face-product flux exceeds the
+    centre-product flux by gamma n (phi_R - phi_L)^2 / 4 (phi_f (1 - phi_f) against the
+    mean of phi (1 - phi)), so on cells whose four neighbouring normals agree the two steps
+    differ by -(dt/dx) of the difference of that term across the cell."""
+    n = 64
+    h = 1.0 / n
+    x = I.centres(n, h)
+    phi = 0.5 * (1 + np.tanh((0.3 - np.abs(x - 0.5)) / (2 * 1.3 * h)))
+    phi = (phi + 0.02 * np.sin(6 * np.pi * x)).reshape(1, 1, n)
+    u = np.full((1, 1, n), 0.4)
+    z = np.zeros_like(phi)
+    dt, eps, gamma = 0.1 * h, 1.1 * h, 0.9
+    c = oracle.step(phi, u, z, z, h, dt, eps, gamma)[0, 0]
+    f = oracle.step(phi, u, z, z, h, dt, eps, gamma, sharpen="face")[0, 0]
+    p = phi[0, 0]
+    nn = np.sign(np.roll(p, -1) - np.roll(p, 1))
+    D = gamma * nn * (np.roll(p, -1) - p) ** 2 / 4          # on face i+1/2 (cells i, i+1)
+    expect = c - dt / h * (D - np.roll(D, 1))
+    ok = (np.roll(nn, 1) == nn) & (np.roll(nn, -1) == nn) & (nn != 0)
+    assert ok.sum() > n // 2
+    assert np.abs(f - expect)[ok].max() < 1e-15
+    assert np.abs(f - c)[ok].max() > 1e-5
+
+
+@pytest.mark.parametrize("solenoidal", [True, False])
+def test_face_form_conserves_and_is_symmetric(solenoidal):
+    """The face form telescopes like the centre form (conservation for any periodic u) and
+    keeps Eq. 16's phi -> 1 - phi symmetry for discretely solenoidal u."""
+    phi, u, v, w, h = rand_case((5, 6, 7), 23, solenoidal)
+    args = dict(dx=h, dt=0.2 * h * h, eps=h, gamma=1.2, sharpen="face")
+    out = oracle.step(phi, u, v, w, **args)
+    assert abs(out.sum() - phi.sum()) < 1e-12 * phi.size
+    if solenoidal:
+        assert np.abs(oracle.step(1 - phi, u, v, w, **args) - (1 - out)).max() < 1e-15
+
+
 def test_boundedness_theorem_random_boxes():
     """0 <= phi <= 1 (within machine eps) under Eq. 24 and A <= 1/(2 D_f).
 
@@ -308,10 +356,12 @@ def test_table1_e_eps():
         assert abs(E / ref - 1) < 0.03, (eoh, E, ref)
 
 
-def test_equivariance():
-    """Periodic shift, x<->y swap (with u<->v) and x-reflection (u -> -u)."""
+@pytest.mark.parametrize("sharpen", ["centre", "face"])
+def test_equivariance(sharpen):
+    """Periodic shift, x<->y swap (with u<->v) and x-reflection (u -> -u); for the face form
+    the reflection also pins the normal's two-sided interpolation to the face."""
     phi, u, v, w, h = rand_case((5, 6, 6), 9)
-    args = dict(dx=h, dt=0.2 * h * h, eps=h, gamma=1.1)
+    args = dict(dx=h, dt=0.2 * h * h, eps=h, gamma=1.1, sharpen=sharpen)
     base = oracle.step(phi, u, v, w, **args)
     r = lambda a: np.roll(np.roll(a, 2, 2), -1, 0)
     assert np.abs(oracle.step(r(phi), r(u), r(v), r(w), **args) - r(base)).max() == 0.0
