@@ -277,6 +277,21 @@ CDI_API int cdi_batch_get_launch(const cdi_batch *b, int *tile, int *zdepth, int
  * and records are as before the call.  Synchronises. */
 CDI_API int cdi_batch_autotune(cdi_batch *b, int reps, float *best_ms, void *stream);
 
+/* Sharpening form of the forward step.  CDI_SHARPEN_CENTRE (the default) is
+ * Section 2.2's: s = phi (1 - phi) n at cell centres, averaged onto the faces,
+ * the form Eq. 13 and Eq. 19 and the boundedness proof hold for.
+ * CDI_SHARPEN_FACE is the product of face values instead, the sharpening flux
+ * gamma phi_f (1 - phi_f) n_f with phi_f = (phi_L + phi_R)/2 and n_f =
+ * (n_L + n_R)/2 (the cell-centre unit normals interpolated to the face): not
+ * covered by the proof, and not stationary on the scheme's discrete
+ * equilibrium.  It runs on forward tile 0 with explicit Euler steps only;
+ * cdi_step_rk, cdi_run_rk and cdi_step_adjoint return CDI_ERR_ARG while it is
+ * set, and batches always use the centre form.  Setting a mode resets the
+ * forward launch configuration to the mode's default. */
+enum { CDI_SHARPEN_CENTRE = 0, CDI_SHARPEN_FACE = 1 };
+CDI_API int cdi_set_sharpening(cdi_grid *g, int mode);
+CDI_API int cdi_get_sharpening(const cdi_grid *g, int *mode);
+
 /* Kernels with a tunable launch configuration. */
 enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
 

@@ -25,6 +25,8 @@ CDI_EULER, CDI_RK2, CDI_RK3, CDI_RK4 = 0, 1, 2, 3
 CDI_CHECK_CONDITION = 1
 CDI_KERNEL_FORWARD, CDI_KERNEL_ADJOINT = 0, 1
 CDI_NCHUNKS_BALANCED = -1   # forward work split: equal contiguous shares per block
+CDI_SHARPEN_CENTRE, CDI_SHARPEN_FACE = 0, 1
+SHARPEN = {"centre": CDI_SHARPEN_CENTRE, "face": CDI_SHARPEN_FACE}
 FWD_TILES = 7
 ADJ_TILES = 4
 
@@ -72,6 +74,8 @@ SIGNATURES = {
     "cdi_step_adjoint": [_V, _V, _V, _V, _V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _V],
     "cdi_check_condition": [_Dbl, _Dbl, _Dbl, _I],
     "cdi_max_dt": [_Dbl, _Dbl, _Dbl, _I, _I, _P(_Dbl)],
+    "cdi_set_sharpening": [_V, _I],
+    "cdi_get_sharpening": [_V, _P(_I)],
     "cdi_set_launch": [_V, _I, _I, _I, _I],
     "cdi_get_launch": [_V, _I, _P(_I), _P(_I), _P(_I)],
     "cdi_autotune": [_V, _V, _V, _Dbl, _Dbl, _Dbl, _I, _P(_Dbl), _V],
@@ -285,6 +289,16 @@ class Grid:
                                 CDI_CHECK_CONDITION if check else 0, ctypes.byref(s),
                                 _stream(stream)))
         return s.as_dict()
+
+    def set_sharpening(self, mode):
+        """"centre" (Section 2.2, the default) or "face" (face-product sharpening, forward
+        tile 0 with Euler steps only)."""
+        _ck(lib().cdi_set_sharpening(self._h, SHARPEN[mode]))
+
+    def get_sharpening(self):
+        m = ctypes.c_int()
+        _ck(lib().cdi_get_sharpening(self._h, ctypes.byref(m)))
+        return {v: k for k, v in SHARPEN.items()}[m.value]
 
     def set_launch(self, which=CDI_KERNEL_FORWARD, tile=-1, blocks_per_sm=0, nchunks=0):
         """Force a launch configuration (tile < 0: the default)."""

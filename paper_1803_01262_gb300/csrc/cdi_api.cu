@@ -66,6 +66,7 @@ struct cdi_grid {
     // launch configuration of the forward and adjoint kernels
     LaunchCfg fwd, adj;
     LaunchCfg rk;  // Runge-Kutta stage kernels (set on first use; nblocks 0 = unset)
+    int sharpen;   // CDI_SHARPEN_CENTRE (Section 2.2) or CDI_SHARPEN_FACE
     // staging for cdi_step_host (owned, allocated on first use)
     void *stage_in, *stage_out;
     int sm_count;
@@ -116,14 +117,17 @@ static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, 
     if (tile < 0 || tile >= cdi::fwd_num_tiles())
         return fail(CDI_ERR_ARG, "forward tile %d out of range", tile);
     if (rk && !cdi::fwd_tile_has_rk(tile)) return fail(CDI_ERR_ARG, "no Runge-Kutta kernel for tile %d", tile);
+    const bool face = g->sharpen == CDI_SHARPEN_FACE;
+    if (face && (rk || tile != 0))
+        return fail(CDI_ERR_ARG, "face-product sharpening runs on forward tile 0 with Euler steps only");
     const int es = (int)esize(g);
     if (cdi::fwd_tile_is_vec(tile) && g->nx % (16 / es) != 0)
         return fail(CDI_ERR_ARG, "vector tile needs nx %% %d == 0", 16 / es);
     if (tile == 6 && !cdi::tma_eligible(es, g->nx, g->ny, g->nz))
         return fail(CDI_ERR_ARG, "tile 6 needs nx %% %d == 0 and ny %% 16 == 0", 16 * (16 / es));
     int resident = 0;
-    cudaError_t e = g->dtype == CDI_F64 ? cdi::fwd_occupancy<double>(tile, rk, &resident)
-                                        : cdi::fwd_occupancy<float>(tile, rk, &resident);
+    cudaError_t e = g->dtype == CDI_F64 ? cdi::fwd_occupancy<double>(tile, rk, &resident, face)
+                                        : cdi::fwd_occupancy<float>(tile, rk, &resident, face);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (resident < 1) return fail(CDI_ERR_CUDA, "forward kernel does not fit on an SM");
     if (blocks_per_sm > 0 && blocks_per_sm < resident) resident = blocks_per_sm;
@@ -171,6 +175,7 @@ static int fwd_cfg_rk(const cdi_grid *g, int tile, LaunchCfg *c) { return fwd_cf
 
 static int default_fwd_tile(const cdi_grid *g)
 {
+    if (g->sharpen == CDI_SHARPEN_FACE) return 0;
     const int vx = 16 / (int)esize(g);
     if (g->nx % vx == 0 && g->nx >= 48) return g->ny >= 12 ? 4 : 5;
     return (g->nx >= 32 && g->ny >= 16) ? 1 : 3;
@@ -473,7 +478,8 @@ static int step_t(cdi_grid *g, const void *in, void *out, double dt, double eps,
     a.rk_alpha = a.rk_delta = a.rk_mu = a.rk_beta = T(0);
     if (g->fwd.nblocks > g->capacity)
         return fail(CDI_ERR_STATE, "launch configuration exceeds the reduction scratch");
-    cudaError_t e = cdi::launch_fwd<T>(a, g->fwd.tile, g->fwd.nblocks, g->fwd.nchunks, false, s);
+    cudaError_t e = cdi::launch_fwd<T>(a, g->fwd.tile, g->fwd.nblocks, g->fwd.nchunks, false, s,
+                                       g->sharpen == CDI_SHARPEN_FACE);
     if (e != cudaSuccess) return cuda_fail(e, "forward step launch");
     return CDI_OK;
 }
@@ -587,6 +593,7 @@ static int check_rk_args(cdi_grid *g, const void *a, void *b, void *w1, void *w2
 int cdi_step_rk(cdi_grid *g, const void *phi_in, void *phi_out, void *work1, void *work2, double dt,
                 double eps, double gamma, double t, double period, int scheme, int flags, void *stream)
 {
+    if (g && g->sharpen == CDI_SHARPEN_FACE) return fail(CDI_ERR_ARG, "Runge-Kutta stages use the centre-product sharpening");
     if (int rc = check_rk_args(g, phi_in, phi_out, work1, work2, dt, eps, gamma, scheme, flags)) return rc;
     return rk_step_impl(g, phi_in, phi_out, work1, work2, dt, eps, gamma, t, period, scheme,
                         (cudaStream_t)stream);
@@ -597,6 +604,7 @@ int cdi_run_rk(cdi_grid *g, void *buf_a, void *buf_b, void *work1, void *work2, 
                void *stream)
 {
     if (nsteps < 0) return fail(CDI_ERR_ARG, "nsteps must be >= 0");
+    if (g && g->sharpen == CDI_SHARPEN_FACE) return fail(CDI_ERR_ARG, "Runge-Kutta stages use the centre-product sharpening");
     if (int rc = check_rk_args(g, buf_a, buf_b, work1, work2, dt, eps, gamma, scheme, flags)) return rc;
     void *src = buf_a, *dst = buf_b;
     for (int i = 0; i < nsteps; ++i) {
@@ -753,6 +761,8 @@ int cdi_step_adjoint(cdi_grid *g, const void *phi_k, const void *lam_next, void 
                      void *stream)
 {
     if (int rc = check_step_args(g, phi_k, lam_k, dt, eps, gamma, vel_scale)) return rc;
+    if (g->sharpen == CDI_SHARPEN_FACE)
+        return fail(CDI_ERR_ARG, "the adjoint is of the centre-product step (Section 2.2)");
     if (!lam_next || !aligned16(lam_next)) return fail(CDI_ERR_ARG, "lam_next NULL or misaligned");
     const size_t bytes = (size_t)g->n * esize(g);
     const char *pa = (const char *)lam_next, *pb = (const char *)lam_k;
@@ -799,6 +809,30 @@ int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchu
     return fail(CDI_ERR_ARG, "unknown kernel %d", which);
 }
 
+int cdi_set_sharpening(cdi_grid *g, int mode)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (mode != CDI_SHARPEN_CENTRE && mode != CDI_SHARPEN_FACE) return fail(CDI_ERR_ARG, "sharpening mode %d", mode);
+    const int old = g->sharpen;
+    g->sharpen = mode;
+    LaunchCfg c;
+    if (int rc = fwd_cfg(g, default_fwd_tile(g), 0, 0, &c)) {
+        g->sharpen = old;
+        return rc;
+    }
+    g->fwd = c;
+    g->rk.nblocks = 0;
+    return CDI_OK;
+}
+
+int cdi_get_sharpening(const cdi_grid *g, int *mode)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (!mode) return fail(CDI_ERR_ARG, "mode is NULL");
+    *mode = g->sharpen;
+    return CDI_OK;
+}
+
 int cdi_get_launch(const cdi_grid *g, int which, int *tile, int *nblocks, int *nchunks)
 {
     if (int rc = check_grid(g)) return rc;
@@ -830,6 +864,7 @@ int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps, d
     const int chunk_opts[] = {CDI_NCHUNKS_BALANCED, 0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32};
     for (int tile = 0; tile < cdi::fwd_num_tiles() && rc == CDI_OK; ++tile) {
         if (cdi::fwd_tile_is_vec(tile) && g->nx % (16 / (int)esize(g)) != 0) continue;
+        if (g->sharpen == CDI_SHARPEN_FACE && tile != 0) continue;
         for (int oi = 0; oi < (int)(sizeof(chunk_opts) / sizeof(int)); ++oi) {
             if (chunk_opts[oi] > g->nz) continue;
             LaunchCfg c;

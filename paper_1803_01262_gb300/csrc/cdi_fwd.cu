@@ -371,7 +371,7 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
 // ===========================================================================
 // Scalar kernel (any extents): the per-unit body is in cdi_fwd_scalar.cuh.
 
-template <typename T, int BX, int BY, bool RK>
+template <typename T, int BX, int BY, bool RK, bool FACE = false>
 __global__ void __launch_bounds__(BX * BY)
 fwd_kernel(const FwdArgs<T> a, const int nchunks)
 {
@@ -382,7 +382,8 @@ fwd_kernel(const FwdArgs<T> a, const int nchunks)
     acc.init();
     UnitIter<BX, BY> units(ntiles, a.nz, nchunks);
     Unit un;
-    while (units.next(un, ntiles, tiles_x, a.nz, nchunks)) scalar_unit<T, BX, BY, RK>(a, un, acc, smem_raw);
+    while (units.next(un, ntiles, tiles_x, a.nz, nchunks))
+        scalar_unit<T, BX, BY, RK, SCALAR_PF, FACE>(a, un, acc, smem_raw);
     reduce_and_finish(acc.partial(), a.red);
 }
 
@@ -428,8 +429,12 @@ static cudaError_t occ(K kernel, int threads, size_t smem, int *resident)
 bool fwd_tile_has_rk(int tile) { return tile == 1 || tile == 3 || tile == 4; }
 
 template <typename T>
-cudaError_t fwd_occupancy(int tile, bool rk, int *resident)
+cudaError_t fwd_occupancy(int tile, bool rk, int *resident, bool face)
 {
+    if (face) {
+        if (rk || tile != 0) return cudaErrorInvalidValue;
+        return occ(fwd_kernel<T, 32, 8, false, true>, 256, FwdSmem<T, 32, 8>::bytes, resident);
+    }
     if (rk) {
         switch (tile) {
         case 1: return occ(fwd_kernel<T, 32, 16, true>, 512, FwdSmem<T, 32, 16>::bytes, resident);
@@ -449,12 +454,18 @@ cudaError_t fwd_occupancy(int tile, bool rk, int *resident)
     default: return cudaErrorInvalidValue;
     }
 }
-template cudaError_t fwd_occupancy<float>(int, bool, int *);
-template cudaError_t fwd_occupancy<double>(int, bool, int *);
+template cudaError_t fwd_occupancy<float>(int, bool, int *, bool);
+template cudaError_t fwd_occupancy<double>(int, bool, int *, bool);
 
 template <typename T>
-cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, bool rk, cudaStream_t s)
+cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, bool rk, cudaStream_t s,
+                       bool face)
 {
+    if (face) {  // face-product sharpening: tile 0 only, Euler only
+        if (rk || tile != 0) return cudaErrorInvalidValue;
+        fwd_kernel<T, 32, 8, false, true><<<nblocks, dim3(32, 8), FwdSmem<T, 32, 8>::bytes, s>>>(a, nchunks);
+        return cudaGetLastError();
+    }
     if (rk) {
         switch (tile) {
         case 1: fwd_kernel<T, 32, 16, true><<<nblocks, dim3(32, 16), FwdSmem<T, 32, 16>::bytes, s>>>(a, nchunks); break;
@@ -483,8 +494,8 @@ cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, 
     return cudaGetLastError();
 }
 
-template cudaError_t launch_fwd<float>(const FwdArgs<float> &, int, int, int, bool, cudaStream_t);
-template cudaError_t launch_fwd<double>(const FwdArgs<double> &, int, int, int, bool, cudaStream_t);
+template cudaError_t launch_fwd<float>(const FwdArgs<float> &, int, int, int, bool, cudaStream_t, bool);
+template cudaError_t launch_fwd<double>(const FwdArgs<double> &, int, int, int, bool, cudaStream_t, bool);
 
 // ---------------------------------------------------------------------------
 // Stand-alone reductions: statistics of any field, and max |component| of

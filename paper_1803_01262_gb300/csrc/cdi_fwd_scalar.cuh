@@ -36,7 +36,9 @@ struct FwdSmem {
         sizeof(T) * (NSLOT * PY * PX + 2 * BY * (BX + 2) + 2 * (BY + 2) * BX + NVS * VPL);
 };
 
-template <typename T, int BX, int BY, bool RK = false, int PF = SCALAR_PF>
+// FACE: the non-default face-product sharpening, gamma phi_f (1 - phi_f) n_f with
+// phi_f and n_f the averages of the two cells (the smem s arrays then hold n).
+template <typename T, int BX, int BY, bool RK = false, int PF = SCALAR_PF, bool FACE = false>
 __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un, Acc<T> &acc,
                                             unsigned char *smem_raw)
 {
@@ -81,10 +83,20 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
         const T g2 = sp[mp][Y][X] - sp[mm][Y][X];
         const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, NumLim<T>::tiny())));
         const T inv = rsqrt_t(q);
-        const T wgt = p * (T(1) - p) * inv;
+        const T wgt = FACE ? inv : p * (T(1) - p) * inv;
         s0 = wgt * g0;
         s1 = wgt * g1;
         s2 = wgt * g2;
+    };
+    // Face flux with the sharpening in the configured form (sl, sr: the two cells'
+    // s, or their normals for FACE).
+    auto face_flux = [&](T cadv_u, T pl, T pr, T sl, T sr) {
+        if constexpr (FACE) {
+            const T pf = T(0.5) * (pl + pr);
+            return cadv_u * (pl + pr) - c_dif * (pr - pl) + c_shp * (pf * (T(1) - pf) * (sl + sr));
+        } else {
+            return flux(cadv_u, c_dif, c_shp, pl, pr, sl, sr);
+        }
     };
     auto sharp_plane = [&](int z, T &szc) {
         T q0, q1;
@@ -190,7 +202,7 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
     {
         const T pm = sp[(z0 - 1) & (NSLOT - 1)][ty + 2][tx + 2];
         const T pc = sp[z0 & (NSLOT - 1)][ty + 2][tx + 2];
-        Fzm = flux(c_adv * wlo, c_dif, c_shp, pm, pc, szm, szc);
+        Fzm = face_flux(c_adv * wlo, pm, pc, szm, szc);
     }
 
     // Wrapped offset of the phi plane issued next (k+2+PF) and of the next
@@ -242,8 +254,18 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
         adv = fma(vc, pc + pyp, adv);
         adv = fma(-vm, pym + pc, adv);
         const T dif = fma(T(-4), pc, (pxm + pxp) + (pym + pyp));
-        const T shp = (sxp - sxm) + (syp - sym);
-        const T Fzp = flux(c_adv * wc, c_dif, c_shp, pc, pzp, szc, szn);
+        T shp;
+        if constexpr (FACE) {
+            // each face: phi_f (1 - phi_f) (n_L + n_R); the cell's own normal does not cancel
+            const T nxc = sx[b][ty][tx + 1], nyc = sy[b][ty + 1][tx];
+            const T fxp = T(0.5) * (pc + pxp), fxm = T(0.5) * (pxm + pc);
+            const T fyp = T(0.5) * (pc + pyp), fym = T(0.5) * (pym + pc);
+            shp = (fxp * (T(1) - fxp) * (nxc + sxp) - fxm * (T(1) - fxm) * (sxm + nxc)) +
+                  (fyp * (T(1) - fyp) * (nyc + syp) - fym * (T(1) - fym) * (sym + nyc));
+        } else {
+            shp = (sxp - sxm) + (syp - sym);
+        }
+        const T Fzp = face_flux(c_adv * wc, pc, pzp, szc, szn);
         const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, Fzp - Fzm)));
         T o = fma(-c_upd, div, pc);
         if (own) {

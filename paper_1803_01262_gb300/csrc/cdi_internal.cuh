@@ -97,7 +97,7 @@ long long fwd_tiles_xy(int tile, int esize, int nx, int ny);
 
 // Blocks of the forward kernel with this tile that fit on one SM (sets the smem attribute).
 template <typename T>
-cudaError_t fwd_occupancy(int tile, bool rk, int *resident);
+cudaError_t fwd_occupancy(int tile, bool rk, int *resident, bool face = false);
 
 // Tile 6: tensor-memory-accelerator staging (cdi_fwd_tma.cu); needs
 // nx % W == 0 and ny % 16 == 0 with W = 16 * 16 / sizeof(T).
@@ -107,11 +107,13 @@ cudaError_t tma_occupancy(int *resident);
 template <typename T>
 cudaError_t launch_fwd_tma(const FwdArgs<T> &a, int nblocks, int nchunks, cudaStream_t s);
 
-// rk selects the Runge-Kutta stage variant (tiles with fwd_tile_has_rk only).
+// rk selects the Runge-Kutta stage variant (tiles with fwd_tile_has_rk only);
+// face the face-product sharpening (tile 0, Euler only).
 bool fwd_tile_has_rk(int tile);
 
 template <typename T>
-cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, bool rk, cudaStream_t s);
+cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, bool rk, cudaStream_t s,
+                       bool face = false);
 
 template <typename T>
 cudaError_t launch_stats(const T *phi, long long n, T tol, RedScratch red, int nblocks,
