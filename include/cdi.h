@@ -307,7 +307,8 @@ enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
  * round-robin by the persistent blocks; CDI_NCHUNKS_BALANCED gives every block
  * an equal contiguous share of the tile-planes (tile-major, cut at column
  * ends); 0 picks one of these from a cost model.  Adjoint
- * tiles: 0..2 (32x8, 32x16, 32x4 cells), nchunks sets its z chunking.  Every
+ * tiles: 0..2 (32x8, 32x16, 32x4 cells) and 3 (vector), nchunks sets the z
+ * chunking (CDI_NCHUNKS_BALANCED: balanced shares, tile 3 only).  Every
  * configuration computes the same result up to the order of the reduction
  * partials. */
 CDI_API int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchunks);

@@ -367,8 +367,6 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
     const long long plane = (long long)nx * ny;
     const int tiles_x = (nx + W - 1) / W;
     const int ntiles = tiles_x * ((ny + H - 1) / H);
-    const int zc = (nz + nchunks - 1) / nchunks;
-    const int units = ntiles * ((nz + zc - 1) / zc);
     const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_upd = a.c.c_upd, c_sb = a.c_shp_adj;
     const T c_vel = a.c_vel;
     const bool want_vel = a.gu != nullptr;
@@ -445,8 +443,9 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
         return p * (T(1) - p) * inv * fma(sb0, floor_part(inv), n1 * x2_ - n2 * x1_);
     };
 
-    for (int u = blockIdx.x; u < units; u += gridDim.x) {
-        const Unit un = unit_of(u, ntiles, tiles_x, W, H, zc, nz);
+    UnitIter<W, H> units(ntiles, nz, nchunks);
+    Unit un;
+    while (units.next(un, ntiles, tiles_x, nz, nchunks)) {
         const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
 
         // The 64 ring threads issue every 16-byte copy; global in-plane
@@ -723,10 +722,18 @@ static cudaError_t launch_adj_vec(const AdjArgs<T> &a, cudaStream_t s)
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    const int nchunks = (a.nz + a.zchunk - 1) / a.zchunk;
-    const int zc = (a.nz + nchunks - 1) / nchunks;
-    const long long units = (long long)((a.nx + C::W - 1) / C::W) * ((a.ny + C::H - 1) / C::H) *
-                            ((a.nz + zc - 1) / zc);
+    // zchunk < 0: balanced shares of the tile-planes (UnitIter); else z chunks
+    const long long tiles = (long long)((a.nx + C::W - 1) / C::W) * ((a.ny + C::H - 1) / C::H);
+    int nchunks;
+    long long units;
+    if (a.zchunk < 0) {
+        nchunks = -1;
+        units = tiles * a.nz;
+    } else {
+        nchunks = (a.nz + a.zchunk - 1) / a.zchunk;
+        const int zc = (a.nz + nchunks - 1) / nchunks;
+        units = tiles * ((a.nz + zc - 1) / zc);
+    }
     long long nb = (long long)resident * sms;
     if (nb > units) nb = units;
     adj_vec_kernel<T, 16, 8><<<(int)nb, C::NT, C::bytes, s>>>(a, nchunks);

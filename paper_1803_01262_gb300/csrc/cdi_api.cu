@@ -182,7 +182,8 @@ static int default_fwd_tile(const cdi_grid *g)
 }
 
 // Vector adjoint: z chunking from the forward cost model (rounds of the
-// persistent grid against per-unit prologues).
+// persistent grid against per-unit prologues), or -1 for the balanced split
+// when that model favours it.
 static int adj_vec_zchunk(const cdi_grid *g)
 {
     int resident = 0;
@@ -207,6 +208,9 @@ static int adj_vec_zchunk(const cdi_grid *g)
             nch = nc;
         }
     }
+    const long long P = (tiles * nz + G - 1) / G;
+    const double bal = (double)P + 3.0 * (double)((P + nz - 1) / nz + 1);
+    if (bal < best * (1.0 - 1e-9) && tiles * nz < (1LL << 31)) return -1;
     return (nz + nch - 1) / nch;
 }
 
@@ -801,7 +805,18 @@ int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchu
         if (cdi::adj_tile_is_vec(tile) && !cdi::adj_tile_is_vec(c.tile)) c.zchunk = adj_vec_zchunk(g);
         c.tile = tile;
         if (nchunks > 0) c.zchunk = (g->nz + nchunks - 1) / nchunks;
-        if (cdi::adj_blocks(c.tile, c.zchunk, g->nx, g->ny, g->nz) > g->capacity)
+        if (nchunks == CDI_NCHUNKS_BALANCED) {
+            if (!cdi::adj_tile_is_vec(tile)) return fail(CDI_ERR_ARG, "balanced split: vector adjoint tile only");
+            int bw, bh;
+            cdi::adj_vec_tile_dims((int)esize(g), &bw, &bh);
+            if ((long long)((g->nx + bw - 1) / bw) * ((g->ny + bh - 1) / bh) * g->nz >= (1LL << 31))
+                return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
+            c.zchunk = -1;
+        } else if (nchunks < 0) {
+            return fail(CDI_ERR_ARG, "nchunks %d", nchunks);
+        }
+        if (c.zchunk < 0 && !cdi::adj_tile_is_vec(c.tile)) c.zchunk = adj_default(g).zchunk;
+        if (c.zchunk > 0 && cdi::adj_blocks(c.tile, c.zchunk, g->nx, g->ny, g->nz) > g->capacity)
             return fail(CDI_ERR_ARG, "adjoint configuration needs more blocks than the scratch holds");
         g->adj = c;
         return CDI_OK;
@@ -840,7 +855,10 @@ int cdi_get_launch(const cdi_grid *g, int which, int *tile, int *nblocks, int *n
     if (!c) return fail(CDI_ERR_ARG, "unknown kernel %d", which);
     if (tile) *tile = c->tile;
     if (nblocks) *nblocks = c->nblocks;
-    if (nchunks) *nchunks = which == CDI_KERNEL_FORWARD ? c->nchunks : (g->nz + c->zchunk - 1) / c->zchunk;
+    if (nchunks)
+        *nchunks = which == CDI_KERNEL_FORWARD ? c->nchunks
+                   : c->zchunk < 0           ? CDI_NCHUNKS_BALANCED
+                                             : (g->nz + c->zchunk - 1) / c->zchunk;
     return CDI_OK;
 }
 

@@ -135,6 +135,43 @@ def test_adjoint_floor_regime(dtype, tile):
         assert np.abs(unit - ref).max() > 1e-4 * scale
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("shape", [(64, 64, 256), (9, 21, 68), (2, 17, 132), (20, 9, 64)])
+@pytest.mark.parametrize("with_vel", [False, True])
+def test_adjoint_balanced_split(dtype, shape, with_vel):
+    """The vector adjoint with equal contiguous tile-plane shares per block (shares cut
+    inside a column and one-plane shares) gives the oracle's adjoint step."""
+    phi, u, v, w, lam, h = case(shape, 13 + shape[0], dtype == torch.float32)
+    t = np.float64 if dtype == torch.float64 else np.float32
+    phi, u, v, w, lam = (np.asarray(x, t).astype(np.float64) for x in (phi, u, v, w, lam))
+    dt, eps, gamma, vs = 0.15 * h * h / (1.3 * 1.1 * h), 1.1 * h, 1.3, 0.7
+    nz, ny, nx = shape
+    g = cdi.Grid(nx, ny, nz, h, dtype)
+    g.set_velocity(*[dev(x, dtype) for x in (u, v, w)])
+    g.set_launch(cdi.CDI_KERNEL_ADJOINT, 3, 0, cdi.CDI_NCHUNKS_BALANCED)
+    assert g.get_launch(cdi.CDI_KERNEL_ADJOINT)["nchunks"] == cdi.CDI_NCHUNKS_BALANCED
+    out = torch.empty(shape, dtype=dtype, device="cuda")
+    grads = None
+    if with_vel:
+        g0 = np.random.default_rng(6).standard_normal((3,) + shape)
+        grads = [dev(x, dtype) for x in g0]
+    g.step_adjoint(dev(phi, dtype), dev(lam, dtype), out, dt, eps, gamma, vs, grads=grads)
+    ref = oracle.adjoint(phi, u, v, w, lam, h, dt, eps, gamma, vs, want_vel=with_vel,
+                         tiny=oracle.adjoint_floor_of(t))
+    if with_vel:
+        ref, rgu, rgv, rgw = ref
+    scale = max(1.0, np.abs(ref).max())
+    tol = 1e-12 if dtype == torch.float64 else 2e-6
+    assert np.abs(out.double().cpu().numpy() - ref).max() <= tol * scale
+    if with_vel:
+        for gd, rg, base in zip(grads, (rgu, rgv, rgw), g0):
+            base = np.asarray(base, t).astype(np.float64)
+            s2 = max(1.0, np.abs(rg).max())
+            assert np.abs(gd.double().cpu().numpy() - (base + rg)).max() <= tol * s2 * 4
+    with pytest.raises(cdi.CDIError):
+        g.set_launch(cdi.CDI_KERNEL_ADJOINT, 0, 0, cdi.CDI_NCHUNKS_BALANCED)
+
+
 def test_adjoint_constant_lambda_gpu():
     """lam' = const gives lam = lam' exactly (J^T 1 = 1 from conservation)."""
     shape = (6, 10, 40)
