@@ -180,7 +180,15 @@ CDI_API int cdi_mass_and_bounds(cdi_grid *g, const void *phi, cdi_stats *out, vo
 /* Host-buffer step: copies phi_in (host, ideally pinned) to the device,
  * performs cdi_step with the velocity set by cdi_set_velocity, copies
  * phi_out and the statistics back to host memory and synchronises.  Uses
- * two device staging buffers owned by the grid (allocated on first use). */
+ * two device staging buffers owned by the grid (allocated on first use).
+ * For nz >= 16 the step runs as a pipeline of 8 z slabs on two copy streams
+ * of the grid and the given stream: the two seam planes and then the slabs
+ * are copied in, a slab is stepped as soon as the piece holding its halo
+ * planes has landed and copied out while later slabs are still arriving, so
+ * both copy directions and the kernel overlap.
+ * The slabs run the vector kernel where nx allows (else the one-cell-per-
+ * thread kernel), so the result equals cdi_step's up to that kernel's
+ * rounding (bit for bit when the grid's forward tile is the same). */
 CDI_API int cdi_step_host(cdi_grid *g, const void *phi_in_host, void *phi_out_host, double dt,
                   double eps, double gamma, double vel_scale, int flags,
                   cdi_stats *stats_out, void *stream);

@@ -66,9 +66,14 @@ struct cdi_grid {
     // launch configuration of the forward and adjoint kernels
     LaunchCfg fwd, adj;
     LaunchCfg rk;  // Runge-Kutta stage kernels (set on first use; nblocks 0 = unset)
+    LaunchCfg slab;  // z slabs of the pipelined host step (set on first use; nblocks 0 = unset)
     int sharpen;   // CDI_SHARPEN_CENTRE (Section 2.2) or CDI_SHARPEN_FACE
-    // staging for cdi_step_host (owned, allocated on first use)
+    // staging for cdi_step_host (owned, allocated on first use), and the copy
+    // streams and events of its slab pipeline (created on first use)
     void *stage_in, *stage_out;
+    bool pipe_ready;
+    cudaStream_t hs_in, hs_out;
+    cudaEvent_t ev_start, ev_out, ev_in[8], ev_c[8];
     int sm_count;
 };
 
@@ -112,7 +117,7 @@ static void reset_run_host(StatsRec *r)
 //   chunks: max(rounds * (planes per unit + 3), units * (planes per unit + 1) / blocks)
 //   balanced: P + 3 (ceil(P / nz) + 1), P = ceil(tiles * nz / blocks).
 static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, LaunchCfg *c,
-                   bool rk = false)
+                   bool rk = false, bool slab = false)
 {
     if (tile < 0 || tile >= cdi::fwd_num_tiles())
         return fail(CDI_ERR_ARG, "forward tile %d out of range", tile);
@@ -126,8 +131,8 @@ static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, 
     if (tile == 6 && !cdi::tma_eligible(es, g->nx, g->ny, g->nz))
         return fail(CDI_ERR_ARG, "tile 6 needs nx %% %d == 0 and ny %% 16 == 0", 16 * (16 / es));
     int resident = 0;
-    cudaError_t e = g->dtype == CDI_F64 ? cdi::fwd_occupancy<double>(tile, rk, &resident, face)
-                                        : cdi::fwd_occupancy<float>(tile, rk, &resident, face);
+    cudaError_t e = g->dtype == CDI_F64 ? cdi::fwd_occupancy<double>(tile, rk, &resident, face, slab)
+                                        : cdi::fwd_occupancy<float>(tile, rk, &resident, face, slab);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (resident < 1) return fail(CDI_ERR_CUDA, "forward kernel does not fit on an SM");
     if (blocks_per_sm > 0 && blocks_per_sm < resident) resident = blocks_per_sm;
@@ -303,6 +308,16 @@ int cdi_create_grid(cdi_grid **out, int nx, int ny, int nz, double dx, int dtype
 int cdi_destroy_grid(cdi_grid *g)
 {
     if (!g) return CDI_OK;
+    if (g->pipe_ready) {
+        cudaStreamDestroy(g->hs_in);
+        cudaStreamDestroy(g->hs_out);
+        cudaEventDestroy(g->ev_start);
+        cudaEventDestroy(g->ev_out);
+        for (int j = 0; j < 8; ++j) {
+            cudaEventDestroy(g->ev_in[j]);
+            cudaEventDestroy(g->ev_c[j]);
+        }
+    }
     cudaFree(g->partials);
     cudaFree(g->counter);
     cudaFree(g->rec);
@@ -463,9 +478,12 @@ static cdi::StepCoef<T> coefs(const cdi_grid *g, double dt, double eps, double g
     return c;
 }
 
+// One forward step, or (z_hi > 0) its planes [z_lo, z_hi) folded into the record:
+// combine adds to the record's per-step fields, update_run closes the step.
 template <typename T>
 static int step_t(cdi_grid *g, const void *in, void *out, double dt, double eps, double gamma,
-                  double vs, cudaStream_t s)
+                  double vs, cudaStream_t s, int z_lo = 0, int z_hi = 0, int combine = 0,
+                  int update_run = 1)
 {
     cdi::FwdArgs<T> a;
     a.phi = (const T *)in;
@@ -474,15 +492,19 @@ static int step_t(cdi_grid *g, const void *in, void *out, double dt, double eps,
     a.v = (const T *)(g->v ? g->v : g->u);  // ny == nz == 1: v is inert
     a.w = (const T *)(g->w ? g->w : g->u);  // nz == 1: w is inert
     a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
+    a.z_lo = z_lo;
+    a.z_hi = z_hi;
     a.c = coefs<T>(g, dt, eps, gamma, vs);
-    a.red = scratch(g, g->rec, 1);
+    a.red = scratch(g, g->rec, update_run);
+    a.red.combine = combine;
     a.rk_base = nullptr;
     a.rk_q = nullptr;
     a.rk_qout = nullptr;
     a.rk_alpha = a.rk_delta = a.rk_mu = a.rk_beta = T(0);
-    if (g->fwd.nblocks > g->capacity)
+    const LaunchCfg &c = z_hi > 0 ? g->slab : g->fwd;
+    if (c.nblocks > g->capacity)
         return fail(CDI_ERR_STATE, "launch configuration exceeds the reduction scratch");
-    cudaError_t e = cdi::launch_fwd<T>(a, g->fwd.tile, g->fwd.nblocks, g->fwd.nchunks, false, s,
+    cudaError_t e = cdi::launch_fwd<T>(a, c.tile, c.nblocks, c.nchunks, false, s,
                                        g->sharpen == CDI_SHARPEN_FACE);
     if (e != cudaSuccess) return cuda_fail(e, "forward step launch");
     return CDI_OK;
@@ -712,6 +734,82 @@ int cdi_mass_and_bounds(cdi_grid *g, const void *phi, cdi_stats *out, void *stre
     return read_rec(g, g->rec2, out, s);
 }
 
+// cdi_step_host in S = 8 equal z slabs: the two planes of the periodic seam
+// (nz-2, nz-1) are copied in first, then slab j = [b_j, b_j+1) in order on
+// hs_in; slab j is stepped on the caller's stream as soon as the piece holding
+// its upper halo planes has landed, and copied out on hs_out once stepped, so
+// both copy directions and the kernel overlap.  The record is built by folding
+// the slabs' partial results (combine) and closed by the last slab.  (256^3
+// FP32: 2 slabs 0.78 ms per step, 4: 0.65, 8: 0.58, 16: 0.61, 32: 0.88 -- per-
+// slab copy and launch costs against overlap; slabs thinning towards the end
+// 0.62; the unpipelined step 0.80.)
+static int step_host_pipelined(cdi_grid *g, const void *hin, void *hout, double dt, double eps,
+                               double gamma, double vs, cudaStream_t s)
+{
+    cudaError_t e;
+    if (!g->pipe_ready) {
+        if ((e = cudaStreamCreateWithFlags(&g->hs_in, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate");
+        if ((e = cudaStreamCreateWithFlags(&g->hs_out, cudaStreamNonBlocking)) != cudaSuccess) {
+            cudaStreamDestroy(g->hs_in);
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        e = cudaEventCreateWithFlags(&g->ev_start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming);
+        for (int j = 0; j < 8 && e == cudaSuccess; ++j) {
+            e = cudaEventCreateWithFlags(&g->ev_in[j], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ev_c[j], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");  // (process-lifetime leak only)
+        g->pipe_ready = true;
+    }
+    if (g->slab.nblocks == 0) {  // tile 4 where nx allows, else 0; balanced shares
+        const int tile = cdi::fwd_tile_is_vec(4) && g->nx % (16 / (int)esize(g)) == 0 ? 4 : 0;
+        if (int rc = fwd_cfg(g, tile, 0, CDI_NCHUNKS_BALANCED, &g->slab, false, true)) return rc;
+    }
+    const int S = 8, nz = g->nz;  // nz >= 16: every slab holds the two halo planes
+    int b[S + 1];
+    for (int j = 0; j <= S; ++j) b[j] = (int)((long long)j * nz / S);
+    const size_t pb = (size_t)g->nx * g->ny * esize(g);
+    const char *src = (const char *)hin;
+    char *dst = (char *)hout;
+    char *si = (char *)g->stage_in, *so = (char *)g->stage_out;
+    // the copies start after the work already queued on the caller's stream
+    if ((e = cudaEventRecord(g->ev_start, s)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(g->hs_in, g->ev_start, 0)) != cudaSuccess)
+        return cuda_fail(e, "pipeline start");
+    auto h2d = [&](int z0, int z1) {
+        if (z1 <= z0) return cudaSuccess;
+        return cudaMemcpyAsync(si + (size_t)z0 * pb, src + (size_t)z0 * pb, (size_t)(z1 - z0) * pb,
+                               cudaMemcpyHostToDevice, g->hs_in);
+    };
+    if ((e = h2d(nz - 2, nz)) != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+    for (int j = 0; j < S; ++j) {
+        if ((e = h2d(b[j], j == S - 1 ? nz - 2 : b[j + 1])) != cudaSuccess ||
+            (e = cudaEventRecord(g->ev_in[j], g->hs_in)) != cudaSuccess)
+            return cuda_fail(e, "host-to-device copy");
+    }
+    for (int j = 0; j < S; ++j) {
+        // the halo above slab j lies in piece j+1 (the last slab wraps onto slab 0
+        // and the seam planes, both landed before it)
+        const int need = j + 1 < S ? j + 1 : S - 1;
+        if ((e = cudaStreamWaitEvent(s, g->ev_in[need], 0)) != cudaSuccess) return cuda_fail(e, "wait");
+        int rc = g->dtype == CDI_F64
+                     ? step_t<double>(g, si, so, dt, eps, gamma, vs, s, b[j], b[j + 1], j > 0, j == S - 1)
+                     : step_t<float>(g, si, so, dt, eps, gamma, vs, s, b[j], b[j + 1], j > 0, j == S - 1);
+        if (rc) return rc;
+        const size_t off = (size_t)b[j] * pb, len = (size_t)(b[j + 1] - b[j]) * pb;
+        if ((e = cudaEventRecord(g->ev_c[j], s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(g->hs_out, g->ev_c[j], 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(dst + off, so + off, len, cudaMemcpyDeviceToHost, g->hs_out)) != cudaSuccess)
+            return cuda_fail(e, "device-to-host copy");
+    }
+    if ((e = cudaEventRecord(g->ev_out, g->hs_out)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s, g->ev_out, 0)) != cudaSuccess)
+        return cuda_fail(e, "pipeline end");
+    return CDI_OK;
+}
+
 int cdi_step_host(cdi_grid *g, const void *phi_in_host, void *phi_out_host, double dt, double eps,
                   double gamma, double vel_scale, int flags, cdi_stats *stats_out, void *stream)
 {
@@ -724,6 +822,18 @@ int cdi_step_host(cdi_grid *g, const void *phi_in_host, void *phi_out_host, doub
         if ((e = cudaMalloc(&g->stage_out, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc(stage)");
     }
     cudaStream_t s = (cudaStream_t)stream;
+    // slab pipeline when every slab holds at least the two halo planes (the
+    // default sharpening form only)
+    if (g->nz >= 16 && g->sharpen == CDI_SHARPEN_CENTRE) {
+        if (int rc = check_step_args(g, g->stage_in, g->stage_out, dt, eps, gamma, vel_scale)) return rc;
+        if (flags & CDI_CHECK_CONDITION)
+            if (int rc = check_condition_flag(g, dt, eps, gamma, vel_scale)) return rc;
+        if (int rc = step_host_pipelined(g, phi_in_host, phi_out_host, dt, eps, gamma, vel_scale, s))
+            return rc;
+        if (stats_out) return read_rec(g, g->rec, stats_out, s);
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "synchronise");
+        return CDI_OK;
+    }
     if ((e = cudaMemcpyAsync(g->stage_in, phi_in_host, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return cuda_fail(e, "host-to-device copy");
     if (int rc = cdi_step(g, g->stage_in, g->stage_out, dt, eps, gamma, vel_scale, flags, stream)) return rc;

@@ -61,7 +61,9 @@ struct VecCfg {
     static_assert(2 * TX <= 32 && 2 * TY <= 32, "ring warps hold 2*TX groups and 2*TY cells");
 };
 
-template <typename T, int TX, int TY, bool RK>
+// ZR: update only planes [a.z_lo, a.z_hi) (the z slabs of a pipelined host
+// step); the full-box instantiations keep no range.
+template <typename T, int TX, int TY, bool RK, bool ZR = false>
 __global__ void __launch_bounds__(VecCfg<T, TX, TY>::NT, 2)
 fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
 {
@@ -133,10 +135,12 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
     Acc<T> acc;
     acc.init();
 
-    UnitIter<W, H> units(ntiles, nz, nchunks);
+    // planes [z_lo, z_hi) with ZR, else all of them
+    const int zlo = ZR ? a.z_lo : 0, zr = ZR ? a.z_hi - a.z_lo : nz;
+    UnitIter<W, H> units(ntiles, zr, nchunks);
     Unit un;
-    while (units.next(un, ntiles, tiles_x, nz, nchunks)) {
-        const int x0 = un.x0, y0 = un.y0, z0 = un.z0, z1 = un.z1;
+    while (units.next(un, ntiles, tiles_x, zr, nchunks)) {
+        const int x0 = un.x0, y0 = un.y0, z0 = un.z0 + zlo, z1 = un.z1 + zlo;
 
         // The 64 ring threads issue every 16-byte copy (they are idle while the
         // own warps evaluate fluxes).  Global in-plane offsets of their chunks:
@@ -365,13 +369,13 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
         }
         cp_async_wait<0>();
     }
-    reduce_and_finish(acc.partial(), a.red);
+    reduce_and_finish<ZR>(acc.partial(), a.red);
 }
 
 // ===========================================================================
 // Scalar kernel (any extents): the per-unit body is in cdi_fwd_scalar.cuh.
 
-template <typename T, int BX, int BY, bool RK, bool FACE = false>
+template <typename T, int BX, int BY, bool RK, bool FACE = false, bool ZR = false>
 __global__ void __launch_bounds__(BX * BY)
 fwd_kernel(const FwdArgs<T> a, const int nchunks)
 {
@@ -380,11 +384,15 @@ fwd_kernel(const FwdArgs<T> a, const int nchunks)
     const int ntiles = tiles_x * ((a.ny + BY - 1) / BY);
     Acc<T> acc;
     acc.init();
-    UnitIter<BX, BY> units(ntiles, a.nz, nchunks);
+    const int zlo = ZR ? a.z_lo : 0, zr = ZR ? a.z_hi - a.z_lo : a.nz;
+    UnitIter<BX, BY> units(ntiles, zr, nchunks);
     Unit un;
-    while (units.next(un, ntiles, tiles_x, a.nz, nchunks))
+    while (units.next(un, ntiles, tiles_x, zr, nchunks)) {
+        un.z0 += zlo;
+        un.z1 += zlo;
         scalar_unit<T, BX, BY, RK, SCALAR_PF, FACE>(a, un, acc, smem_raw);
-    reduce_and_finish(acc.partial(), a.red);
+    }
+    reduce_and_finish<ZR>(acc.partial(), a.red);
 }
 
 // ===========================================================================
@@ -429,8 +437,16 @@ static cudaError_t occ(K kernel, int threads, size_t smem, int *resident)
 bool fwd_tile_has_rk(int tile) { return tile == 1 || tile == 3 || tile == 4; }
 
 template <typename T>
-cudaError_t fwd_occupancy(int tile, bool rk, int *resident, bool face)
+cudaError_t fwd_occupancy(int tile, bool rk, int *resident, bool face, bool slab)
 {
+    if (slab) {  // the z-slab kernels of the pipelined host step
+        if (rk || face) return cudaErrorInvalidValue;
+        if (tile == 4)
+            return occ(fwd_vec_kernel<T, 16, 16, false, true>, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes,
+                       resident);
+        if (tile == 0) return occ(fwd_kernel<T, 32, 8, false, false, true>, 256, FwdSmem<T, 32, 8>::bytes, resident);
+        return cudaErrorInvalidValue;
+    }
     if (face) {
         if (rk || tile != 0) return cudaErrorInvalidValue;
         return occ(fwd_kernel<T, 32, 8, false, true>, 256, FwdSmem<T, 32, 8>::bytes, resident);
@@ -454,13 +470,24 @@ cudaError_t fwd_occupancy(int tile, bool rk, int *resident, bool face)
     default: return cudaErrorInvalidValue;
     }
 }
-template cudaError_t fwd_occupancy<float>(int, bool, int *, bool);
-template cudaError_t fwd_occupancy<double>(int, bool, int *, bool);
+template cudaError_t fwd_occupancy<float>(int, bool, int *, bool, bool);
+template cudaError_t fwd_occupancy<double>(int, bool, int *, bool, bool);
 
 template <typename T>
 cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, bool rk, cudaStream_t s,
                        bool face)
 {
+    if (a.z_hi > 0) {  // a z slab: tile 4 (vector) or 0 (any extents), centre form, Euler
+        if (rk || face) return cudaErrorInvalidValue;
+        if (tile == 4)
+            fwd_vec_kernel<T, 16, 16, false, true>
+                <<<nblocks, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, s>>>(a, nchunks);
+        else if (tile == 0)
+            fwd_kernel<T, 32, 8, false, false, true><<<nblocks, dim3(32, 8), FwdSmem<T, 32, 8>::bytes, s>>>(a, nchunks);
+        else
+            return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
     if (face) {  // face-product sharpening: tile 0 only, Euler only
         if (rk || tile != 0) return cudaErrorInvalidValue;
         fwd_kernel<T, 32, 8, false, true><<<nblocks, dim3(32, 8), FwdSmem<T, 32, 8>::bytes, s>>>(a, nchunks);

@@ -33,6 +33,8 @@ struct RedScratch {
     double dV;              // cell measure dx^D_f
     int update_run;         // 1: fold this result into the *_run accumulators
     unsigned int *status;   // nullable: bit 0 set if a bounded device wait gave up
+    int combine = 0;        // 1: add this launch's result to the record's per-step fields
+                            //    (a step done in several launches over z slabs)
 };
 
 // Coefficients of one step, precomputed on the host in double and cast.
@@ -64,6 +66,8 @@ struct FwdArgs {
     const T *rk_q;
     T *rk_qout;
     T rk_alpha, rk_delta, rk_mu, rk_beta;
+    int z_lo = 0, z_hi = 0;  // z_hi > 0: only planes [z_lo, z_hi) are updated (forward
+                             // tiles 0 and 4, the slabs of a pipelined host step)
 };
 
 template <typename T>
@@ -97,7 +101,7 @@ long long fwd_tiles_xy(int tile, int esize, int nx, int ny);
 
 // Blocks of the forward kernel with this tile that fit on one SM (sets the smem attribute).
 template <typename T>
-cudaError_t fwd_occupancy(int tile, bool rk, int *resident, bool face = false);
+cudaError_t fwd_occupancy(int tile, bool rk, int *resident, bool face = false, bool slab = false);
 
 // Tile 6: tensor-memory-accelerator staging (cdi_fwd_tma.cu); needs
 // nx % W == 0 and ny % 16 == 0 with W = 16 * 16 / sizeof(T).

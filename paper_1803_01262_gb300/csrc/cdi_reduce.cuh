@@ -201,6 +201,9 @@ __device__ __forceinline__ Partial block_reduce(Partial p)
 // Block-reduce p (every thread of the block must call this), store the block
 // partial, and let the last block to finish combine all partials in index
 // order into red.rec.  The block size must be a multiple of 32.
+// COMBINE: the launch may be a further z slab of a step (red.combine); only the
+// slab kernels are built with it.
+template <bool COMBINE = false>
 __device__ __forceinline__ void reduce_and_finish(Partial p, const RedScratch &red)
 {
     __shared__ Partial wsum[32];
@@ -238,17 +241,25 @@ __device__ __forceinline__ void reduce_and_finish(Partial p, const RedScratch &r
         q = warp_reduce(q);
         if (lane == 0) {
             StatsRec *r = red.rec;
-            r->mass = red.dV * q.sum;
-            r->sum = q.sum;
-            r->mn = q.mn;
-            r->mx = q.mx;
-            r->ns = q.ns;
-            r->nt = q.nt;
+            if (COMBINE && red.combine) {  // a further z slab of the same step
+                r->sum += q.sum;
+                r->mn = fmin(r->mn, q.mn);
+                r->mx = fmax(r->mx, q.mx);
+                r->ns += q.ns;
+                r->nt += q.nt;
+            } else {
+                r->sum = q.sum;
+                r->mn = q.mn;
+                r->mx = q.mx;
+                r->ns = q.ns;
+                r->nt = q.nt;
+            }
+            r->mass = red.dV * r->sum;
             if (red.update_run) {
-                r->mn_run = fmin(r->mn_run, q.mn);
-                r->mx_run = fmax(r->mx_run, q.mx);
-                r->ns_run += q.ns;
-                r->nt_run += q.nt;
+                r->mn_run = fmin(r->mn_run, r->mn);
+                r->mx_run = fmax(r->mx_run, r->mx);
+                r->ns_run += r->ns;
+                r->nt_run += r->nt;
                 r->steps_run += 1;
             }
             __threadfence();

@@ -83,6 +83,19 @@ def test_face_run_parity_and_modes(dtype):
     assert np.abs(b.double().cpu().numpy() - cen).max() <= TOL[dtype]
 
 
+def test_face_host_step():
+    """cdi_step_host in the face form (nz >= 16: unpipelined) equals the device step."""
+    shape = (20, 12, 16)
+    phi, u, v, w, h = case(shape, 3, torch.float64)
+    g = face_grid(shape, h, torch.float64, (u, v, w))
+    dt, eps, gamma = 0.1 * h, h, 1.0
+    hout = np.empty(shape)
+    g.step_host(np.ascontiguousarray(phi), hout, dt, eps, gamma)
+    d = torch.empty(shape, dtype=torch.float64, device="cuda")
+    g.step(dev(phi, torch.float64), d, dt, eps, gamma)
+    assert np.array_equal(hout, d.cpu().numpy())
+
+
 def test_face_form_boundedness_on_table2_points():
     """Empirical boundedness of the face form (not covered by the proof) on Table 2's seven
     points, one period each with the Table 2 step: the GPU verdict equals the oracle's, and

@@ -140,6 +140,37 @@ def test_run_equals_steps_and_host_step():
     assert st["sum"] == pytest.approx(hout.sum(), rel=1e-14)
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape", [(40, 24, 64), (17, 10, 20), (16, 8, 8), (64, 33, 36)])
+def test_host_step_slab_pipeline(dtype, shape):
+    """cdi_step_host for nz >= 16 runs 8 z slabs through two copy streams and the kernel
+    (slabs of two planes included): the result equals the device step to the kernels'
+    parity tolerance (the slabs run the vector kernel where nx allows, the full step the
+    grid's tuned tile), the statistics likewise, one run step per call."""
+    f = random_fields(shape, 21 + shape[0], True, smooth=True)
+    dt, eps, gamma = 0.1 * f.h * f.h / (1.1 * f.h), 1.1 * f.h, 1.0
+    g, vel = make_grid(f, dtype)
+    t = NPT[dtype]
+    hin = torch.from_numpy(np.asarray(f.phi, t)).pin_memory().numpy()
+    hout = torch.empty(shape, dtype=dtype).pin_memory().numpy()
+    g.reset_run_stats()
+    st = g.step_host(hin, hout, dt, eps, gamma, 0.7)
+    st = g.step_host(hin, hout, dt, eps, gamma, 0.7)
+    assert st["steps_run"] == 2
+    d = torch.empty(shape, dtype=dtype, device="cuda")
+    g.step(dev(f.phi, dtype), d, dt, eps, gamma, 0.7)
+    sd = g.stats()
+    assert np.abs(hout - d.cpu().numpy()).max() <= TOL[dtype]
+    assert st["min"] == hout.min() and st["max"] == hout.max()
+    assert st["n_strict"] == sd["n_strict"] and st["n_tol"] == sd["n_tol"]
+    assert st["sum"] == pytest.approx(hout.astype(np.float64).sum(), rel=1e-13 if dtype == torch.float64 else 1e-7)
+    assert st["mass"] == pytest.approx(sd["mass"], rel=1e-12 if dtype == torch.float64 else 1e-6)
+    # non-pinned host arrays take the same path
+    out2 = np.empty_like(hout)
+    g.step_host(np.ascontiguousarray(hin), out2, dt, eps, gamma, 0.7)
+    assert np.array_equal(out2, hout)
+
+
 def test_condition_flag():
     f = I.single_vortex_2d(32)
     g, vel = make_grid(f, torch.float64)
