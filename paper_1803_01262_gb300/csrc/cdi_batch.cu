@@ -35,7 +35,9 @@ struct BoxDev {
     int tiles_x, ntiles, zc, unit0, nunits;
 };
 
-template <typename T, int BX, int BY>
+// FLAT: every box has nz == 1 (e.g. a phase-diagram sweep of 2D boxes): the
+// single-plane unit body, which stages the plane once (see flat_unit).
+template <typename T, int BX, int BY, bool FLAT = false>
 __global__ void __launch_bounds__(BX * BY)
 batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_box,
              const int total_units, const int parity, const T vs, Partial *partials,
@@ -57,7 +59,10 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
         const Unit un = unit_of(lu, boxes[bi].ntiles, boxes[bi].tiles_x, BX, BY, boxes[bi].zc, a.nz);
         Acc<T> acc;
         acc.init();
-        scalar_unit<T, BX, BY>(a, un, acc, smem_raw);
+        if constexpr (FLAT)
+            flat_unit<T, BX, BY>(a, un, acc, smem_raw);
+        else
+            scalar_unit<T, BX, BY>(a, un, acc, smem_raw);
         const Partial p = block_reduce(acc.partial());
         if (tid == 0) {
             partials[u] = p;
@@ -105,6 +110,7 @@ using cdi::StatsRec;
 struct cdi_batch {
     int nbox, dtype, total_units, nblocks, parity;
     int tile, zdepth;          // launch configuration: batch tile, planes per unit (0: whole box)
+    bool flat;                 // every box has nz == 1: the single-plane kernel
     std::vector<cdi_box_desc> desc;
     void *boxes_dev;           // BoxDev<T>[nbox]
     int *unit_box;             // [unit_cap]
@@ -118,26 +124,33 @@ struct cdi_batch {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (nsteps, parity) -> exec
 };
 
-template <typename T, int BX, int BY>
+template <typename T, int BX, int BY, bool FLAT>
 static cudaError_t batch_occ_one(int *resident)
 {
     const size_t smem = cdi::FwdSmem<T, BX, BY>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, BX, BY>,
+    cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, BX, BY, FLAT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, BX, BY>, BX * BY, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, BX, BY, FLAT>, BX * BY,
+                                                         smem);
+}
+
+template <typename T, bool FLAT>
+static cudaError_t batch_occ_t(int tile, int *resident)
+{
+    switch (tile) {
+    case 0: return batch_occ_one<T, 32, 8, FLAT>(resident);
+    case 1: return batch_occ_one<T, 32, 16, FLAT>(resident);
+    case 2: return batch_occ_one<T, 64, 8, FLAT>(resident);
+    case 3: return batch_occ_one<T, 32, 4, FLAT>(resident);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename T>
-static cudaError_t batch_occ(int tile, int *resident)
+static cudaError_t batch_occ(int tile, bool flat, int *resident)
 {
-    switch (tile) {
-    case 0: return batch_occ_one<T, 32, 8>(resident);
-    case 1: return batch_occ_one<T, 32, 16>(resident);
-    case 2: return batch_occ_one<T, 64, 8>(resident);
-    case 3: return batch_occ_one<T, 32, 4>(resident);
-    default: return cudaErrorInvalidValue;
-    }
+    return flat ? batch_occ_t<T, true>(tile, resident) : batch_occ_t<T, false>(tile, resident);
 }
 
 static int batch_free(cdi_batch *b)
@@ -201,7 +214,7 @@ static int build_units(cdi_batch *b, int tile, int zdepth)
         tab.push_back(e);
     }
     int resident = 0;
-    cudaError_t e = batch_occ<T>(tile, &resident);
+    cudaError_t e = batch_occ<T>(tile, b->flat, &resident);
     if (e != cudaSuccess) return cdi::set_error(CDI_ERR_CUDA, "batch occupancy: %s", cudaGetErrorString(e));
     if (resident < 1) return cdi::set_error(CDI_ERR_CUDA, "batch kernel does not fit on an SM");
     if (ub.size() > b->unit_cap) {
@@ -242,9 +255,14 @@ static int rebuild(cdi_batch *b, int tile, int zdepth)
 template <typename T, int BX, int BY>
 static void batch_launch_one(cdi_batch *b, int parity, double vs, cudaStream_t s)
 {
-    cdi::batch_kernel<T, BX, BY><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
-        (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-        b->box_done, b->recs);
+    if (b->flat)
+        cdi::batch_kernel<T, BX, BY, true><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
+            (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
+            b->box_done, b->recs);
+    else
+        cdi::batch_kernel<T, BX, BY, false><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
+            (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
+            b->box_done, b->recs);
 }
 
 template <typename T>
@@ -293,6 +311,8 @@ int cdi_batch_create(cdi_batch **out, const cdi_box_desc *boxes, int nbox, int d
     b->nbox = nbox;
     b->dtype = dtype;
     b->desc.assign(boxes, boxes + nbox);
+    b->flat = true;
+    for (int i = 0; i < nbox; ++i) b->flat = b->flat && boxes[i].nz == 1;
     cudaError_t e;
     int dev = 0;
     std::vector<StatsRec> hrec(nbox);

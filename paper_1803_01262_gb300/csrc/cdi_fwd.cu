@@ -390,7 +390,10 @@ fwd_kernel(const FwdArgs<T> a, const int nchunks)
     while (units.next(un, ntiles, tiles_x, zr, nchunks)) {
         un.z0 += zlo;
         un.z1 += zlo;
-        scalar_unit<T, BX, BY, RK, SCALAR_PF, FACE>(a, un, acc, smem_raw);
+        if (!RK && !FACE && a.nz == 1)
+            flat_unit<T, BX, BY>(a, un, acc, smem_raw);
+        else
+            scalar_unit<T, BX, BY, RK, SCALAR_PF, FACE>(a, un, acc, smem_raw);
     }
     reduce_and_finish<ZR>(acc.partial(), a.red);
 }

@@ -286,4 +286,98 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
     cp_async_wait<0>();
 }
 
+// Per-unit body for a box with nz == 1 (2D, or 1D with ny == 1).  The single
+// plane is its own periodic neighbour in z, so g_z = 0, s_z = 0 and the two z-face
+// fluxes are equal (identical inputs) and cancel exactly; the plane and its u, v
+// velocities are staged once and the sharpening is evaluated once, where the
+// 3D body stages five copies of the plane and evaluates three planes of
+// sharpening.  The arithmetic of the remaining terms is the 3D body's
+// expression by expression, so the result is the same bit for bit.
+template <typename T, int BX, int BY>
+__device__ __forceinline__ void flat_unit(const FwdArgs<T> &a, const Unit &un, Acc<T> &acc,
+                                          unsigned char *smem_raw)
+{
+    using S = FwdSmem<T, BX, BY>;
+    constexpr int PX = BX + 4, PY = BY + 4, PLANE = PX * PY;
+    constexpr int NT = BX * BY;
+    constexpr int NU = S::NU, NV = S::NV;
+    T(*sp)[PY][PX] = reinterpret_cast<T(*)[PY][PX]>(smem_raw);           // phi (slot 0)
+    T(*sx)[BY][BX + 2] = reinterpret_cast<T(*)[BY][BX + 2]>(sp + NSLOT);  // s_x [0]
+    T(*sy)[BY + 2][BX] = reinterpret_cast<T(*)[BY + 2][BX]>(sx + 2);      // s_y [0]
+    T *const sv = reinterpret_cast<T *>(sy + 2);                          // u | v (slot 0)
+
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+    __builtin_assume(tx >= 0 && tx < BX && ty >= 0 && ty < BY);
+    const int nx = a.nx, ny = a.ny;
+    const int x0 = un.x0, y0 = un.y0;
+    const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_shp = a.c.c_shp, c_upd = a.c.c_upd;
+
+    __syncthreads();  // the previous unit's readers are done with the buffers
+    for (int e = tid; e < PLANE; e += NT) {
+        const int ey = e / PX, ex = e - ey * PX;
+        cp_async<sizeof(T)>(&sp[0][0][0] + e, a.phi + wrapi(y0 + ey - 2, ny) * nx + wrapi(x0 + ex - 2, nx));
+    }
+    for (int e = tid; e < NU; e += NT) {
+        const int ey = e / (BX + 1), ex = e - ey * (BX + 1);
+        cp_async<sizeof(T)>(sv + e, a.u + wrapi(y0 + ey, ny) * nx + wrapi(x0 - 1 + ex, nx));
+    }
+    for (int e = tid; e < NV; e += NT) {
+        const int ey = e / BX, ex = e - ey * BX;
+        cp_async<sizeof(T)>(sv + NU + e, a.v + wrapi(y0 - 1 + ey, ny) * nx + wrapi(x0 + ex, nx));
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+
+    auto sharp = [&](int lx, int ly, T &s0, T &s1) {
+        const int X = lx + 2, Y = ly + 2;
+        const T p = sp[0][Y][X];
+        const T g0 = sp[0][Y][X + 1] - sp[0][Y][X - 1];
+        const T g1 = sp[0][Y + 1][X] - sp[0][Y - 1][X];
+        const T g2 = T(0);
+        const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, NumLim<T>::tiny())));
+        const T wgt = p * (T(1) - p) * rsqrt_t(q);
+        s0 = wgt * g0;
+        s1 = wgt * g1;
+    };
+    {
+        T q0, q1;
+        sharp(tx, ty, q0, q1);
+        sx[0][ty][tx + 1] = q0;
+        sy[0][ty + 1][tx] = q1;
+        // the one-cell ring: s_y of rows -1 and BY, s_x of columns -1 and BX
+        if (tid < 2 * BX) {
+            const int rx = tid % BX, ry = tid < BX ? -1 : BY;
+            T r0, r1;
+            sharp(rx, ry, r0, r1);
+            sy[0][ry + 1][rx] = r1;
+        } else if (tid < 2 * BX + 2 * BY) {
+            const int r = tid - 2 * BX, ry = r % BY, rx = r < BY ? -1 : BX;
+            T r0, r1;
+            sharp(rx, ry, r0, r1);
+            sx[0][ry][rx + 1] = r0;
+        }
+    }
+    __syncthreads();
+    if ((x0 + tx < nx) && (y0 + ty < ny)) {
+        const T pc = sp[0][ty + 2][tx + 2];
+        const T pxm = sp[0][ty + 2][tx + 1], pxp = sp[0][ty + 2][tx + 3];
+        const T pym = sp[0][ty + 1][tx + 2], pyp = sp[0][ty + 3][tx + 2];
+        const T sxm = sx[0][ty][tx], sxp = sx[0][ty][tx + 2];
+        const T sym = sy[0][ty][tx], syp = sy[0][ty + 2][tx];
+        const T uc = sv[ty * (BX + 1) + tx + 1], um = sv[ty * (BX + 1) + tx];
+        const T vc = sv[NU + (ty + 1) * BX + tx], vm = sv[NU + ty * BX + tx];
+        T adv = uc * (pc + pxp);
+        adv = fma(-um, pxm + pc, adv);
+        adv = fma(vc, pc + pyp, adv);
+        adv = fma(-vm, pym + pc, adv);
+        const T dif = fma(T(-4), pc, (pxm + pxp) + (pym + pyp));
+        const T shp = (sxp - sxm) + (syp - sym);
+        const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, T(0))));  // z faces: Fzp - Fzm = 0
+        const T o = fma(-c_upd, div, pc);
+        a.out[wrapi(y0 + ty, ny) * nx + wrapi(x0 + tx, nx)] = o;
+        acc.add(o, a.c.tol);
+    }
+}
+
 }  // namespace cdi

@@ -116,3 +116,49 @@ def test_batch_autotune_keeps_state_and_records():
         ref = oracle.run(*rin, f.h, x["dt"], x["eps"], x["gamma"], 2)
         assert np.abs(b.current(i).double().cpu().numpy() - ref).max() <= 3e-6, i
     assert b.stats()[0]["steps_run"] == 2
+
+
+def flat_boxes(dtype, sizes, seed):
+    """2D boxes (nz == 1): a smoothed random field and a random divergence-free velocity."""
+    boxes = []
+    for i, (ny, nx) in enumerate(sizes):
+        shape = (1, ny, nx)
+        h = 1.0 / max(shape)
+        phi = I.random_phi(shape, seed + i, smooth=True)
+        u, v, w = I.random_velocity(shape, h, 8, 3, seed + 50 + i)
+        eps, gamma = 1.1 * h, 1.0
+        dt = 0.8 * h * h / (2 * 2 * gamma * eps)
+        f = I.Fields(phi, u, v, w, h, I.face_umax(u, v, w))
+        boxes.append(dict(dx=h, dt=dt, eps=eps, gamma=gamma, u=dev(u, dtype), v=dev(v, dtype),
+                          w=dev(w, dtype), phi_a=dev(phi, dtype),
+                          phi_b=torch.empty(shape, dtype=dtype, device="cuda"), fields=f))
+    return boxes
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_of_2d_boxes_matches_oracle(dtype, mixed):
+    """A batch of only 2D boxes runs the single-plane kernel; mixed with 3D boxes, the 3D
+    one.  Both give the oracle's steps, every launch configuration."""
+    boxes = flat_boxes(dtype, [(7, 9), (33, 40), (16, 64), (1, 37), (50, 50)], 11)
+    if mixed:
+        boxes += make_boxes(dtype, nbox=3, seed=9)
+    t = np.float64 if dtype == torch.float64 else np.float32
+    tol = 1e-12 if dtype == torch.float64 else 3e-6
+    for tile in range(4):
+        for x in boxes:
+            x["phi_a"].copy_(dev(x["fields"].phi, dtype))
+        b = cdi.Batch(boxes)
+        b.set_launch(tile, 0)
+        for i in range(3):
+            b.step(0.9)
+        st = b.stats()
+        for i, x in enumerate(boxes):
+            f = x["fields"]
+            rin = [np.asarray(a, t).astype(np.float64) for a in (f.phi, f.u, f.v, f.w)]
+            ref = rin[0]
+            for _ in range(3):
+                ref = oracle.step(ref, *rin[1:], f.h, x["dt"], x["eps"], x["gamma"], 0.9)
+            ours = b.current(i).double().cpu().numpy()
+            assert np.abs(ours - ref).max() <= tol, (tile, i)
+            assert st[i]["min"] == ours.min() and st[i]["max"] == ours.max()
