@@ -145,6 +145,17 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (every rank gets it); x itself on one process.
+    The timings of a multi-rank run are the slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_oracle_rate(fields, dt, eps, gamma, planes, steps):
     """Gcell-updates/s of the oracle on `planes` z-planes of the box (periodic wrap)."""
     import oracle
@@ -388,11 +399,7 @@ def main():
         torch.cuda.synchronize()
 
     def maxrank(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(x, dist, dev)
 
     def setup(dtype):
         g = cdi.Grid(n, n, n, f.h, dtype)
