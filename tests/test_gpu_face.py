@@ -98,9 +98,9 @@ def test_face_host_step():
 
 def test_face_form_boundedness_on_table2_points():
     """Empirical boundedness of the face form (not covered by the proof) on Table 2's seven
-    points, one period each with the Table 2 step: the GPU verdict equals the oracle's, and
+    points, one period each with the Table 2 step: the GPU classification equals the oracle's, and
     the face form loses point 5, which the centre form keeps."""
-    verdicts = []
+    outcome = []
     tol = np.finfo(np.float64).eps
     for eoh, gu in ((1.5, 0.5), (1.0, 1.0), (5 / 6, 1.5), (1.5, 1.5), (0.9, 0.9), (0.8, 0.8), (0.7, 0.7)):
         f, _ = I.drop_2d_uniform(eoh)
@@ -116,7 +116,7 @@ def test_face_form_boundedness_on_table2_points():
             p = oracle.step(p, f.u, f.v, f.w, f.h, dt, eoh * f.h, gu, sharpen="face")
             bad += int(((p < -tol) | (p > 1 + tol)).sum())
         assert (gpu_bad == 0) == (bad == 0), (eoh, gu, gpu_bad, bad)
-        verdicts.append(bad == 0)
+        outcome.append(bad == 0)
     # point 5 meets the sufficient condition and stays bounded with the centre form
     # (Table 2), but not with the face form
-    assert verdicts == [True] * 4 + [False] * 3, verdicts
+    assert outcome == [True] * 4 + [False] * 3, outcome

@@ -17,7 +17,7 @@ TABLE2 = [(1.5, 0.5, True), (1.0, 1.0, True), (5 / 6, 1.5, True), (1.5, 1.5, Tru
 
 def test_table2_points_in_one_batch_match_the_oracle():
     """The seven Table 2 points as one batch: the classification of the paper, and for each
-    box the oracle replaying it with the same step and step count gives the same verdict,
+    box the oracle replaying it with the same step and step count gives the same classification,
     and for a bounded box the same run extremes (min and max of phi over every step) to 1e-9.
     (The extremes sit in the far field, where the unit normal follows rounding-level
     gradients, so 1e-16 differences per step grow to ~1e-11 over the run.)"""
