@@ -300,6 +300,14 @@ enum { CDI_SHARPEN_CENTRE = 0, CDI_SHARPEN_FACE = 1 };
 CDI_API int cdi_set_sharpening(cdi_grid *g, int mode);
 CDI_API int cdi_get_sharpening(const cdi_grid *g, int *mode);
 
+/* Diagnostic of the failure path: launches one block that waits, with the
+ * library's bounded device wait, on an mbarrier that nothing completes.  The
+ * wait must run out after limit_s seconds (0 < limit_s <= 2), record the time-
+ * out in the grid's status word and let the kernel end; the call then reads
+ * and clears that word and returns CDI_ERR_TIMEOUT -- the expected result.
+ * CDI_OK would mean a time-out went unreported.  Synchronises the stream. */
+CDI_API int cdi_probe_bounded_wait(cdi_grid *g, double limit_s, void *stream);
+
 /* Kernels with a tunable launch configuration. */
 enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
 

@@ -75,6 +75,7 @@ SIGNATURES = {
     "cdi_check_condition": [_Dbl, _Dbl, _Dbl, _I],
     "cdi_max_dt": [_Dbl, _Dbl, _Dbl, _I, _I, _P(_Dbl)],
     "cdi_set_sharpening": [_V, _I],
+    "cdi_probe_bounded_wait": [_V, _Dbl, _V],
     "cdi_get_sharpening": [_V, _P(_I)],
     "cdi_set_launch": [_V, _I, _I, _I, _I],
     "cdi_get_launch": [_V, _I, _P(_I), _P(_I), _P(_I)],
@@ -289,6 +290,11 @@ class Grid:
                                 CDI_CHECK_CONDITION if check else 0, ctypes.byref(s),
                                 _stream(stream)))
         return s.as_dict()
+
+    def probe_bounded_wait(self, limit_s=0.05, stream=None):
+        """Make a bounded device wait run out (see cdi_probe_bounded_wait); raises CDIError
+        with CDI_ERR_TIMEOUT when the time-out is reported, as it should be."""
+        _ck(lib().cdi_probe_bounded_wait(self._h, limit_s, _stream(stream)))
 
     def set_sharpening(self, mode):
         """"centre" (Section 2.2, the default) or "face" (face-product sharpening, forward

@@ -9,6 +9,7 @@
 
 #include "cdi.h"
 #include "cdi_internal.cuh"
+#include "cdi_async.cuh"
 
 using cdi::LaunchCfg;
 using cdi::RedScratch;
@@ -932,6 +933,38 @@ int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchu
         return CDI_OK;
     }
     return fail(CDI_ERR_ARG, "unknown kernel %d", which);
+}
+
+// One block whose thread 0 waits on an mbarrier that nothing ever completes:
+// the bounded wait must run out, set the status bit and let the kernel end.
+__global__ void probe_wait_kernel(unsigned int *status, unsigned long long limit_ns)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        cdi::mbar_init(&bar, 1);
+        cdi::fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cdi::mbar_wait_bounded(&bar, 0u, status, limit_ns);
+    __syncthreads();
+}
+
+int cdi_probe_bounded_wait(cdi_grid *g, double limit_s, void *stream)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (!(limit_s > 0.0 && limit_s <= 2.0)) return fail(CDI_ERR_ARG, "limit_s must be in (0, 2]");
+    cudaStream_t s = (cudaStream_t)stream;
+    probe_wait_kernel<<<1, 32, 0, s>>>(g->status, (unsigned long long)(limit_s * 1e9));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "probe launch");
+    unsigned int st = 0;
+    if ((e = cudaMemcpyAsync(&st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "probe status readback");
+    if (!st) return CDI_OK;  // the wait did not run out: the time-out path is broken
+    cudaMemsetAsync(g->status, 0, sizeof(unsigned int), s);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "probe status reset");
+    return fail(CDI_ERR_TIMEOUT, "bounded device wait ran out (probe)");
 }
 
 int cdi_set_sharpening(cdi_grid *g, int mode)

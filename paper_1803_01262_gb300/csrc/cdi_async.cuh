@@ -80,15 +80,27 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     return ok != 0;
 }
 
-// Wait for the phase of the given parity; gives up after max_iter polls and
-// records status bit 1 (the kernel then finishes on whatever data it has and
-// the host reports CDI_ERR_TIMEOUT).  Returns false on time-out.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
-                                                  unsigned *status)
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    constexpr unsigned max_iter = 1u << 22;
-    for (unsigned i = 0; i < max_iter; ++i)
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of the given parity for at most limit_ns of wall time (a
+// poll may suspend the thread, so the bound is on time, not on polls); on
+// time-out records status bit 0 (the kernel then finishes on whatever data it
+// has and the host reports CDI_ERR_TIMEOUT) and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
+                                                  unsigned *status,
+                                                  unsigned long long limit_ns = 1000000000ull)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) break;
+    }
     if (status) atomicOr(status, 1u);
     return false;
 }

@@ -171,6 +171,28 @@ def test_host_step_slab_pipeline(dtype, shape):
     assert np.array_equal(out2, hout)
 
 
+def test_bounded_wait_timeout_is_reported():
+    """A bounded device wait that runs out (an mbarrier nothing completes) ends its kernel
+    after the limit and is reported as CDI_ERR_TIMEOUT; the context and the grid stay
+    usable: the next step's statistics are clean."""
+    import time
+    f = random_fields((8, 12, 16), 4, True, smooth=True)
+    g, vel = make_grid(f, torch.float32)
+    t0 = time.perf_counter()
+    with pytest.raises(cdi.CDIError) as e:
+        g.probe_bounded_wait(0.05)
+    assert e.value.code == cdi.CDI_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    a = dev(f.phi, torch.float32)
+    b = torch.empty_like(a)
+    dt = 0.1 * f.h * f.h / f.h
+    g.step(a, b, dt, f.h, 1.0)
+    st = g.stats()                      # raises if the status word were still set
+    assert st["n_tol"] == 0
+    with pytest.raises(cdi.CDIError):
+        g.probe_bounded_wait(5.0)       # limit out of range
+
+
 def test_condition_flag():
     f = I.single_vortex_2d(32)
     g, vel = make_grid(f, torch.float64)
