@@ -83,7 +83,7 @@ def profiled_traffic():
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("kernel_source_sha") != kernel_source_hash():
+    if (kv.get("kernel_source_sha") or "").split()[:1] != [kernel_source_hash()]:
         return None
     try:
         return float(kv["dram_bytes_per_launch"])

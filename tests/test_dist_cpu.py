@@ -59,3 +59,17 @@ def test_reference_arm_runs_on_rank0_only():
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     for k in ("metric", "unit", "ms_per_step", "cpu_baseline", "e2e", "config"):
         assert k in line
+
+
+def test_profiled_traffic_reads_summary_and_checks_source(tmp_path, monkeypatch):
+    """The roofline's traffic comes from the committed ncu summary only while its recorded
+    source hash equals the current kernel sources' (a note after the hash is allowed)."""
+    p = tmp_path / "fwd.txt"
+    monkeypatch.setattr(bench, "PROFILE_F32", str(p))
+    h = bench.kernel_source_hash()
+    p.write_text(f"# header: x\nkernel_source_sha: {h}  (files)\ndram_bytes_per_launch: 123\n")
+    assert bench.profiled_traffic() == 123.0
+    p.write_text("kernel_source_sha: 0000000000000000\ndram_bytes_per_launch: 123\n")
+    assert bench.profiled_traffic() is None
+    p.write_text("kernel_source_sha:\ndram_bytes_per_launch: 123\n")
+    assert bench.profiled_traffic() is None
