@@ -180,6 +180,77 @@ def test_constant_field():
         assert np.abs(p - c).max() < 1e-14
 
 
+def stencil_rhs_at(phi, u, v, w, dx, eps, gamma, c):
+    """d phi/dt at cell c = (k, j, i) evaluated on its own from the five steps of
+    Section 2.2: every normal, sharpening value and face flux it needs is formed
+    from explicit neighbour indices (no whole-array passes), a third formulation
+    next to the oracle's passes and the coefficient form."""
+    nz, ny, nx = phi.shape
+    ext = (nx, ny, nz)
+    vel = (u, v, w)
+
+    def at(a, q):
+        return a[q[2] % nz, q[1] % ny, q[0] % nx]
+
+    def shift(q, d, s):
+        r = list(q)
+        r[d] += s
+        return tuple(r)
+
+    def sharp(q):
+        g = [at(phi, shift(q, d, 1)) - at(phi, shift(q, d, -1)) for d in range(3)]
+        m = math.sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2])
+        p = at(phi, q)
+        return [0.0 if m == 0 else p * (1 - p) * gd / m for gd in g]
+
+    q0 = (c[2], c[1], c[0])  # (i, j, k)
+    div = 0.0
+    for d in range(3):
+        if ext[d] == 1:
+            continue   # a degenerate axis: its faces carry equal fluxes
+        for lo, hi, sign in ((q0, shift(q0, d, 1), 1.0), (shift(q0, d, -1), q0, -1.0)):
+            uf = at(vel[d], lo)   # u[k][j][i] is the face at i + 1/2
+            pl, pr = at(phi, lo), at(phi, hi)
+            F = uf * (pl + pr) / 2 - gamma * eps * (pr - pl) / dx + gamma * (sharp(lo)[d] + sharp(hi)[d]) / 2
+            div += sign * F
+    return -div / dx
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 6), (1, 5, 6), (3, 4, 5), (6, 6, 6), (2, 3, 1)])
+@pytest.mark.parametrize("solenoidal", [True, False])
+def test_brute_force_stencil(shape, solenoidal):
+    """The oracle's right-hand side equals a cell-by-cell evaluation from the stencil."""
+    phi, u, v, w, h = rand_case(shape, 17 + sum(shape), solenoidal)
+    eps, gamma = 1.3 * h, 0.8
+    ref = oracle.rhs(phi, u, v, w, h, eps, gamma)
+    nz, ny, nx = shape
+    brute = np.array([[[stencil_rhs_at(phi, u, v, w, h, eps, gamma, (k, j, i)) for i in range(nx)]
+                       for j in range(ny)] for k in range(nz)])
+    assert np.abs(brute - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_stencil_footprint_is_25_points():
+    """d phi/dt at a cell depends on exactly 25 cells: itself, +-1 and +-2 along each axis
+    and the 12 edge diagonals (normals of the face neighbours reach one cell beyond)."""
+    n = 7
+    phi, u, v, w, h = rand_case((n, n, n), 5)
+    eps, gamma = h, 1.0
+    c = (3, 3, 3)
+    base = oracle.rhs(phi, u, v, w, h, eps, gamma)[c]
+    found = set()
+    for k in range(n):
+        for j in range(n):
+            for i in range(n):
+                q = phi.copy()
+                q[k, j, i] += 1e-6
+                if abs(oracle.rhs(q, u, v, w, h, eps, gamma)[c] - base) > 1e-12:
+                    found.add((k - 3, j - 3, i - 3))
+    axes = {t for d in range(3) for s in (-2, -1, 1, 2) for t in [tuple(s if e == d else 0 for e in range(3))]}
+    diag = {t for a in range(3) for b in range(a + 1, 3) for sa in (-1, 1) for sb in (-1, 1)
+            for t in [tuple(sa if e == a else sb if e == b else 0 for e in range(3))]}
+    assert found == {(0, 0, 0)} | axes | diag and len(found) == 25
+
+
 def discrete_equilibrium_1d(n, e):
     """Exact zero-flux profile of the scheme at u = 0, eps/dx = e (derived).
 
@@ -293,13 +364,14 @@ def test_face_form_conserves_and_is_symmetric(solenoidal):
 def test_boundedness_theorem_random_boxes():
     """0 <= phi <= 1 (within machine eps) under Eq. 24 and A <= 1/(2 D_f).
 
-    Many seeded small periodic boxes with random solenoidal velocity, eps/dx
-    on or above the crossover line, U = max face |component|.
+    1000 seeded small periodic boxes with random solenoidal velocity, eps/dx
+    on or above the crossover line (every fifth box exactly on it), A up to
+    1/(2 D_f) (every seventh box exactly at it), U = max face |component|.
     """
     rng = np.random.default_rng(2024)
     tol = np.finfo(np.float64).eps
     worst = 0
-    for b in range(120):
+    for b in range(1000):
         dims = rng.integers(3, 10, size=3)
         if b % 4 == 0:
             dims[0] = 1
@@ -310,10 +382,10 @@ def test_boundedness_theorem_random_boxes():
         U = I.face_umax(u, v, w)
         eoh = float(rng.uniform(0.55, 2.0))
         gmin = 1.0 / (2 * eoh - 1) if eoh > 0.5 else np.inf
-        gamma = U * gmin * float(rng.uniform(1.0, 2.0))
+        gamma = U * gmin * (1.0 if b % 5 == 0 else float(rng.uniform(1.0, 2.0)))
         Df = sum(1 for s in shape if s > 1)
         eps = eoh * h
-        dt = float(rng.uniform(0.5, 1.0)) * h * h / (2 * Df * gamma * eps)
+        dt = (1.0 if b % 7 == 0 else float(rng.uniform(0.5, 1.0))) * h * h / (2 * Df * gamma * eps)
         p = phi
         for _ in range(25):
             p = oracle.step(p, u, v, w, h, dt, eps, gamma)
