@@ -271,6 +271,12 @@ CDI_API int cdi_batch_reset_run_stats(cdi_batch *b, void *stream);
 /* Launch configuration of the batch (a performance control, not part of the
  * paper): tile 0..3 = 32x8, 32x16, 64x8, 32x4 cells per work unit (one cell
  * per thread), zdepth = about that many planes per unit (0: whole box depth).
+ * Tile 4 = one work unit per box, for batches of 2D boxes only (every nz = 1)
+ * whose largest plane fits in one block's shared memory as 3 nx ny values
+ * (about 9600 cells in FP64, 19000 in FP32): the whole plane is staged once
+ * and each cell's sharpening evaluated once; the results are those of tiles
+ * 0..3 bit for bit (the statistics' sums to rounding).  CDI_ERR_ARG, with the
+ * launch unchanged, where it does not apply; zdepth is ignored for it.
  * tile = -1 / zdepth = -1 restore the defaults (32x8, CDI_BATCH_DEFAULT_ZDEPTH).
  * Rebuilds the work list (synchronises the device; drops captured graphs). */
 #define CDI_BATCH_DEFAULT_ZDEPTH 32
@@ -278,7 +284,8 @@ CDI_API int cdi_batch_set_launch(cdi_batch *b, int tile, int zdepth);
 CDI_API int cdi_batch_get_launch(const cdi_batch *b, int *tile, int *zdepth, int *nblocks,
                                  int *total_units);
 
-/* Time every tile x zdepth in {8, 16, 32, 64, whole} with reps launches each
+/* Time every tile x zdepth in {8, 16, 32, 64, whole} (a batch of 2D boxes: every
+ * tile once, tile 4 where it applies) with reps launches each
  * (after one warm-up) and keep the fastest; *best_ms (nullable) gets its time
  * per launch.  The trial launches read the current state and write the other
  * buffer only, and the statistics records are restored, so the batch's state

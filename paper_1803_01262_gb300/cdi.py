@@ -401,7 +401,8 @@ class Batch:
         _ck(lib().cdi_batch_run(self._h, nsteps, _stream(stream)))
 
     def set_launch(self, tile=-1, zdepth=-1):
-        """Work-unit tile (0..3: 32x8, 32x16, 64x8, 32x4) and planes per unit (0: whole box)."""
+        """Work-unit tile (0..3: 32x8, 32x16, 64x8, 32x4; 4: one unit per whole 2D box, for
+        batches of 2D boxes whose planes fit in shared memory) and planes per unit (0: whole box)."""
         _ck(lib().cdi_batch_set_launch(self._h, tile, zdepth))
 
     def get_launch(self):

@@ -10,8 +10,10 @@
 // unit order, into the box's statistics record (reproducible, and spread over
 // the launch instead of serialised at its end).  The tile shape and the number
 // of planes per unit are a launch configuration (cdi_batch_set_launch), which
-// cdi_batch_autotune picks by timing.  Multi-step runs are captured once into
-// a CUDA graph and replayed.
+// cdi_batch_autotune picks by timing.  A batch of 2D boxes small enough to
+// hold a whole plane in shared memory can also take one unit per box (the
+// whole-plane body below).  Multi-step runs are captured once into a CUDA
+// graph and replayed.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
@@ -35,9 +37,78 @@ struct BoxDev {
     int tiles_x, ntiles, zc, unit0, nunits;
 };
 
-// FLAT: every box has nz == 1 (e.g. a phase-diagram sweep of 2D boxes): the
-// single-plane unit body, which stages the plane once (see flat_unit).
-template <typename T, int BX, int BY, bool FLAT = false>
+// Whole-plane unit body: the unit is a whole 2D box (nz == 1) whose phi and
+// both sharpening components fit in shared memory (3 nx ny values).  Cells
+// are visited by their linear index l = y nx + x and the periodic neighbours
+// found by index arithmetic, so every lane holds a cell of the box (no tile
+// overhang) and each sharpening value is evaluated once (no ring around a
+// tile).  The arithmetic is flat_unit's, expression by expression, so the
+// result is the same bit for bit.
+template <typename T, int NT>
+__device__ __forceinline__ void plane_unit(const FwdArgs<T> &a, Acc<T> &acc, unsigned char *smem_raw)
+{
+    const int nx = a.nx, ny = a.ny, P = nx * ny;
+    T *const sp = reinterpret_cast<T *>(smem_raw);  // phi [P]
+    T *const ssx = sp + P;                          // s_x [P]
+    T *const ssy = ssx + P;                         // s_y [P]
+    const int tid = threadIdx.x;
+    const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_shp = a.c.c_shp, c_upd = a.c.c_upd;
+
+    // periodic neighbours of cell l (a neighbour is l itself along an axis of extent 1)
+    auto nbr = [&](int l, int &xm, int &xp, int &ym, int &yp) {
+        const int y = l / nx, x = l - y * nx;
+        xm = x == 0 ? l + nx - 1 : l - 1;
+        xp = x == nx - 1 ? l - nx + 1 : l + 1;
+        ym = y == 0 ? l + P - nx : l - nx;
+        yp = y == ny - 1 ? l - P + nx : l + nx;
+    };
+
+    __syncthreads();  // the previous unit's readers are done with the buffers
+    for (int l = tid; l < P; l += NT) cp_async<sizeof(T)>(sp + l, a.phi + l);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int l = tid; l < P; l += NT) {
+        int xm, xp, ym, yp;
+        nbr(l, xm, xp, ym, yp);
+        const T p = sp[l];
+        const T g0 = sp[xp] - sp[xm];
+        const T g1 = sp[yp] - sp[ym];
+        const T g2 = T(0);
+        const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, NumLim<T>::tiny())));
+        const T wgt = p * (T(1) - p) * rsqrt_t(q);
+        ssx[l] = wgt * g0;
+        ssy[l] = wgt * g1;
+    }
+    __syncthreads();
+    for (int l = tid; l < P; l += NT) {
+        int xm, xp, ym, yp;
+        nbr(l, xm, xp, ym, yp);
+        const T pc = sp[l];
+        const T pxm = sp[xm], pxp = sp[xp];
+        const T pym = sp[ym], pyp = sp[yp];
+        const T sxm = ssx[xm], sxp = ssx[xp];
+        const T sym = ssy[ym], syp = ssy[yp];
+        const T uc = __ldg(a.u + l), um = __ldg(a.u + xm);
+        const T vc = __ldg(a.v + l), vm = __ldg(a.v + ym);
+        T adv = uc * (pc + pxp);
+        adv = fma(-um, pxm + pc, adv);
+        adv = fma(vc, pc + pyp, adv);
+        adv = fma(-vm, pym + pc, adv);
+        const T dif = fma(T(-4), pc, (pxm + pxp) + (pym + pyp));
+        const T shp = (sxp - sxm) + (syp - sym);
+        const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, T(0))));  // z faces: Fzp - Fzm = 0
+        const T o = fma(-c_upd, div, pc);
+        a.out[l] = o;
+        acc.add(o, a.c.tol);
+    }
+}
+
+// BODY 0: the 3D unit body (scalar_unit).  BODY 1: every box has nz == 1
+// (e.g. a phase-diagram sweep of 2D boxes): the single-plane unit body, which
+// stages the plane once (flat_unit).  BODY 2: every box has nz == 1 and fits
+// in shared memory: one unit per box, the whole-plane body (plane_unit).
+template <typename T, int BX, int BY, int BODY = 0>
 __global__ void __launch_bounds__(BX * BY)
 batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_box,
              const int total_units, const int parity, const T vs, Partial *partials,
@@ -55,14 +126,18 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
             a.phi = t;
         }
         a.c.c_adv *= vs;
-        const int lu = u - boxes[bi].unit0;
-        const Unit un = unit_of(lu, boxes[bi].ntiles, boxes[bi].tiles_x, BX, BY, boxes[bi].zc, a.nz);
         Acc<T> acc;
         acc.init();
-        if constexpr (FLAT)
-            flat_unit<T, BX, BY>(a, un, acc, smem_raw);
-        else
-            scalar_unit<T, BX, BY>(a, un, acc, smem_raw);
+        if constexpr (BODY == 2) {
+            plane_unit<T, BX * BY>(a, acc, smem_raw);
+        } else {
+            const int lu = u - boxes[bi].unit0;
+            const Unit un = unit_of(lu, boxes[bi].ntiles, boxes[bi].tiles_x, BX, BY, boxes[bi].zc, a.nz);
+            if constexpr (BODY == 1)
+                flat_unit<T, BX, BY>(a, un, acc, smem_raw);
+            else
+                scalar_unit<T, BX, BY>(a, un, acc, smem_raw);
+        }
         const Partial p = block_reduce(acc.partial());
         if (tid == 0) {
             partials[u] = p;
@@ -98,9 +173,12 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
     }
 }
 
-// Batch tiles: the scalar tiles of the single-box kernel.
-constexpr int BATCH_TILES = 4;
-static const int batch_tile_dims[BATCH_TILES][2] = {{32, 8}, {32, 16}, {64, 8}, {32, 4}};
+// Batch tiles 0..3: the scalar tiles of the single-box kernel; tile 4: one
+// unit per whole 2D box (plane_unit, PLANE_NT threads).
+constexpr int BATCH_TILES = 5;
+constexpr int BATCH_TILE_PLANE = 4;
+constexpr int PLANE_NT = 256;
+static const int batch_tile_dims[4][2] = {{32, 8}, {32, 16}, {64, 8}, {32, 4}};
 
 }  // namespace cdi
 
@@ -111,6 +189,7 @@ struct cdi_batch {
     int nbox, dtype, total_units, nblocks, parity;
     int tile, zdepth;          // launch configuration: batch tile, planes per unit (0: whole box)
     bool flat;                 // every box has nz == 1: the single-plane kernel
+    size_t plane_bytes;        // shared memory of the whole-plane body: 3 nx ny values of the largest box
     std::vector<cdi_box_desc> desc;
     void *boxes_dev;           // BoxDev<T>[nbox]
     int *unit_box;             // [unit_cap]
@@ -124,33 +203,79 @@ struct cdi_batch {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (nsteps, parity) -> exec
 };
 
-template <typename T, int BX, int BY, bool FLAT>
-static cudaError_t batch_occ_one(int *resident)
+template <typename T, int BX, int BY, int BODY>
+static cudaError_t batch_occ_one(int *resident, size_t smem)
 {
-    const size_t smem = cdi::FwdSmem<T, BX, BY>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, BX, BY, FLAT>,
+    cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, BX, BY, BODY>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, BX, BY, FLAT>, BX * BY,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, BX, BY, BODY>, BX * BY,
                                                          smem);
 }
 
-template <typename T, bool FLAT>
+template <typename T, int BODY>
 static cudaError_t batch_occ_t(int tile, int *resident)
 {
     switch (tile) {
-    case 0: return batch_occ_one<T, 32, 8, FLAT>(resident);
-    case 1: return batch_occ_one<T, 32, 16, FLAT>(resident);
-    case 2: return batch_occ_one<T, 64, 8, FLAT>(resident);
-    case 3: return batch_occ_one<T, 32, 4, FLAT>(resident);
+    case 0: return batch_occ_one<T, 32, 8, BODY>(resident, cdi::FwdSmem<T, 32, 8>::bytes);
+    case 1: return batch_occ_one<T, 32, 16, BODY>(resident, cdi::FwdSmem<T, 32, 16>::bytes);
+    case 2: return batch_occ_one<T, 64, 8, BODY>(resident, cdi::FwdSmem<T, 64, 8>::bytes);
+    case 3: return batch_occ_one<T, 32, 4, BODY>(resident, cdi::FwdSmem<T, 32, 4>::bytes);
     default: return cudaErrorInvalidValue;
     }
 }
 
+// Largest dynamic shared memory the whole-plane kernel can launch with (the
+// opt-in maximum less its static shared memory); 0 if it cannot be queried.
 template <typename T>
-static cudaError_t batch_occ(int tile, bool flat, int *resident)
+static size_t plane_limit()
 {
-    return flat ? batch_occ_t<T, true>(tile, resident) : batch_occ_t<T, false>(tile, resident);
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2>) != cudaSuccess ||
+        (size_t)optin <= fa.sharedSizeBytes)
+        return 0;
+    return ((size_t)optin - fa.sharedSizeBytes) & ~(size_t)15;
+}
+
+template <typename T>
+static cudaError_t batch_occ(const cdi_batch *b, int tile, int *resident)
+{
+    if (tile == cdi::BATCH_TILE_PLANE) {
+        // The attribute belongs to the kernel, shared by every batch: it is set
+        // to the largest size any batch launches with, the occupancy taken at
+        // this batch's size.
+        const size_t lim = plane_limit<T>();
+        if (lim == 0 || b->plane_bytes > lim) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2>,
+                                                             cdi::PLANE_NT, b->plane_bytes);
+    }
+    return b->flat ? batch_occ_t<T, 1>(tile, resident) : batch_occ_t<T, 0>(tile, resident);
+}
+
+// Shared memory the whole-plane body needs for this batch (3 nx ny values of
+// its largest box), 0 if some box is 3D or does not fit.
+template <typename T>
+static size_t plane_bytes_t(const cdi_batch *b)
+{
+    if (!b->flat) return 0;
+    size_t need = 0;
+    for (const cdi_box_desc &x : b->desc) {
+        const size_t bytes = 3 * sizeof(T) * (size_t)x.nx * (size_t)x.ny;
+        if (bytes > need) need = bytes;
+    }
+    need = (need + 15) & ~(size_t)15;
+    return need <= plane_limit<T>() ? need : 0;
+}
+
+static size_t plane_bytes(const cdi_batch *b)
+{
+    return b->dtype == CDI_F64 ? plane_bytes_t<double>(b) : plane_bytes_t<float>(b);
 }
 
 static int batch_free(cdi_batch *b)
@@ -178,7 +303,10 @@ static void drop_graphs(cdi_batch *b)
 template <typename T>
 static int build_units(cdi_batch *b, int tile, int zdepth)
 {
-    const int bw = cdi::batch_tile_dims[tile][0], bh = cdi::batch_tile_dims[tile][1];
+    const bool plane = tile == cdi::BATCH_TILE_PLANE;
+    if (plane && b->plane_bytes == 0)
+        return cdi::set_error(CDI_ERR_ARG, "batch tile 4 needs 2D boxes (nz = 1) whose planes fit in shared memory");
+    const int bw = plane ? 1 : cdi::batch_tile_dims[tile][0], bh = plane ? 1 : cdi::batch_tile_dims[tile][1];
     std::vector<BoxDev<T>> tab;
     std::vector<int> ub;
     int unit = 0;
@@ -200,9 +328,9 @@ static int build_units(cdi_batch *b, int tile, int zdepth)
         e.a.c.tol = sizeof(T) == 8 ? (T)DBL_EPSILON : (T)FLT_EPSILON;
         const int Df = (x.nx > 1) + (x.ny > 1) + (x.nz > 1);
         e.dV = pow(x.dx, (double)Df);
-        e.tiles_x = (x.nx + bw - 1) / bw;
-        e.ntiles = e.tiles_x * ((x.ny + bh - 1) / bh);
-        int nch = zdepth > 0 ? (x.nz + zdepth / 2) / zdepth : 1;  // about zdepth planes per unit
+        e.tiles_x = plane ? 1 : (x.nx + bw - 1) / bw;
+        e.ntiles = plane ? 1 : e.tiles_x * ((x.ny + bh - 1) / bh);  // whole-plane body: one unit per box
+        int nch = zdepth > 0 && !plane ? (x.nz + zdepth / 2) / zdepth : 1;  // about zdepth planes per unit
         if (nch < 1) nch = 1;
         e.zc = (x.nz + nch - 1) / nch;
         e.unit0 = unit;
@@ -214,7 +342,7 @@ static int build_units(cdi_batch *b, int tile, int zdepth)
         tab.push_back(e);
     }
     int resident = 0;
-    cudaError_t e = batch_occ<T>(tile, b->flat, &resident);
+    cudaError_t e = batch_occ<T>(b, tile, &resident);
     if (e != cudaSuccess) return cdi::set_error(CDI_ERR_CUDA, "batch occupancy: %s", cudaGetErrorString(e));
     if (resident < 1) return cdi::set_error(CDI_ERR_CUDA, "batch kernel does not fit on an SM");
     if (ub.size() > b->unit_cap) {
@@ -256,13 +384,21 @@ template <typename T, int BX, int BY>
 static void batch_launch_one(cdi_batch *b, int parity, double vs, cudaStream_t s)
 {
     if (b->flat)
-        cdi::batch_kernel<T, BX, BY, true><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
+        cdi::batch_kernel<T, BX, BY, 1><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
             (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
             b->box_done, b->recs);
     else
-        cdi::batch_kernel<T, BX, BY, false><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
+        cdi::batch_kernel<T, BX, BY, 0><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
             (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
             b->box_done, b->recs);
+}
+
+template <typename T>
+static void batch_launch_plane(cdi_batch *b, int parity, double vs, cudaStream_t s)
+{
+    cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2><<<b->nblocks, dim3(cdi::PLANE_NT, 1), b->plane_bytes, s>>>(
+        (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
+        b->recs);
 }
 
 template <typename T>
@@ -273,6 +409,7 @@ static int batch_launch(cdi_batch *b, int parity, double vs, cudaStream_t s)
     case 1: batch_launch_one<T, 32, 16>(b, parity, vs, s); break;
     case 2: batch_launch_one<T, 64, 8>(b, parity, vs, s); break;
     case 3: batch_launch_one<T, 32, 4>(b, parity, vs, s); break;
+    case cdi::BATCH_TILE_PLANE: batch_launch_plane<T>(b, parity, vs, s); break;
     default: return cdi::set_error(CDI_ERR_STATE, "bad batch tile");
     }
     cudaError_t e = cudaGetLastError();
@@ -313,6 +450,7 @@ int cdi_batch_create(cdi_batch **out, const cdi_box_desc *boxes, int nbox, int d
     b->desc.assign(boxes, boxes + nbox);
     b->flat = true;
     for (int i = 0; i < nbox; ++i) b->flat = b->flat && boxes[i].nz == 1;
+    b->plane_bytes = plane_bytes(b);
     cudaError_t e;
     int dev = 0;
     std::vector<StatsRec> hrec(nbox);
@@ -452,11 +590,15 @@ int cdi_batch_autotune(cdi_batch *b, int reps, float *best_ms, void *stream)
         cudaEventDestroy(e0);
         return cdi::set_error(CDI_ERR_CUDA, "cudaEventCreate");
     }
+    // (2D batches: the z depth changes nothing, one trial per tile; the
+    // whole-plane tile where the planes fit)
     const int zopts[] = {8, 16, 32, 64, 0};
+    const int nz_opts = b->flat ? 1 : (int)(sizeof(zopts) / sizeof(int));
     int best_tile = b->tile, best_z = b->zdepth, rc = CDI_OK;
     float best_t = 1e30f;
     for (int tile = 0; tile < cdi::BATCH_TILES && rc == CDI_OK; ++tile) {
-        for (int zi = 0; zi < (int)(sizeof(zopts) / sizeof(int)) && rc == CDI_OK; ++zi) {
+        if (tile == cdi::BATCH_TILE_PLANE && b->plane_bytes == 0) continue;
+        for (int zi = 0; zi < nz_opts && rc == CDI_OK; ++zi) {
             if ((rc = rebuild(b, tile, zopts[zi])) != CDI_OK) break;
             if ((rc = launch_any(b, b->parity, 1.0, s)) != CDI_OK) break;  // warm-up
             if ((e = cudaEventRecord(e0, s)) != cudaSuccess) {

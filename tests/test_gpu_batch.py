@@ -162,3 +162,82 @@ def test_batch_of_2d_boxes_matches_oracle(dtype, mixed):
             ours = b.current(i).double().cpu().numpy()
             assert np.abs(ours - ref).max() <= tol, (tile, i)
             assert st[i]["min"] == ours.min() and st[i]["max"] == ours.max()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_whole_plane_tile(dtype):
+    """Batch tile 4 (one unit per whole 2D box, the plane held in shared memory) gives the
+    oracle's steps and, bit for bit, the single-plane tiles' fields, extrema and counts
+    (the sums group the cells differently), stepped one launch at a time and as a graph
+    run; extents 1 and 2 included."""
+    sizes = [(7, 9), (33, 40), (16, 64), (1, 37), (37, 1), (2, 5), (1, 1), (50, 50), (3, 2)]
+    boxes = flat_boxes(dtype, sizes, 23)
+    twins = [dict(x, phi_a=x["phi_a"].clone(), phi_b=torch.empty_like(x["phi_b"])) for x in boxes]
+    bp, bt = cdi.Batch(boxes), cdi.Batch(twins)
+    bp.set_launch(4, 0)
+    bt.set_launch(0, 0)
+    lp = bp.get_launch()
+    assert lp["tile"] == 4 and lp["units"] == len(sizes)
+    for _ in range(3):
+        bp.step(0.9)
+        bt.step(0.9)
+    sp, stt = bp.stats(), bt.stats()
+    t = np.float64 if dtype == torch.float64 else np.float32
+    tol = 1e-12 if dtype == torch.float64 else 3e-6
+    for i, x in enumerate(boxes):
+        ours = bp.current(i)
+        assert torch.equal(ours, bt.current(i)), i
+        same_stats(sp[i], stt[i], dtype)
+        f = x["fields"]
+        rin = [np.asarray(a, t).astype(np.float64) for a in (f.phi, f.u, f.v, f.w)]
+        ref = rin[0]
+        for _ in range(3):
+            ref = oracle.step(ref, *rin[1:], f.h, x["dt"], x["eps"], x["gamma"], 0.9)
+        assert np.abs(ours.double().cpu().numpy() - ref).max() <= tol, i
+    bp.run(4)
+    bt.run(4)
+    for i, (a, b) in enumerate(zip(bp.stats(), bt.stats())):
+        assert torch.equal(bp.current(i), bt.current(i)), i
+        same_stats(a, b, dtype)
+
+
+def same_stats(a, b, dtype):
+    """Equal statistics records: extrema and counts exactly, sums to rounding."""
+    rel = 1e-13 if dtype == torch.float64 else 1e-6
+    for k in a:
+        if k in ("mass", "sum"):
+            assert abs(a[k] - b[k]) <= rel * max(abs(b[k]), 1e-300), k
+        else:
+            assert a[k] == b[k], k
+
+
+def test_whole_plane_tile_refusals():
+    """Tile 4 is refused for 3D boxes and for planes larger than shared memory (the launch
+    stays as it was), and the autotuner then does not try it."""
+    b3 = cdi.Batch(make_boxes(torch.float32, nbox=2, seed=5))
+    with pytest.raises(cdi.CDIError):
+        b3.set_launch(4, 0)
+    assert b3.get_launch()["tile"] == 0
+    big = cdi.Batch(flat_boxes(torch.float64, [(200, 200), (10, 10)], 3))  # 3 x 40000 x 8 B
+    with pytest.raises(cdi.CDIError):
+        big.set_launch(4, 0)
+    big.autotune(reps=1)
+    assert big.get_launch()["tile"] != 4
+
+
+def test_whole_plane_batches_of_different_sizes():
+    """Two batches whose planes need different shared memory (about 190 KB and 3 KB),
+    stepped alternately with tile 4: both follow the oracle."""
+    A = flat_boxes(torch.float64, [(90, 90), (20, 30)], 7)
+    B = flat_boxes(torch.float64, [(10, 12)], 8)
+    ba, bb = cdi.Batch(A), cdi.Batch(B)
+    ba.set_launch(4, 0)
+    bb.set_launch(4, 0)
+    for _ in range(2):
+        ba.step(1.0)
+        bb.step(1.0)
+    for bt, boxes in ((ba, A), (bb, B)):
+        for i, x in enumerate(boxes):
+            f = x["fields"]
+            ref = oracle.run(f.phi, f.u, f.v, f.w, f.h, x["dt"], x["eps"], x["gamma"], 2)
+            assert np.abs(bt.current(i).cpu().numpy() - ref).max() <= 1e-12, i
