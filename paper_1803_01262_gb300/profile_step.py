@@ -9,7 +9,10 @@ configuration set explicitly so that a profiler capture is deterministic:
 
 ``--kernel batch`` runs the 64-box batch workload of the benchmark instead
 (edges U{32..160}, seed 0), with ``--tile`` / ``--zdepth`` as its work-unit
-tile and planes per unit (``--tile -1``: the autotuner's choice).
+tile and planes per unit (``--tile -1``: the autotuner's choice);
+``--kernel phase`` the benchmark's phase-diagram sweep (256 FP64 boxes of
+50 x 50 cells, the Table 2 drop at a 16 x 16 grid of (eps/dx, gamma/|u|)
+points) with ``--tile`` as its batch tile (4: one unit per whole box).
 """
 from __future__ import annotations
 
@@ -26,7 +29,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
-    ap.add_argument("--kernel", choices=["forward", "adjoint", "batch"], default="forward")
+    ap.add_argument("--kernel", choices=["forward", "adjoint", "batch", "phase"], default="forward")
     ap.add_argument("--zdepth", type=int, default=64)
     ap.add_argument("--tile", type=int, default=-1)
     ap.add_argument("--nchunks", type=int, default=0)
@@ -35,6 +38,8 @@ def main():
     dtype = torch.float32 if args.dtype == "f32" else torch.float64
     if args.kernel == "batch":
         return run_batch(args, dtype)
+    if args.kernel == "phase":
+        return run_phase(args)
     n = args.n
     f = I.deformation_3d(n)
     g = cdi.Grid(n, n, n, f.h, dtype)
@@ -72,6 +77,21 @@ def run_batch(args, dtype):
         b.autotune(reps=2)
     else:
         b.set_launch(args.tile, args.zdepth)
+    for _ in range(args.steps):
+        b.step(1.0)
+    torch.cuda.synchronize()
+    print("launch", b.get_launch(), b.info())
+
+
+def run_phase(args):
+    import numpy as np
+    from . import phase as P
+    pts = [(float(a), float(b)) for a in np.linspace(0.55, 2.0, 16) for b in np.linspace(0.3, 3.0, 16)]
+    b = cdi.Batch(P.phase_boxes(pts, 50, torch.float64))
+    if args.tile < 0:
+        b.autotune(reps=2)
+    else:
+        b.set_launch(args.tile, 0)
     for _ in range(args.steps):
         b.step(1.0)
     torch.cuda.synchronize()
