@@ -46,7 +46,8 @@ __device__ __forceinline__ Partial warp_reduce(Partial p)
 
 // Per-thread accumulator.  FP32 keeps a compensated (Kahan) float sum so the
 // per-thread partial is accurate before it is promoted to double; FP64 sums
-// directly.  min/max are exact; NaN is ignored by min/max and not counted.
+// directly.  min/max are exact; NaN is ignored by min/max and not counted
+// (FP64: min, max and range tests on order keys, below).
 template <typename T>
 struct Acc;
 
@@ -116,50 +117,77 @@ struct Acc<float> {
     }
 };
 
+// Order-preserving 64-bit integer key of a double: for numbers a < b exactly
+// when okey(a) < okey(b) (the magnitude bits of negatives are flipped; -0
+// sorts just below +0); NaNs fall outside [okey(-inf), okey(+inf)].  The FP64
+// accumulator takes its min, max and range tests on these keys, on the
+// integer pipes, leaving GB300's narrow FP64 pipe to the step itself.
+__device__ __forceinline__ long long okey(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double from_okey(long long k)
+{
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+constexpr long long KEY_PINF = 0x7ff0000000000000LL;              // okey(+inf)
+constexpr long long KEY_NINF = (long long)0x800fffffffffffffULL;  // okey(-inf)
+constexpr long long KEY_NZERO = -1;                                // okey(-0.0)
+constexpr long long KEY_ONE = 0x3ff0000000000000LL;               // okey(1.0)
+
 template <>
 struct Acc<double> {
-    double s, mn, mx;
+    double s;
+    long long kmn, kmx;  // keys of the min and max so far
     int ns, nt;
     __device__ __forceinline__ void init()
     {
-        s = 0.0; mn = INFINITY; mx = -INFINITY; ns = 0; nt = 0;
+        s = 0.0; kmn = KEY_PINF; kmx = KEY_NINF; ns = 0; nt = 0;
+    }
+    // p < 0 (strictly: -0 is not below 0), p > 1, p < -tol, p > 1 + tol, for a number p
+    __device__ __forceinline__ static bool num(long long k) { return k >= KEY_NINF && k <= KEY_PINF; }
+    __device__ __forceinline__ void count(long long k, double tol)
+    {
+        ns += num(k) & ((k < KEY_NZERO) | (k > KEY_ONE));
+        nt += num(k) & ((k < okey(-tol)) | (k > okey(1.0 + tol)));
     }
     __device__ __forceinline__ void add(double p, double tol)
     {
         s += p;
-        mn = fmin(mn, p);
-        mx = fmax(mx, p);
-        if (p < 0.0 || p > 1.0) {
-            ++ns;
-            nt += (p < -tol) | (p > 1.0 + tol);
+        const long long k = okey(p);
+        if (num(k)) {
+            kmn = min(kmn, k);
+            kmx = max(kmx, k);
+            if ((k < KEY_NZERO) | (k > KEY_ONE)) count(k, tol);
         }
     }
     template <int N>
     __device__ __forceinline__ void add_group(const double *o, double tol)
     {
-        double gmn = o[0], gmx = o[0];
+        long long k[N], gmn = KEY_PINF, gmx = KEY_NINF;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
             s += o[i];
-            gmn = fmin(gmn, o[i]);
-            gmx = fmax(gmx, o[i]);
-        }
-        mn = fmin(mn, gmn);
-        mx = fmax(mx, gmx);
-        if (gmn < 0.0 || gmx > 1.0) {
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                ns += (o[i] < 0.0) | (o[i] > 1.0);
-                nt += (o[i] < -tol) | (o[i] > 1.0 + tol);
+            k[i] = okey(o[i]);
+            if (num(k[i])) {
+                gmn = min(gmn, k[i]);
+                gmx = max(gmx, k[i]);
             }
+        }
+        kmn = min(kmn, gmn);
+        kmx = max(kmx, gmx);
+        if ((gmn < KEY_NZERO) | (gmx > KEY_ONE)) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) count(k[i], tol);
         }
     }
     __device__ __forceinline__ Partial partial() const
     {
         Partial r;
         r.sum = s;
-        r.mn = mn;
-        r.mx = mx;
+        r.mn = from_okey(kmn);
+        r.mx = from_okey(kmx);
         r.ns = ns;
         r.nt = nt;
         return r;
