@@ -236,6 +236,7 @@ def test_mass_and_bounds_planted(dtype):
     t = NPT[dtype]
     tol = float(np.finfo(t).eps)
     p[1, 1, 1] = 1.0 + tol            # inside the tolerant bound, outside [0, 1]
+    p[3, 3, 3] = -0.0                 # not below 0 (the FP64 range tests run on integer keys)
     g = cdi.Grid(shape[2], shape[1], shape[0], 0.1, dtype)
     s = g.mass_and_bounds(dev(p, dtype))
     pr = p.astype(t).astype(np.float64)
