@@ -19,7 +19,11 @@
  *     phi'_c = phi_c - (dt/dx) sum_d (F_{c+1/2 e_d} - F_{c-1/2 e_d}),
  *
  * where vs is the caller's velocity scale (the time factor of a
- * time-periodic field, e.g. cos(pi t/T) in Eq. 33).
+ * time-periodic field, e.g. cos(pi t/T) in Eq. 33).  The kernels evaluate
+ * the normal as g * rsqrt(|g|^2 + tau), tau the smallest normal number of
+ * the dtype (FLT_MIN, DBL_MIN): finite at g = 0, where s = 0 exactly, and
+ * the unit normal wherever |g|^2 is far above tau (the paper divides by
+ * |grad phi| and is silent where it vanishes).
  *
  * Conventions shared by every call:
  *  - Arrays are dense [nz][ny][nx] (x fastest), element type float
