@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libcdi.so")
-SOURCES = ["cdi_fwd.cu", "cdi_fwd_tma.cu", "cdi_adj.cu", "cdi_batch.cu", "cdi_rk.cu", "cdi_api.cu", "cdi_noalloc.cu"]
+SOURCES = ["cdi_fwd.cu", "cdi_fwd_tma.cu", "cdi_adj.cu", "cdi_batch.cu", "cdi_api.cu", "cdi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The forward step flushes FP32 denormals (values below 1.2e-38) to zero; this
 # removes denormal handling around rsqrtf and is far below every tolerance.
@@ -55,7 +55,10 @@ def build(force: bool = False, ptxas_verbose: bool = False, verbose: bool = Fals
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     cc = nvcc()
-    srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
+    missing = [s for s in SOURCES if not os.path.exists(os.path.join(CSRC, s))]
+    if missing:
+        raise RuntimeError(f"CUDA sources missing: {', '.join(missing)}")
+    srcs = SOURCES
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
 
     def compile_one(src):
