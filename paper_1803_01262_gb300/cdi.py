@@ -48,6 +48,7 @@ class Stats(ctypes.Structure):
                 ("n_tol_run", ctypes.c_longlong), ("steps_run", ctypes.c_longlong)]
 
     def as_dict(self):
+        """The record as a dict keyed by its field names."""
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
@@ -194,9 +195,11 @@ class Grid:
 
     @property
     def Df(self):
+        """Number of axes with extent > 1 (D_f of Eq. 19 and Eq. 25)."""
         return sum(1 for s in self.shape if s > 1)
 
     def close(self):
+        """Free the grid and its device scratch (cdi_destroy_grid); idempotent."""
         if self._h:
             lib().cdi_destroy_grid(self._h)
             self._h = ctypes.c_void_p()
@@ -225,6 +228,7 @@ class Grid:
 
     @property
     def U(self):
+        """U of the velocity set: the largest face |component| (Eq. 24 reading)."""
         out = ctypes.c_double()
         _ck(lib().cdi_get_umax(self._h, ctypes.byref(out)))
         return out.value
@@ -270,9 +274,11 @@ class Grid:
         return s.as_dict()
 
     def reset_run_stats(self, stream=None):
+        """Zero the run accumulators (*_run, steps_run) of the statistics record."""
         _ck(lib().cdi_reset_run_stats(self._h, _stream(stream)))
 
     def mass_and_bounds(self, phi, stream=None):
+        """Mass, sum, min, max and violation counts of any field phi (synchronises)."""
         s = Stats()
         _ck(lib().cdi_mass_and_bounds(self._h, self._arr(phi, "phi"), ctypes.byref(s),
                                       _stream(stream)))
@@ -302,6 +308,7 @@ class Grid:
         _ck(lib().cdi_set_sharpening(self._h, SHARPEN[mode]))
 
     def get_sharpening(self):
+        """The sharpening form of the forward step: "centre" (default) or "face"."""
         m = ctypes.c_int()
         _ck(lib().cdi_get_sharpening(self._h, ctypes.byref(m)))
         return {v: k for k, v in SHARPEN.items()}[m.value]
@@ -311,6 +318,7 @@ class Grid:
         _ck(lib().cdi_set_launch(self._h, which, tile, blocks_per_sm, nchunks))
 
     def get_launch(self, which=CDI_KERNEL_FORWARD):
+        """The launch configuration in use: tile, resident blocks and z-chunk count."""
         t, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _ck(lib().cdi_get_launch(self._h, which, ctypes.byref(t), ctypes.byref(b), ctypes.byref(c)))
         return dict(tile=t.value, nblocks=b.value, nchunks=c.value)
@@ -374,6 +382,7 @@ class Batch:
                                    len(boxes), _dtype_code(self.dtype)))
 
     def close(self):
+        """Free the batch's device tables and captured graphs; idempotent."""
         if self._h:
             lib().cdi_batch_destroy(self._h)
             self._h = ctypes.c_void_p()
@@ -385,15 +394,18 @@ class Batch:
             pass
 
     def info(self):
+        """Parity (which buffer holds the state), work units, blocks per launch, cells."""
         p, u, n, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
         _ck(lib().cdi_batch_info(self._h, ctypes.byref(p), ctypes.byref(u), ctypes.byref(n),
                                  ctypes.byref(c)))
         return dict(parity=p.value, units=u.value, nblocks=n.value, cells=c.value)
 
     def current(self, i):
+        """The tensor holding box i's current state."""
         return self.boxes[i]["phi_b" if self.info()["parity"] else "phi_a"]
 
     def step(self, vel_scale=1.0, stream=None):
+        """One Euler step of every box with face velocity vel_scale * (u, v, w)."""
         _ck(lib().cdi_batch_step(self._h, vel_scale, _stream(stream)))
 
     def run(self, nsteps, stream=None):
@@ -406,6 +418,7 @@ class Batch:
         _ck(lib().cdi_batch_set_launch(self._h, tile, zdepth))
 
     def get_launch(self):
+        """The batch launch configuration: tile, z depth, blocks per launch, work units."""
         t, z, n, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _ck(lib().cdi_batch_get_launch(self._h, ctypes.byref(t), ctypes.byref(z), ctypes.byref(n),
                                        ctypes.byref(u)))
@@ -418,9 +431,11 @@ class Batch:
         return ms.value
 
     def stats(self, stream=None):
+        """Per-box statistics records, last step and run accumulators (synchronises)."""
         out = (Stats * len(self.boxes))()
         _ck(lib().cdi_batch_stats(self._h, ctypes.cast(out, ctypes.c_void_p), _stream(stream)))
         return [s.as_dict() for s in out]
 
     def reset_run_stats(self, stream=None):
+        """Zero every box's run accumulators."""
         _ck(lib().cdi_batch_reset_run_stats(self._h, _stream(stream)))
