@@ -318,7 +318,7 @@ class Grid:
         _ck(lib().cdi_set_launch(self._h, which, tile, blocks_per_sm, nchunks))
 
     def get_launch(self, which=CDI_KERNEL_FORWARD):
-        """The launch configuration in use: tile, resident blocks and z-chunk count."""
+        """The launch configuration in use: tile, blocks per launch, z chunks (-1: balanced)."""
         t, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _ck(lib().cdi_get_launch(self._h, which, ctypes.byref(t), ctypes.byref(b), ctypes.byref(c)))
         return dict(tile=t.value, nblocks=b.value, nchunks=c.value)
