@@ -15,7 +15,8 @@ from paper_1803_01262_gb300 import autograd as AG
 
 
 class FakeGrid:
-    """phi' = phi + dt vs (sin(phi) + u phi); its adjoint lam = lam' (1 + dt vs (cos(phi) + u))."""
+    """phi' = phi + dt vs (sin(phi) + u phi); its adjoint lam = lam' (1 + dt vs (cos(phi) + u)),
+    and the velocity gradient it accumulates, d phi'/du = dt vs phi (v and w do not enter)."""
 
     def __init__(self):
         self.steps = 0
@@ -30,6 +31,8 @@ class FakeGrid:
 
     def step_adjoint(self, phi, lam, out, dt, eps, gamma, vs=1.0, grads=None):
         self.adjoints += 1
+        if grads is not None:
+            grads[0].add_(lam * dt * vs * phi)
         out.copy_(lam * (1 + dt * vs * (torch.cos(phi) + self.u)))
 
 
@@ -73,6 +76,28 @@ def test_gradient_matches_autograd_for_every_layout(nsteps, ckpt, inner, period)
         last = s + ((e - 1 - s) // inn) * inn
         expect += last - s + sum(min(ss + inn, e) - ss - 1 for ss in range(s, e, inn))
     assert grid.steps - fwd_steps == expect
+
+
+@pytest.mark.parametrize("nsteps,ckpt,inner", [(1, 16, None), (37, 16, 5), (50, 8, 3)])
+@pytest.mark.parametrize("period", [0.0, 0.37])
+def test_velocity_gradient_matches_autograd(nsteps, ckpt, inner, period):
+    """The velocity gradient summed over the recomputed states (each step with its own
+    velocity scale) equals torch autograd through the same map; phi0's gradient too."""
+    g = torch.Generator().manual_seed(100 + nsteps)
+    phi0 = torch.rand(4, 5, 3, dtype=torch.float64, generator=g)
+    u0 = torch.rand(4, 5, 3, dtype=torch.float64, generator=g) - 0.5
+    v = torch.zeros_like(u0)
+    w = torch.randn(4, 5, 3, dtype=torch.float64, generator=g)
+    dt = 0.05
+    x, ur = phi0.clone().requires_grad_(True), u0.clone().requires_grad_(True)
+    (reference(x, ur, nsteps, dt, period) * w).sum().backward()
+
+    y, uy = phi0.clone().requires_grad_(True), u0.clone().requires_grad_(True)
+    out = AG.rollout(y, uy, v, v, FakeGrid(), nsteps, dt, 1.0, 1.0, period=period, ckpt_every=ckpt,
+                     inner_every=inner)
+    (out * w).sum().backward()
+    assert torch.allclose(uy.grad, ur.grad, rtol=1e-13, atol=1e-14)
+    assert torch.allclose(y.grad, x.grad, rtol=1e-13, atol=1e-14)
 
 
 def test_rejects_bad_intervals():
