@@ -1,4 +1,4 @@
-"""Host logic of the checkpoint-recompute rollout, on the CPU.
+"""Host logic of the checkpoint-recompute rollout and the inverse problem, on the CPU.
 
 A stand-in grid whose step is an elementwise nonlinear map (and whose adjoint
 is that map's exact transpose) checks that the backward applies the adjoint
@@ -107,3 +107,38 @@ def test_rejects_bad_intervals():
         AG.rollout(p, p, p, p, grid, 3, 0.1, 1.0, 1.0, ckpt_every=0)
     with pytest.raises(ValueError):
         AG.rollout(p, p, p, p, grid, 3, 0.1, 1.0, 1.0, ckpt_every=4, inner_every=0)
+
+
+def test_sphere_phi_matches_the_host_generator():
+    """The differentiable torch sphere equals the numpy generator's tanh sphere (periodic
+    minimum image) to rounding."""
+    import numpy as np
+
+    from paper_1803_01262_gb300 import inputs as I
+    shape, h = (12, 10, 14), 1.0 / 14
+    p = torch.tensor([0.45, 0.62, 0.05, 0.25], dtype=torch.float64)   # wraps in z
+    a = AG.sphere_phi(p, shape, h, h).numpy()
+    b = I.tanh_profile(I.sphere_distance(shape, h, (0.45, 0.62, 0.05), 0.25), h)
+    assert np.abs(a - b).max() < 1e-14
+
+
+def test_inverse_problem_loop_descends():
+    """The inverse-problem loop (sphere -> rollout -> loss -> adjoint -> Adam) on the stand-in
+    grid: the loss falls by two orders and the parameters approach the target's."""
+    shape, h = (12, 12, 12), 1.0 / 12
+
+    class Grid(FakeGrid):
+        dx, Df, dtype = h, 3, torch.float64
+
+    Grid.shape = shape
+    g = Grid()
+    u = torch.full(shape, 0.3, dtype=torch.float64)
+    z = torch.zeros(shape, dtype=torch.float64)
+    true = torch.tensor([0.5, 0.5, 0.5, 0.3], dtype=torch.float64)
+    with torch.no_grad():
+        target = AG.rollout(AG.sphere_phi(true, shape, h, h), u, z, z, g, 20, 0.02, h, 1.0)
+    init = torch.tensor([0.47, 0.52, 0.5, 0.27], dtype=torch.float64)
+    theta, losses = AG.inverse_problem(target, u, z, z, g, 20, 0.02, h, 1.0, init, iters=40, lr=5e-3,
+                                       ckpt_every=8)
+    assert losses[-1] < 0.02 * losses[0]
+    assert float((theta - true).abs().max()) < 0.5 * float((init - true).abs().max())
