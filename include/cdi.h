@@ -65,7 +65,8 @@ enum {
     CDI_ERR_CONDITION = -4,  /* Eq. 17/24 or A <= 1/(2 D_f) not satisfied */
     CDI_ERR_NAN = -5,        /* non-finite value detected in a reduction   */
     CDI_ERR_TIMEOUT = -6,    /* a bounded device-side wait gave up         */
-    CDI_ERR_STATE = -7       /* call out of order (e.g. no velocity set)   */
+    CDI_ERR_STATE = -7,      /* call out of order (e.g. no velocity set)   */
+    CDI_ERR_BOUNDS = -8      /* checked build: a kernel index was out of range */
 };
 
 enum { CDI_F32 = 0, CDI_F64 = 1 };
@@ -232,6 +233,18 @@ CDI_API int cdi_check_condition(double eps_over_dx, double gamma_over_U, double 
  * gamma eps) (Eq. 27), RK4 2.79 dx^2/(4 D_f gamma eps) (Eq. 28). */
 CDI_API int cdi_max_dt(double dx, double eps, double gamma, int Df, int scheme, double *dt);
 
+/* Time step for points that may lie below the crossover line: the smaller of
+ * the scheme's diffusive limit (cdi_max_dt) and a mixed advective-diffusive
+ * limit c dx / (sum_d umax[d] + D_f gamma), umax[d] (d < Df) the largest face
+ * |velocity component| along each non-degenerate axis.  CDI_RK4: c = 2.83, the
+ * mixed criterion of Eq. 32 (2D: dx 2.83/(max u + max v + 2 gamma)), so the
+ * result is min(Eq. 31, Eq. 32) in 2D.  CDI_EULER: c = 1, the 1D step of
+ * Eq. 10 at the crossover line, dx/(u + gamma), summed over the axes
+ * (2D: dx/(max u + max v + 2 gamma)).  The paper gives no mixed criterion for
+ * RK2 and RK3: CDI_ERR_ARG.  Host arithmetic only. */
+CDI_API int cdi_max_dt_mixed(double dx, double eps, double gamma, const double *umax, int Df,
+                             int scheme, double *dt);
+
 /*
  * Batched boxes.  Many independent periodic boxes of uneven sizes, each with
  * its own spacing, eps, gamma, dt and face velocities, advance together: one
@@ -319,6 +332,23 @@ CDI_API int cdi_get_sharpening(const cdi_grid *g, int *mode);
  * CDI_OK would mean a time-out went unreported.  Synchronises the stream. */
 CDI_API int cdi_probe_bounded_wait(cdi_grid *g, double limit_s, void *stream);
 
+/* Checked builds.  A library compiled with -DCDI_CHECKED (build.py
+ * --checked, _lib/libcdi_checked.so) tests every index its kernels derive for a
+ * global access -- in-plane offsets of staged tiles, plane indices, output
+ * offsets -- against the array extent before use; an index out of range is
+ * replaced by 0 (the access stays inside the array) and recorded in the
+ * grid's device status words, and the next statistics read-back
+ * (cdi_step_stats, cdi_mass_and_bounds, cdi_step_host) returns CDI_ERR_BOUNDS
+ * with the count and the last bad index in the message.  A debugging aid, not
+ * part of the paper; the regular build has no checks. */
+CDI_API int cdi_is_checked_build(void);
+
+/* Diagnostic of the checked build: one kernel thread tests an index one past
+ * its limit.  Returns CDI_ERR_BOUNDS (the expected result: the check recorded
+ * it), CDI_OK if nothing was recorded, CDI_ERR_STATE in a regular build.
+ * Synchronises the stream. */
+CDI_API int cdi_probe_bounds_check(cdi_grid *g, void *stream);
+
 /* Kernels with a tunable launch configuration. */
 enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
 
@@ -373,9 +403,13 @@ CDI_API int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, doubl
  *
  * The first call on a device, made with that device current, looks up the
  * scratch's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  Every call shares the one scratch array, which
- * keeps the last call's contents: calls that overlap on the GPU race on it.
- * Each call clears the block counter on its stream before its launch.
+ * before any stream capture.  The address is kept per device together with
+ * the id of the context it was found in; a call in a new context of the
+ * device (after cudaDeviceReset) looks it up again, and that call too should
+ * come before any stream capture.  Every call shares the one scratch array,
+ * which keeps the last call's contents: calls that overlap on the GPU race on
+ * it.  Each call clears the block counter on its stream before its launch.
+ * phi_out and stats_dev may overlap none of the other arrays (CDI_ERR_ARG).
  */
 #define CDI_NOALLOC_MAX_BLOCKS 8192
 CDI_API int cdi_step_noalloc(int nx, int ny, int nz, double dx, int dtype, const void *phi_in,

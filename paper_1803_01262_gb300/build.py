@@ -1,9 +1,12 @@
 """Build the CDI CUDA library ``_lib/libcdi.so`` for sm_103a with nvcc.
 
 Each translation unit is compiled in parallel, then linked into one shared
-library with a plain C ABI (include/cdi.h).  Usage::
+library with a plain C ABI (include/cdi.h).  ``checked=True`` builds the
+bounds-checked variant ``_lib/libcdi_checked.so`` (-DCDI_CHECKED: kernels test
+the indices they derive and record bad ones in the device status words).
+Usage::
 
-    python -m paper_1803_01262_gb300.build [--force] [--ptxas-v]
+    python -m paper_1803_01262_gb300.build [--force] [--ptxas-v] [--checked]
 """
 from __future__ import annotations
 
@@ -20,6 +23,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libcdi.so")
+LIB_CHECKED = os.path.join(OUT_DIR, "libcdi_checked.so")
 SOURCES = ["cdi_fwd.cu", "cdi_fwd_tma.cu", "cdi_adj.cu", "cdi_batch.cu", "cdi_api.cu", "cdi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The forward step flushes FP32 denormals (values below 1.2e-38) to zero; this
@@ -42,18 +46,22 @@ def _deps():
     return [f for f in files if os.path.isfile(f)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, ptxas_verbose: bool = False, verbose: bool = False) -> str:
-    """Compile and link the library if any source is newer than it."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, ptxas_verbose: bool = False, verbose: bool = False,
+          checked: bool = False) -> str:
+    """Compile and link the library (the checked variant with ``checked``) if any source
+    is newer than it; returns its path."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
+    obj_dir = os.path.join(OUT_DIR, "checked") if checked else OUT_DIR
+    os.makedirs(obj_dir, exist_ok=True)
     cc = nvcc()
     missing = [s for s in SOURCES if not os.path.exists(os.path.join(CSRC, s))]
     if missing:
@@ -61,9 +69,12 @@ def build(force: bool = False, ptxas_verbose: bool = False, verbose: bool = Fals
     srcs = SOURCES
     extra = ["-Xptxas", "-v"] if ptxas_verbose else []
 
+    defs = ["-DCDI_CHECKED"] if checked else []
+
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *PER_FILE.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *FLAGS, *defs, *PER_FILE.get(src, []), *extra, "-c", os.path.join(CSRC, src),
+               "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         return src, obj, r
 
@@ -74,19 +85,20 @@ def build(force: bool = False, ptxas_verbose: bool = False, verbose: bool = Fals
             sys.stderr.write(r.stdout + r.stderr)
         if r.returncode:
             raise RuntimeError(f"nvcc failed on {src}")
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for _, o, _ in results]]
+    tmp = lib + f".{os.getpid()}.tmp"
+    cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for _, o, _ in results], "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode:
         sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError("nvcc link failed")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
     ap.add_argument("--ptxas-v", action="store_true")
+    ap.add_argument("--checked", action="store_true")
     a = ap.parse_args()
-    print(build(force=a.force, ptxas_verbose=a.ptxas_v, verbose=True))
+    print(build(force=a.force, ptxas_verbose=a.ptxas_v, verbose=True, checked=a.checked))

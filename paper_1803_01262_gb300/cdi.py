@@ -16,10 +16,13 @@ import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "libcdi.so")
+# CDI_LIBRARY=checked selects the bounds-checked build (build.build(checked=True)).
+LIB_PATH = os.path.join(_PKG, "_lib", "libcdi_checked.so" if os.environ.get("CDI_LIBRARY") == "checked"
+                        else "libcdi.so")
 
 CDI_OK, CDI_ERR_ARG, CDI_ERR_DIM, CDI_ERR_CUDA = 0, -1, -2, -3
 CDI_ERR_CONDITION, CDI_ERR_NAN, CDI_ERR_TIMEOUT, CDI_ERR_STATE = -4, -5, -6, -7
+CDI_ERR_BOUNDS = -8
 CDI_F32, CDI_F64 = 0, 1
 CDI_EULER, CDI_RK2, CDI_RK3, CDI_RK4 = 0, 1, 2, 3
 CDI_CHECK_CONDITION = 1
@@ -31,7 +34,7 @@ FWD_TILES = 7
 ADJ_TILES = 4
 
 _ERRNAMES = {-1: "CDI_ERR_ARG", -2: "CDI_ERR_DIM", -3: "CDI_ERR_CUDA", -4: "CDI_ERR_CONDITION",
-             -5: "CDI_ERR_NAN", -6: "CDI_ERR_TIMEOUT", -7: "CDI_ERR_STATE"}
+             -5: "CDI_ERR_NAN", -6: "CDI_ERR_TIMEOUT", -7: "CDI_ERR_STATE", -8: "CDI_ERR_BOUNDS"}
 
 
 class CDIError(RuntimeError):
@@ -75,8 +78,11 @@ SIGNATURES = {
     "cdi_step_adjoint": [_V, _V, _V, _V, _V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _V],
     "cdi_check_condition": [_Dbl, _Dbl, _Dbl, _I],
     "cdi_max_dt": [_Dbl, _Dbl, _Dbl, _I, _I, _P(_Dbl)],
+    "cdi_max_dt_mixed": [_Dbl, _Dbl, _Dbl, _P(_Dbl), _I, _I, _P(_Dbl)],
     "cdi_set_sharpening": [_V, _I],
     "cdi_probe_bounded_wait": [_V, _Dbl, _V],
+    "cdi_is_checked_build": [],
+    "cdi_probe_bounds_check": [_V, _V],
     "cdi_get_sharpening": [_V, _P(_I)],
     "cdi_set_launch": [_V, _I, _I, _I, _I],
     "cdi_get_launch": [_V, _I, _P(_I), _P(_I), _P(_I)],
@@ -143,6 +149,11 @@ def _dtype_code(dtype):
     raise ValueError("dtype must be torch.float32 or torch.float64")
 
 
+def is_checked_build():
+    """True if the loaded library is the bounds-checked build."""
+    return bool(lib().cdi_is_checked_build())
+
+
 def check_condition(eps_over_dx, gamma_over_U, A, Df):
     """Eq. 17/24 and A <= 1/(2 D_f): True if both hold."""
     return bool(_ck(lib().cdi_check_condition(eps_over_dx, gamma_over_U, A, Df)))
@@ -152,6 +163,16 @@ def max_dt(dx, eps, gamma, Df, scheme=CDI_EULER):
     """Largest bounded step of Eq. 25-28 for the given scheme."""
     out = ctypes.c_double()
     _ck(lib().cdi_max_dt(dx, eps, gamma, Df, scheme, ctypes.byref(out)))
+    return out.value
+
+
+def max_dt_mixed(dx, eps, gamma, umax, scheme=CDI_EULER):
+    """min(diffusive limit of the scheme, mixed advective-diffusive limit): Eq. 31/32 for
+    RK4, the Eq. 10 analogue for Euler; ``umax`` lists the largest |velocity component| of
+    each non-degenerate axis."""
+    um = (ctypes.c_double * len(umax))(*[float(x) for x in umax])
+    out = ctypes.c_double()
+    _ck(lib().cdi_max_dt_mixed(dx, eps, gamma, um, len(umax), scheme, ctypes.byref(out)))
     return out.value
 
 
@@ -301,6 +322,11 @@ class Grid:
         """Make a bounded device wait run out (see cdi_probe_bounded_wait); raises CDIError
         with CDI_ERR_TIMEOUT when the time-out is reported, as it should be."""
         _ck(lib().cdi_probe_bounded_wait(self._h, limit_s, _stream(stream)))
+
+    def probe_bounds_check(self, stream=None):
+        """Checked builds: make the index check record one bad index (cdi_probe_bounds_check);
+        raises CDIError with CDI_ERR_BOUNDS when it is reported, as it should be."""
+        _ck(lib().cdi_probe_bounds_check(self._h, _stream(stream)))
 
     def set_sharpening(self, mode):
         """"centre" (Section 2.2, the default) or "face" (face-product sharpening, forward

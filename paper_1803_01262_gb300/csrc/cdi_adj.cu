@@ -105,23 +105,23 @@ adj_kernel(const AdjArgs<T> a)
     for (int r = 0; r < NLOAD; ++r) {
         const int e = tid + r * NT;
         const int ey = e / PX, ex = e - ey * PX;
-        loff[r] = (e < PLANE) ? wrapi(y0 + ey - 2, ny) * nx + wrapi(x0 + ex - 2, nx) : 0;
+        loff[r] = (e < PLANE) ? (int)CDI_CHK(wrapi(y0 + ey - 2, ny) * nx + wrapi(x0 + ex - 2, nx), plane, a.status) : 0;
     }
     int uoff[RU], voff[RV], woff[RW];
 #pragma unroll
     for (int r = 0; r < RU; ++r) {
         const int e = tid + r * NT, ey = e / (BX + 1), ex = e - ey * (BX + 1);
-        uoff[r] = (e < NU) ? wrapi(y0 + ey, ny) * nx + wrapi(x0 - 1 + ex, nx) : 0;
+        uoff[r] = (e < NU) ? (int)CDI_CHK(wrapi(y0 + ey, ny) * nx + wrapi(x0 - 1 + ex, nx), plane, a.status) : 0;
     }
 #pragma unroll
     for (int r = 0; r < RV; ++r) {
         const int e = tid + r * NT, ey = e / BX, ex = e - ey * BX;
-        voff[r] = (e < NV) ? wrapi(y0 - 1 + ey, ny) * nx + wrapi(x0 + ex, nx) : 0;
+        voff[r] = (e < NV) ? (int)CDI_CHK(wrapi(y0 - 1 + ey, ny) * nx + wrapi(x0 + ex, nx), plane, a.status) : 0;
     }
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
         const int e = tid + r * NT, ey = e / BX, ex = e - ey * BX;
-        woff[r] = (e < NW) ? wrapi(y0 + ey, ny) * nx + wrapi(x0 + ex, nx) : 0;
+        woff[r] = (e < NW) ? (int)CDI_CHK(wrapi(y0 + ey, ny) * nx + wrapi(x0 + ex, nx), plane, a.status) : 0;
     }
     const int gx = wrapi(x0 + tx, nx), gy = wrapi(y0 + ty, ny);
     const bool own = (x0 + tx < nx) && (y0 + ty < ny);
@@ -276,7 +276,7 @@ adj_kernel(const AdjArgs<T> a)
 
         T gz_p, t_p;
         gbar_plane(k + 1, gz_p, t_p);  // buffer (k+1)&1; phase C reads buffer k&1
-        const long long zb = (long long)k * plane;
+        const long long zb = (long long)CDI_CHK(k, nz, a.status) * plane;
         const int m = k & (NSLOT_A - 1), b = k & 1, mp = (k + 1) & (NSLOT_A - 1);
         const T *vel = sv + (k & (NVS_A - 1)) * S::VPL;
         const T uc = vel[ty * (BX + 1) + tx + 1], um = vel[ty * (BX + 1) + tx];
@@ -459,22 +459,22 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
 #pragma unroll
             for (int r = 0; r < RPHI; ++r) {
                 const int e = ct + r * NC, row = e / (PP / VX), col = e - row * (PP / VX);
-                gphi[r] = wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+                gphi[r] = (int)CDI_CHK(wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx), plane - VX + 1, a.status);
             }
 #pragma unroll
             for (int r = 0; r < RU; ++r) {
                 const int e = ct + r * NC, row = e / (UP / VX), col = e - row * (UP / VX);
-                gu_[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+                gu_[r] = (int)CDI_CHK(wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx), plane - VX + 1, a.status);
             }
 #pragma unroll
             for (int r = 0; r < RV; ++r) {
                 const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
-                gv_[r] = wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+                gv_[r] = (int)CDI_CHK(wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx), plane - VX + 1, a.status);
             }
 #pragma unroll
             for (int r = 0; r < RW; ++r) {
                 const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
-                gw_[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+                gw_[r] = (int)CDI_CHK(wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx), plane - VX + 1, a.status);
             }
         }
         auto issue_pl = [&](int z, int slot) {
@@ -643,7 +643,8 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
                     tc[i] = tp[i];
                 }
                 if (writes) {
-                    const long long ko = (long long)k * plane + own_off;
+                    const long long ko = (long long)CDI_CHK(k, nz, a.status) * plane +
+                                         CDI_CHK(own_off, plane - VX + 1, a.status);
                     VV::st(a.out + ko, o);
                     if (want_vel) {
                         const T *Pk = sphi + pk * C::PHI, *Pk1 = sphi + pk1 * C::PHI;

@@ -10,6 +10,7 @@
 #include "cdi.h"
 #include "cdi_internal.cuh"
 #include "cdi_async.cuh"
+#include "cdi_nvtx.h"
 
 using cdi::LaunchCfg;
 using cdi::RedScratch;
@@ -284,14 +285,14 @@ int cdi_create_grid(cdi_grid **out, int nx, int ny, int nz, double dx, int dtype
         (e = cudaMalloc(&g->counter, sizeof(unsigned int))) != cudaSuccess ||
         (e = cudaMalloc(&g->rec, sizeof(StatsRec))) != cudaSuccess ||
         (e = cudaMalloc(&g->rec2, sizeof(StatsRec))) != cudaSuccess ||
-        (e = cudaMalloc(&g->status, sizeof(unsigned int))) != cudaSuccess) {
+        (e = cudaMalloc(&g->status, sizeof(unsigned int) * cdi::kStatusWords)) != cudaSuccess) {
         cdi_destroy_grid(g);
         return cuda_fail(e, "cudaMalloc(scratch)");
     }
     StatsRec h;
     reset_run_host(&h);
     if ((e = cudaMemset(g->counter, 0, sizeof(unsigned int))) != cudaSuccess ||
-        (e = cudaMemset(g->status, 0, sizeof(unsigned int))) != cudaSuccess ||
+        (e = cudaMemset(g->status, 0, sizeof(unsigned int) * cdi::kStatusWords)) != cudaSuccess ||
         (e = cudaMemcpy(g->rec, &h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(g->rec2, &h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess) {
         cdi_destroy_grid(g);
@@ -417,6 +418,28 @@ int cdi_max_dt(double dx, double eps, double gamma, int Df, int scheme, double *
     case CDI_RK4: *dt = 2.79 * base / 4.0; break;   // Eq. 28
     default: return fail(CDI_ERR_ARG, "unknown scheme %d", scheme);
     }
+    return CDI_OK;
+}
+
+int cdi_max_dt_mixed(double dx, double eps, double gamma, const double *umax, int Df, int scheme,
+                     double *dt)
+{
+    if (!dt || !umax) return fail(CDI_ERR_ARG, "NULL argument to cdi_max_dt_mixed");
+    double c;
+    switch (scheme) {
+    case CDI_EULER: c = 1.0; break;   // Eq. 10 at the crossover line, summed over axes
+    case CDI_RK4: c = 2.83; break;    // Eq. 32
+    default: return fail(CDI_ERR_ARG, "no mixed advective-diffusive criterion for scheme %d", scheme);
+    }
+    double dif;
+    if (int rc = cdi_max_dt(dx, eps, gamma, Df, scheme, &dif)) return rc;
+    double den = Df * gamma;
+    for (int d = 0; d < Df; ++d) {
+        if (!(umax[d] >= 0) || !isfinite(umax[d])) return fail(CDI_ERR_ARG, "umax[%d] must be finite and >= 0", d);
+        den += umax[d];
+    }
+    const double adv = c * dx / den;
+    *dt = adv < dif ? adv : dif;
     return CDI_OK;
 }
 
@@ -620,6 +643,7 @@ static int check_rk_args(cdi_grid *g, const void *a, void *b, void *w1, void *w2
 int cdi_step_rk(cdi_grid *g, const void *phi_in, void *phi_out, void *work1, void *work2, double dt,
                 double eps, double gamma, double t, double period, int scheme, int flags, void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_step_rk");
     if (g && g->sharpen == CDI_SHARPEN_FACE) return fail(CDI_ERR_ARG, "Runge-Kutta stages use the centre-product sharpening");
     if (int rc = check_rk_args(g, phi_in, phi_out, work1, work2, dt, eps, gamma, scheme, flags)) return rc;
     return rk_step_impl(g, phi_in, phi_out, work1, work2, dt, eps, gamma, t, period, scheme,
@@ -630,6 +654,7 @@ int cdi_run_rk(cdi_grid *g, void *buf_a, void *buf_b, void *work1, void *work2, 
                double dt, double eps, double gamma, double period, int scheme, int flags, int *final_in_b,
                void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_run_rk");
     if (nsteps < 0) return fail(CDI_ERR_ARG, "nsteps must be >= 0");
     if (g && g->sharpen == CDI_SHARPEN_FACE) return fail(CDI_ERR_ARG, "Runge-Kutta stages use the centre-product sharpening");
     if (int rc = check_rk_args(g, buf_a, buf_b, work1, work2, dt, eps, gamma, scheme, flags)) return rc;
@@ -649,6 +674,7 @@ int cdi_run_rk(cdi_grid *g, void *buf_a, void *buf_b, void *work1, void *work2, 
 int cdi_step(cdi_grid *g, const void *phi_in, void *phi_out, double dt, double eps, double gamma,
              double vel_scale, int flags, void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_step");
     if (int rc = check_step_args(g, phi_in, phi_out, dt, eps, gamma, vel_scale)) return rc;
     if (flags & CDI_CHECK_CONDITION)
         if (int rc = check_condition_flag(g, dt, eps, gamma, vel_scale)) return rc;
@@ -660,6 +686,7 @@ int cdi_step(cdi_grid *g, const void *phi_in, void *phi_out, double dt, double e
 int cdi_run(cdi_grid *g, void *buf_a, void *buf_b, int nsteps, double t0, double dt, double eps,
             double gamma, double period, int flags, int *final_in_b, void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_run");
     if (nsteps < 0) return fail(CDI_ERR_ARG, "nsteps must be >= 0");
     if (int rc = check_step_args(g, buf_a, buf_b, dt, eps, gamma, 1.0)) return rc;
     if (flags & CDI_CHECK_CONDITION)
@@ -680,21 +707,31 @@ int cdi_run(cdi_grid *g, void *buf_a, void *buf_b, int nsteps, double t0, double
     return CDI_OK;
 }
 
+// Read and clear the status words: CDI_ERR_TIMEOUT / CDI_ERR_BOUNDS if a kernel
+// recorded a failure since the last read, else CDI_OK.  st (4 words) is the
+// host copy, already transferred and synchronised.
+static int status_code(const cdi_grid *g, const unsigned *st, cudaStream_t s)
+{
+    if (!st[0]) return CDI_OK;
+    cudaMemsetAsync(g->status, 0, sizeof(unsigned int) * cdi::kStatusWords, s);
+    if (st[0] & 2u)
+        return fail(CDI_ERR_BOUNDS, "checked build: %u index(es) out of range, the last %u against a limit of %u",
+                    st[1], st[2], st[3]);
+    return fail(CDI_ERR_TIMEOUT, "a bounded device-side wait gave up; results are unreliable");
+}
+
 static int read_rec(const cdi_grid *g, const StatsRec *dev, cdi_stats *out, cudaStream_t s)
 {
     StatsRec h;
-    unsigned int st = 0;
+    unsigned int st[cdi::kStatusWords] = {0, 0, 0, 0};
     cudaError_t e;
     if ((e = cudaMemcpyAsync(&h, dev, sizeof(h), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(&st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "statistics readback");
     static_assert(sizeof(StatsRec) == sizeof(cdi_stats), "record layout");
     memcpy(out, &h, sizeof(h));
-    if (st) {
-        cudaMemsetAsync(g->status, 0, sizeof(unsigned int), s);
-        return fail(CDI_ERR_TIMEOUT, "a bounded device-side wait gave up; results are unreliable");
-    }
+    if (int rc = status_code(g, st, s)) return rc;
     if (!isfinite(h.sum)) return fail(CDI_ERR_NAN, "non-finite phi (sum = %g)", h.sum);
     return CDI_OK;
 }
@@ -722,6 +759,7 @@ int cdi_reset_run_stats(cdi_grid *g, void *stream)
 
 int cdi_mass_and_bounds(cdi_grid *g, const void *phi, cdi_stats *out, void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_mass_and_bounds");
     if (int rc = check_grid(g)) return rc;
     if (!phi || !out) return fail(CDI_ERR_ARG, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
@@ -814,6 +852,7 @@ static int step_host_pipelined(cdi_grid *g, const void *hin, void *hout, double 
 int cdi_step_host(cdi_grid *g, const void *phi_in_host, void *phi_out_host, double dt, double eps,
                   double gamma, double vel_scale, int flags, cdi_stats *stats_out, void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_step_host");
     if (int rc = check_grid(g)) return rc;
     if (!phi_in_host || !phi_out_host) return fail(CDI_ERR_ARG, "host pointer is NULL");
     const size_t bytes = (size_t)g->n * esize(g);
@@ -864,6 +903,7 @@ static int adjoint_t(cdi_grid *g, const void *phi, const void *lam, void *out, v
     a.c = coefs<T>(g, dt, eps, gamma, vs);
     a.c_shp_adj = (T)(gamma * dt / (2.0 * g->dx));
     a.c_vel = (T)(0.5 * vs);
+    a.status = g->status;
     if (cdi::adj_blocks(g->adj.tile, a.zchunk, g->nx, g->ny, g->nz) > g->capacity)
         return fail(CDI_ERR_STATE, "adjoint launch configuration out of range");
     cudaError_t e = cdi::launch_adj<T>(a, g->adj.tile, s);
@@ -875,6 +915,7 @@ int cdi_step_adjoint(cdi_grid *g, const void *phi_k, const void *lam_next, void 
                      void *gv, void *gw, double dt, double eps, double gamma, double vel_scale,
                      void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_step_adjoint");
     if (int rc = check_step_args(g, phi_k, lam_k, dt, eps, gamma, vel_scale)) return rc;
     if (g->sharpen == CDI_SHARPEN_FACE)
         return fail(CDI_ERR_ARG, "the adjoint is of the centre-product step (Section 2.2)");
@@ -962,9 +1003,42 @@ int cdi_probe_bounded_wait(cdi_grid *g, double limit_s, void *stream)
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cuda_fail(e, "probe status readback");
     if (!st) return CDI_OK;  // the wait did not run out: the time-out path is broken
-    cudaMemsetAsync(g->status, 0, sizeof(unsigned int), s);
+    cudaMemsetAsync(g->status, 0, sizeof(unsigned int) * cdi::kStatusWords, s);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "probe status reset");
     return fail(CDI_ERR_TIMEOUT, "bounded device wait ran out (probe)");
+}
+
+// One thread tests an index one past the limit with the checked-build test.
+__global__ void probe_bounds_kernel(unsigned int *status, long long limit)
+{
+    if (threadIdx.x == 0) {
+        const long long i = CDI_CHK(limit, limit, status);
+        (void)i;
+    }
+}
+
+int cdi_is_checked_build(void)
+{
+#ifdef CDI_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int cdi_probe_bounds_check(cdi_grid *g, void *stream)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (!cdi_is_checked_build()) return fail(CDI_ERR_STATE, "not a checked build (CDI_CHECKED)");
+    cudaStream_t s = (cudaStream_t)stream;
+    probe_bounds_kernel<<<1, 32, 0, s>>>(g->status, 12345);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "probe launch");
+    unsigned int st[cdi::kStatusWords] = {0, 0, 0, 0};
+    if ((e = cudaMemcpyAsync(st, g->status, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(e, "probe status readback");
+    return status_code(g, st, s);
 }
 
 int cdi_set_sharpening(cdi_grid *g, int mode)
@@ -1008,6 +1082,7 @@ int cdi_get_launch(const cdi_grid *g, int which, int *tile, int *nblocks, int *n
 int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps, double gamma, int reps,
                  double *best_ms, void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_autotune");
     if (int rc = check_step_args(g, phi_a, phi_b, dt, eps, gamma, 1.0)) return rc;
     if (reps < 1) return fail(CDI_ERR_ARG, "reps must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;

@@ -26,6 +26,7 @@
 #include "cdi.h"
 #include "cdi_fwd_scalar.cuh"
 #include "cdi_internal.cuh"
+#include "cdi_nvtx.h"
 #include "cdi_reduce.cuh"
 
 namespace cdi {
@@ -197,6 +198,7 @@ struct cdi_batch {
     size_t unit_cap;
     unsigned int *box_done;    // [nbox] units completed in the current launch
     StatsRec *recs;            // [nbox]
+    unsigned int *status;      // status words (checked builds record out-of-range indices)
     long long cells;
     int sms;
     cudaStream_t cap;          // capture stream for graphs
@@ -288,6 +290,7 @@ static int batch_free(cdi_batch *b)
     cudaFree(b->partials);
     cudaFree(b->box_done);
     cudaFree(b->recs);
+    cudaFree(b->status);
     delete b;
     return CDI_OK;
 }
@@ -326,6 +329,7 @@ static int build_units(cdi_batch *b, int tile, int zdepth)
         e.a.c.c_shp = (T)(0.5 * x.gamma);
         e.a.c.c_upd = (T)(x.dt / x.dx);
         e.a.c.tol = sizeof(T) == 8 ? (T)DBL_EPSILON : (T)FLT_EPSILON;
+        e.a.red.status = b->status;
         const int Df = (x.nx > 1) + (x.ny > 1) + (x.nz > 1);
         e.dV = pow(x.dx, (double)Df);
         e.tiles_x = plane ? 1 : (x.nx + bw - 1) / bw;
@@ -459,6 +463,8 @@ int cdi_batch_create(cdi_batch **out, const cdi_box_desc *boxes, int nbox, int d
         (e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
         (e = cudaMalloc(&b->box_done, sizeof(unsigned int) * nbox)) != cudaSuccess ||
         (e = cudaMalloc(&b->recs, sizeof(StatsRec) * nbox)) != cudaSuccess ||
+        (e = cudaMalloc(&b->status, sizeof(unsigned int) * cdi::kStatusWords)) != cudaSuccess ||
+        (e = cudaMemset(b->status, 0, sizeof(unsigned int) * cdi::kStatusWords)) != cudaSuccess ||
         (e = cudaMemset(b->box_done, 0, sizeof(unsigned int) * nbox)) != cudaSuccess ||
         (e = cudaMemcpy(b->recs, hrec.data(), sizeof(StatsRec) * nbox, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -487,6 +493,7 @@ int cdi_batch_info(const cdi_batch *b, int *parity, int *total_units, int *nbloc
 
 int cdi_batch_step(cdi_batch *b, double vel_scale, void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_batch_step");
     if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
     if (!isfinite(vel_scale)) return cdi::set_error(CDI_ERR_ARG, "vel_scale must be finite");
     cudaStream_t s = (cudaStream_t)stream;
@@ -497,6 +504,7 @@ int cdi_batch_step(cdi_batch *b, double vel_scale, void *stream)
 
 int cdi_batch_run(cdi_batch *b, int nsteps, void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_batch_run");
     if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
     if (nsteps < 1) return cdi::set_error(CDI_ERR_ARG, "nsteps must be >= 1");
     const std::pair<int, int> key(nsteps, b->parity);
@@ -532,9 +540,16 @@ int cdi_batch_stats(cdi_batch *b, cdi_stats *out, void *stream)
     static_assert(sizeof(StatsRec) == sizeof(cdi_stats), "record layout");
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
+    unsigned int st[cdi::kStatusWords] = {0, 0, 0, 0};
     if ((e = cudaMemcpyAsync(out, b->recs, sizeof(StatsRec) * b->nbox, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(st, b->status, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return cdi::set_error(CDI_ERR_CUDA, "batch statistics: %s", cudaGetErrorString(e));
+    if (st[0]) {
+        cudaMemsetAsync(b->status, 0, sizeof(st), s);
+        return cdi::set_error(CDI_ERR_BOUNDS, "checked build: %u index(es) out of range, the last %u against a limit of %u",
+                              st[1], st[2], st[3]);
+    }
     for (int i = 0; i < b->nbox; ++i)
         if (!isfinite(out[i].sum)) return cdi::set_error(CDI_ERR_NAN, "box %d: non-finite phi", i);
     return CDI_OK;
@@ -573,6 +588,7 @@ int cdi_batch_get_launch(const cdi_batch *b, int *tile, int *zdepth, int *nblock
 
 int cdi_batch_autotune(cdi_batch *b, int reps, float *best_ms, void *stream)
 {
+    cdi::NvtxRange nvtx_("cdi_batch_autotune");
     if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
     if (reps < 1) return cdi::set_error(CDI_ERR_ARG, "reps must be >= 1");
     cudaStream_t s = (cudaStream_t)stream;

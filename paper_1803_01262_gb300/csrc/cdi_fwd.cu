@@ -149,26 +149,30 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
         constexpr int RV = (C::CV + NC - 1) / NC, RW = (C::CW + NC - 1) / NC;
         const int ct = tid - C::NOWN;
         int gphi[RPHI], gu[RU], gv[RV], gw[RW];
+        unsigned *const st = a.red.status;
+        (void)st;
+        const long long lastv = plane - VX + 1;  // a 16-byte chunk must end inside the plane
+        (void)lastv;
         if (!is_own) {
 #pragma unroll
             for (int r = 0; r < RPHI; ++r) {
                 const int e = ct + r * NC, row = e / (PP / VX), col = e - row * (PP / VX);
-                gphi[r] = wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+                gphi[r] = (int)CDI_CHK(wrapi(y0 - 2 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx), lastv, st);
             }
 #pragma unroll
             for (int r = 0; r < RU; ++r) {
                 const int e = ct + r * NC, row = e / (UP / VX), col = e - row * (UP / VX);
-                gu[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx);
+                gu[r] = (int)CDI_CHK(wrapi(y0 + row, ny) * nx + wrapi(x0 - VX + col * VX, nx), lastv, st);
             }
 #pragma unroll
             for (int r = 0; r < RV; ++r) {
                 const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
-                gv[r] = wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+                gv[r] = (int)CDI_CHK(wrapi(y0 - 1 + row, ny) * nx + wrapi(x0 + col * VX, nx), lastv, st);
             }
 #pragma unroll
             for (int r = 0; r < RW; ++r) {
                 const int e = ct + r * NC, row = e / (W / VX), col = e - row * (W / VX);
-                gw[r] = wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx);
+                gw[r] = (int)CDI_CHK(wrapi(y0 + row, ny) * nx + wrapi(x0 + col * VX, nx), lastv, st);
             }
         }
         auto issue_phi = [&](int z, int slot) {
@@ -183,7 +187,7 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
         };
         auto issue_vel = [&](int z, int slot) {
             if (is_own) return;
-            const long long zo = (long long)z * plane;
+            const long long zo = (long long)CDI_CHK(z, nz, st) * plane;
             T *dst = svel + slot * C::VEL;
 #pragma unroll
             for (int r = 0; r < RU; ++r) {
@@ -347,7 +351,7 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
                     szc[i] = szn[i];
                 }
                 if (writes) {
-                    const long long ko = (long long)k * plane + own_off;
+                    const long long ko = (long long)CDI_CHK(k, nz, st) * plane + CDI_CHK(own_off, lastv, st);
                     if constexpr (RK) {
                         T qo[VX];
 #pragma unroll

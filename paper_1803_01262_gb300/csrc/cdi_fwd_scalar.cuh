@@ -111,12 +111,14 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
         }
     };
 
+    unsigned *const st = a.red.status;
+    (void)st;
     int loff[NLOAD];
 #pragma unroll
     for (int r = 0; r < NLOAD; ++r) {
         const int e = tid + r * NT;
         const int ey = e / PX, ex = e - ey * PX;
-        loff[r] = (e < PLANE) ? wrapi(y0 + ey - 2, ny) * nx + wrapi(x0 + ex - 2, nx) : 0;
+        loff[r] = (e < PLANE) ? (int)CDI_CHK(wrapi(y0 + ey - 2, ny) * nx + wrapi(x0 + ex - 2, nx), plane, st) : 0;
     }
     const int gx = wrapi(x0 + tx, nx), gy = wrapi(y0 + ty, ny);
     const bool own = (x0 + tx < nx) && (y0 + ty < ny);
@@ -138,17 +140,17 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
 #pragma unroll
     for (int r = 0; r < RU; ++r) {
         const int e = tid + r * NT, ey = e / (BX + 1), ex = e - ey * (BX + 1);
-        uoff[r] = (e < NU) ? wrapi(y0 + ey, ny) * nx + wrapi(x0 - 1 + ex, nx) : 0;
+        uoff[r] = (e < NU) ? (int)CDI_CHK(wrapi(y0 + ey, ny) * nx + wrapi(x0 - 1 + ex, nx), plane, st) : 0;
     }
 #pragma unroll
     for (int r = 0; r < RV; ++r) {
         const int e = tid + r * NT, ey = e / BX, ex = e - ey * BX;
-        voff[r] = (e < NV) ? wrapi(y0 - 1 + ey, ny) * nx + wrapi(x0 + ex, nx) : 0;
+        voff[r] = (e < NV) ? (int)CDI_CHK(wrapi(y0 - 1 + ey, ny) * nx + wrapi(x0 + ex, nx), plane, st) : 0;
     }
 #pragma unroll
     for (int r = 0; r < RW; ++r) {
         const int e = tid + r * NT, ey = e / BX, ex = e - ey * BX;
-        woff[r] = (e < NW) ? wrapi(y0 + ey, ny) * nx + wrapi(x0 + ex, nx) : 0;
+        woff[r] = (e < NW) ? (int)CDI_CHK(wrapi(y0 + ey, ny) * nx + wrapi(x0 + ex, nx), plane, st) : 0;
     }
     auto issue_plane = [&](int z) { issue_plane_at(z, (long long)wrapi(z, nz) * plane); };
     // Stage velocity plane z (0 <= z < nz) from plane offset zo = z * plane.
@@ -170,7 +172,7 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
             if (e < NW) cp_async<sizeof(T)>(dst + NU + NV + e, a.w + zo + woff[r]);
         }
     };
-    auto issue_vel = [&](int z) { issue_vel_at(z, (long long)z * plane); };
+    auto issue_vel = [&](int z) { issue_vel_at(z, (long long)CDI_CHK(z, nz, st) * plane); };
 
     // Commit groups: first phi planes z0-2 .. z0+1; then PF prologue groups,
     // the d-th holding phi plane z0+2+d and velocity plane z0+d; then one group
@@ -269,7 +271,7 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
         const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, Fzp - Fzm)));
         T o = fma(-c_upd, div, pc);
         if (own) {
-            const long long ko = (long long)k * plane + oc;
+            const long long ko = (long long)CDI_CHK(k, nz, st) * plane + CDI_CHK(oc, plane, st);
             if constexpr (RK) {
                 const T r = -c_upd * div;  // dt * RHS
                 const T base = a.rk_base ? rb : pc;

@@ -144,6 +144,12 @@ fwd_tma_kernel(const FwdArgs<T> a, const __grid_constant__ TmaMaps maps, const i
     }
     __syncthreads();
     int sc = 0;  // next stage id: barrier sc & 3, parity (sc >> 2) & 1
+    // Copy thread: after a bounded wait has run out it issues no further tensor
+    // copies, and before the kernel returns it waits (bounded) for every stage
+    // it issued beyond the last one it saw complete, so that no copy is still
+    // writing into this block's shared memory when the block exits.
+    bool timed_out = false;
+    int issued_hi = 0, waited_hi = 0;  // stage ids [waited_hi, issued_hi) may be in flight
 
     Acc<T> acc;
     acc.init();
@@ -161,11 +167,11 @@ fwd_tma_kernel(const FwdArgs<T> a, const __grid_constant__ TmaMaps maps, const i
         int hoff = 0, hdst = 0;
         if (!is_own && ct < 40) {
             const int r = ct >> 1, sd = ct & 1;
-            hoff = wrapi(y0 - 2 + r, ny) * nx + (sd ? xr : xl);
+            hoff = (int)CDI_CHK(wrapi(y0 - 2 + r, ny) * nx + (sd ? xr : xl), plane - VX + 1, a.red.status);
             hdst = r * 2 * VX + sd * VX;
         } else if (!is_own && ct < 56) {
             const int r = ct - 40;
-            hoff = (y0 + r) * nx + xl;
+            hoff = (int)CDI_CHK((y0 + r) * nx + xl, plane - VX + 1, a.red.status);
             hdst = r * VX;
         }
         // Issue one stage: phi planes zp0 .. zp0+np-1 into slots ps0.. (mod 5)
@@ -173,7 +179,8 @@ fwd_tma_kernel(const FwdArgs<T> a, const __grid_constant__ TmaMaps maps, const i
         auto issue_stage = [&](int zp0, int np, int ps0, int zv, int vs) {
             unsigned long long *bar = bars + (sc & 3);
             if (!is_own) fence_proxy_async();
-            if (tma_thread) {
+            if (tma_thread && !timed_out) {
+                issued_hi = sc + 1;
                 for (int d = 0; d < np; ++d) {
                     int s = ps0 + d;
                     if (s >= 5) s -= 5;
@@ -208,14 +215,15 @@ fwd_tma_kernel(const FwdArgs<T> a, const __grid_constant__ TmaMaps maps, const i
         };
         // Stage s has landed: the ring threads wait for their halo copies, one
         // thread for the tensor copies; the barrier that follows publishes both.
-        bool timed_out = false;
         auto wait_stage = [&](int id, int pending) {
             if (!is_own) {
                 if (pending) cp_async_wait<1>();
                 else cp_async_wait<0>();
             }
-            if (tma_thread && !timed_out)
+            if (tma_thread && !timed_out) {
                 timed_out = !mbar_wait_bounded(bars + (id & 3), (unsigned)((id >> 2) & 1), a.red.status);
+                if (!timed_out && id + 1 > waited_hi) waited_hi = id + 1;
+            }
         };
 
         __syncthreads();  // the previous unit's readers are done with every slot
@@ -339,6 +347,12 @@ fwd_tma_kernel(const FwdArgs<T> a, const __grid_constant__ TmaMaps maps, const i
             vk = vk == 2 ? 0 : vk + 1;
         }
         if (!is_own) cp_async_wait<0>();
+    }
+    if (tma_thread) {
+        // Stages issued at the end of the last unit and never waited for (empty
+        // stages in a normal run; after a time-out, whatever was in flight).
+        for (int id = waited_hi; id < issued_hi; ++id)
+            if (!mbar_wait_bounded(bars + (id & 3), (unsigned)((id >> 2) & 1), a.red.status)) break;
     }
     reduce_and_finish(acc.partial(), a.red);
 }

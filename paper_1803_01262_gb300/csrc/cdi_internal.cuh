@@ -32,7 +32,7 @@ struct RedScratch {
     int capacity;           // number of partial slots
     double dV;              // cell measure dx^D_f
     int update_run;         // 1: fold this result into the *_run accumulators
-    unsigned int *status;   // nullable: bit 0 set if a bounded device wait gave up
+    unsigned int *status;   // nullable: the status words (kStatusWords, below)
     int combine = 0;        // 1: add this launch's result to the record's per-step fields
                             //    (a step done in several launches over z slabs)
 };
@@ -84,6 +84,7 @@ struct AdjArgs {
     StepCoef<T> c;
     T c_shp_adj;                 // gamma dt / (2 dx)
     T c_vel;                     // vel_scale / 2 (velocity gradient factor)
+    unsigned int *status;        // nullable: status words (checked builds record here)
 };
 
 // Launch configuration of a kernel: tile shape, z chunk (adjoint), block count.
@@ -146,5 +147,34 @@ __host__ __device__ inline int wrapi(int a, int n)
     int r = a % n;
     return r < 0 ? r + n : r;
 }
+
+// Device status words of a grid or batch (4 x 32 bits, cleared when read):
+//   [0] flags: bit 0 a bounded device wait gave up; bit 1 a checked build found
+//       an index out of range;
+//   [1] number of out-of-range indices found (checked builds);
+//   [2] the last such index (low 32 bits), [3] the limit it was checked against.
+constexpr int kStatusWords = 4;
+
+// Checked builds (-DCDI_CHECKED): CDI_CHK(i, n, status) tests an index a kernel
+// derived for a global access -- an in-plane offset against the plane, a plane
+// index against the box -- and, if it lies outside [0, n), records it in the
+// status words and returns 0 so that the access stays inside the array.  In
+// other builds it is the index itself.
+#ifdef CDI_CHECKED
+__device__ __forceinline__ long long chk_index(long long i, long long n, unsigned *status)
+{
+    if (i >= 0 && i < n) return i;
+    if (status) {
+        atomicOr(status, 2u);
+        atomicAdd(status + 1, 1u);
+        atomicExch(status + 2, (unsigned)i);
+        atomicExch(status + 3, (unsigned)n);
+    }
+    return 0;
+}
+#define CDI_CHK(i, n, status) ::cdi::chk_index((i), (n), (status))
+#else
+#define CDI_CHK(i, n, status) (i)
+#endif
 
 }  // namespace cdi

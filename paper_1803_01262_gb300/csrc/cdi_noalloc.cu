@@ -13,12 +13,19 @@
 // The scratch is shared by every call: calls that overlap on the GPU (for
 // example on two streams at once) race on it and must be avoided.  Each call
 // clears the block counter before its launch, so a call never depends on
-// what an earlier call left behind.
+// what an earlier call left behind.  The host looks the array's device
+// address up once per device context (cudaGetSymbolAddress, which allocates
+// nothing) and looks it up again when the context has changed, as after a
+// cudaDeviceReset.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
+
+#include <mutex>
 
 #include "cdi.h"
 #include "cdi_internal.cuh"
@@ -36,11 +43,44 @@ struct NoAllocScratch {
 
 static __device__ __align__(256) NoAllocScratch g_scratch;
 
-// Device address of g_scratch per device, resolved once per device on the
-// first call made with that device current.
+// Device address of g_scratch and the SM count, per device, resolved on the
+// first call made with that device current.  In host code g_scratch names a
+// host-side stand-in, so the kernel is given this address instead.  Each entry
+// remembers the unique id of the context it was resolved in: after a
+// cudaDeviceReset the device gets a new context, whose module (and array) may
+// sit elsewhere, and the next call resolves the address again.  The mutex
+// keeps concurrent first calls from different host threads from seeing a
+// half-written entry.
 constexpr int kMaxDevices = 64;
-static NoAllocScratch *g_addr[kMaxDevices];
-static int g_sms[kMaxDevices];
+struct DevEntry {
+    unsigned long long ctx_id;  // 0: not resolved
+    NoAllocScratch *addr;
+    int sms;
+};
+static DevEntry g_dev[kMaxDevices];
+static std::mutex g_dev_mutex;
+
+static PFN_cuCtxGetCurrent_v4000 g_ctx_current = nullptr;
+static PFN_cuCtxGetId_v12000 g_ctx_id = nullptr;
+
+// Unique id of the calling thread's current context (0 if none or unavailable).
+static unsigned long long current_ctx_id()
+{
+    if (!g_ctx_current || !g_ctx_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return 0;
+        g_ctx_current = (PFN_cuCtxGetCurrent_v4000)f1;
+        g_ctx_id = (PFN_cuCtxGetId_v12000)f2;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 }  // namespace
 
@@ -127,26 +167,49 @@ extern "C" int cdi_step_noalloc(int nx, int ny, int nz, double dx, int dtype, co
     const char *pa = (const char *)phi_in, *pb = (const char *)phi_out;
     if (pa < pb + bytes && pb < pa + bytes) return na_fail(CDI_ERR_ARG, "phi_in and phi_out overlap");
 
+    const size_t nb_stats = sizeof(cdi_stats);
+    const char *ps = (const char *)stats_dev;
+    // phi_out, u, v, w, stats_dev: the kernel writes phi_out and the record while
+    // it reads the others, so no written buffer may overlap a read one.
+    const char *rd[] = {(const char *)phi_in, (const char *)u, (const char *)v, (const char *)w};
+    for (const char *r : rd)
+        if (r && r != pa && pb < r + bytes && r < pb + bytes)
+            return na_fail(CDI_ERR_ARG, "phi_out overlaps a velocity array");
+    for (const char *r : rd)
+        if (r && ps < r + bytes && r < ps + nb_stats)
+            return na_fail(CDI_ERR_ARG, "stats_dev overlaps phi_in or a velocity array");
+    if (ps < pb + bytes && pb < ps + nb_stats) return na_fail(CDI_ERR_ARG, "stats_dev overlaps phi_out");
+
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(CDI_ERR_CUDA, "cudaGetDevice", e);
     if (dev < 0 || dev >= kMaxDevices) return na_fail(CDI_ERR_STATE, "device ordinal out of range");
-    if (!g_addr[dev]) {
-        // First call on this device (with it current): resolve the scratch
-        // address and the SM count.  Neither allocates.
-        void *ptr = nullptr;
-        if ((e = cudaGetSymbolAddress(&ptr, g_scratch)) != cudaSuccess)
-            return na_fail(CDI_ERR_CUDA, "cudaGetSymbolAddress", e);
-        int sms = 0;
-        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
-            return na_fail(CDI_ERR_CUDA, "cudaDeviceGetAttribute", e);
-        g_sms[dev] = sms;
-        g_addr[dev] = (NoAllocScratch *)ptr;
+    DevEntry ent;
+    {
+        std::lock_guard<std::mutex> lock(g_dev_mutex);
+        unsigned long long id = current_ctx_id();
+        if (id == 0 || g_dev[dev].ctx_id != id) {
+            // First call on this device (or in a new context of it): resolve the
+            // scratch address (this also makes the device's primary context
+            // current) and the SM count.  Neither allocates.
+            void *ptr = nullptr;
+            if ((e = cudaGetSymbolAddress(&ptr, g_scratch)) != cudaSuccess)
+                return na_fail(CDI_ERR_CUDA, "cudaGetSymbolAddress", e);
+            int sms = 0;
+            if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+                return na_fail(CDI_ERR_CUDA, "cudaDeviceGetAttribute", e);
+            id = current_ctx_id();
+            if (id == 0) return na_fail(CDI_ERR_CUDA, "no current CUDA context after cudaGetSymbolAddress");
+            g_dev[dev].addr = (NoAllocScratch *)ptr;
+            g_dev[dev].sms = sms;
+            g_dev[dev].ctx_id = id;
+        }
+        ent = g_dev[dev];
     }
     cudaStream_t s = (cudaStream_t)stream;
     return dtype == CDI_F64
         ? noalloc_t<double>(nx, ny, nz, dx, phi_in, phi_out, u, v, w, dt, eps, gamma, vel_scale,
-                            stats_dev, g_addr[dev], g_sms[dev], s)
+                            stats_dev, ent.addr, ent.sms, s)
         : noalloc_t<float>(nx, ny, nz, dx, phi_in, phi_out, u, v, w, dt, eps, gamma, vel_scale,
-                           stats_dev, g_addr[dev], g_sms[dev], s);
+                           stats_dev, ent.addr, ent.sms, s);
 }

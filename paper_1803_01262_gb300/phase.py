@@ -33,7 +33,7 @@ def euler_dt(eps_over_dx: float, gamma_over_u: float, n: int = 50, L: float = 2.
     h = L / n
     eps, gamma = eps_over_dx * h, gamma_over_u
     c = math.sqrt(2.0) / 2.0
-    return min(h * h / (4.0 * gamma * eps), h / (2.0 * c + 2.0 * gamma))
+    return cdi.max_dt_mixed(h, eps, gamma, (c, c), cdi.CDI_EULER)
 
 
 def phase_boxes(points, n=50, dtype=torch.float64, device="cuda"):

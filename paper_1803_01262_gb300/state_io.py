@@ -2,15 +2,18 @@
 
 save_state / load_state: a phase field as raw little-endian values (``<name>.bin``, x
 fastest, [nz][ny][nx]) beside a JSON header (``<name>.json``: shape, dtype, step, time and
-whatever run parameters the caller passes), so that a long run can stop and resume.  The
-header is written after the data and names its byte count, so a half-written pair is
-refused on load.
+whatever run parameters the caller passes), so that a long run can stop and resume.  Both
+files are written to temporary names and renamed into place, data first; the header names
+the byte count and the SHA-256 of the data, so a truncated file, or data and header left
+from two different saves by a process that died between the two renames, is refused on
+load.
 
 RunLog: appends one JSON line per record with the step, time, mass, the mass drift against
 the first record, min, max and both violation counts, as cdi.Grid.stats() reports them.
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 
@@ -37,14 +40,20 @@ def save_state(path, phi, step: int, t: float, **params) -> None:
         raise ValueError(f"phi must be float32 or float64, got {a.dtype}")
     fbin, fjson = _paths(path)
     data = a.astype(_DTYPES[key], copy=False).tobytes()
-    with open(fbin, "wb") as f:
+    header = {"shape": list(a.shape), "dtype": key, "bytes": len(data),
+              "sha256": hashlib.sha256(data).hexdigest(), "step": int(step), "t": float(t),
+              "params": params}
+    tbin, tjson = fbin + ".tmp", fjson + ".tmp"
+    with open(tbin, "wb") as f:
         f.write(data)
-    header = {"shape": list(a.shape), "dtype": key, "bytes": len(data), "step": int(step),
-              "t": float(t), "params": params}
-    tmp = fjson + ".tmp"
-    with open(tmp, "w") as f:
+        f.flush()
+        os.fsync(f.fileno())
+    with open(tjson, "w") as f:
         json.dump(header, f, indent=1)
-    os.replace(tmp, fjson)
+        f.flush()
+        os.fsync(f.fileno())
+    os.replace(tbin, fbin)
+    os.replace(tjson, fjson)
 
 
 def load_state(path):
@@ -60,7 +69,10 @@ def load_state(path):
     want = int(np.prod(shape)) * dt.itemsize
     if os.path.getsize(fbin) != want or header.get("bytes") != want:
         raise ValueError(f"{fbin}: {os.path.getsize(fbin)} bytes on disk, header expects {want}")
-    phi = np.fromfile(fbin, dtype=dt).reshape(shape).astype(dt.newbyteorder("="), copy=False)
+    raw = open(fbin, "rb").read()
+    if hashlib.sha256(raw).hexdigest() != header.get("sha256"):
+        raise ValueError(f"{fbin}: data does not match the header's SHA-256 (a save was interrupted)")
+    phi = np.frombuffer(raw, dtype=dt).reshape(shape).astype(dt.newbyteorder("="), copy=True)
     return phi, header
 
 

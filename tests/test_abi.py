@@ -71,3 +71,35 @@ def test_product_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_max_dt_mixed_host():
+    """Below-line step: min(diffusive limit, c dx / (sum of component maxima + D_f gamma)),
+    c = 2.83 for RK4 (Eq. 32, so min(Eq. 31, Eq. 32) in 2D), c = 1 for Euler."""
+    from paper_1803_01262_gb300 import cdi
+    dx = 2.0 / 50
+    c = 2.0 ** 0.5 / 2
+    for eoh, gu in ((1.5, 0.5), (1.0, 1.0), (0.7, 0.7), (0.55, 0.3), (2.0, 3.0)):
+        eps, g = eoh * dx, gu
+        eq31 = 2.79 * dx * dx / (8 * g * eps)
+        eq32 = 2.83 * dx / (c + c + 2 * g)
+        assert cdi.max_dt_mixed(dx, eps, g, (c, c), cdi.CDI_RK4) == pytest.approx(min(eq31, eq32), rel=1e-15)
+        eul = min(dx * dx / (4 * g * eps), dx / (c + c + 2 * g))
+        assert cdi.max_dt_mixed(dx, eps, g, (c, c), cdi.CDI_EULER) == pytest.approx(eul, rel=1e-15)
+    # far below the line (eps/dx 0.55, gamma/u 0.3) the advective limit of Eq. 32 binds;
+    # at Table 2's point 7 (0.7, 0.7) Eq. 32 as printed exceeds Eq. 31, which then binds;
+    # above the line (point 1: 1.5, 0.5) Eq. 31 binds
+    assert cdi.max_dt_mixed(dx, 0.55 * dx, 0.3, (c, c), cdi.CDI_RK4) == pytest.approx(
+        2.83 * dx / (2 * c + 0.6), rel=1e-15)
+    assert cdi.max_dt_mixed(dx, 0.7 * dx, 0.7, (c, c), cdi.CDI_RK4) == pytest.approx(
+        2.79 * dx * dx / (8 * 0.7 * 0.7 * dx), rel=1e-15)
+    assert cdi.max_dt_mixed(dx, 1.5 * dx, 0.5, (c, c), cdi.CDI_RK4) == pytest.approx(
+        2.79 * dx * dx / (8 * 0.5 * 1.5 * dx), rel=1e-15)
+    # 1D: Eq. 10 at the crossover line, dx / (u + gamma)
+    assert cdi.max_dt_mixed(0.01, 0.01, 1.0, (1.0,), cdi.CDI_EULER) == pytest.approx(
+        min(0.01 * 0.01 / (2 * 0.01), 0.01 / 2.0))
+    for bad in (cdi.CDI_RK2, cdi.CDI_RK3):
+        with pytest.raises(cdi.CDIError):
+            cdi.max_dt_mixed(dx, dx, 1.0, (c, c), bad)
+    with pytest.raises(cdi.CDIError):
+        cdi.max_dt_mixed(dx, dx, 1.0, (-1.0, c), cdi.CDI_EULER)

@@ -4,6 +4,7 @@ diffusive and the mixed advective-diffusive limits."""
 import math
 
 import numpy as np
+import pytest
 import torch
 
 from paper_1803_01262_gb300 import phase as P
@@ -17,7 +18,7 @@ def test_period_and_step_rule():
         eps, gamma = eoh * h, gu
         dif = h * h / (4.0 * gamma * eps)          # A = dt gamma eps / h^2 = 1/(2 D_f), D_f = 2
         adv = h / (math.sqrt(2.0) + 2.0 * gamma)   # dx / (max u + max v + 2 gamma)
-        assert P.euler_dt(eoh, gu) == min(dif, adv)
+        assert P.euler_dt(eoh, gu) == pytest.approx(min(dif, adv), rel=1e-15)
         A = P.euler_dt(eoh, gu) * gamma * eps / h ** 2
         assert A <= 0.25 * (1 + 1e-15)
 

@@ -40,3 +40,15 @@ def test_run_log(tmp_path):
     assert [r["step"] for r in lines] == [0, 10]
     assert lines[0]["mass_drift_rel"] == 0.0 and abs(lines[1]["mass_drift_rel"] - 1e-12) < 1e-15
     assert lines[1]["n_strict"] == 3 and lines[1]["gcells"] == 1.5
+
+
+def test_state_refuses_data_from_another_save(tmp_path):
+    """A process that died between renaming the new data and the new header leaves the new
+    data under the old header, with the same byte count: the header's hash refuses it."""
+    import shutil
+    S.save_state(tmp_path / "s", np.zeros((2, 3, 4)), step=1, t=0.1)
+    shutil.copy(tmp_path / "s.json", tmp_path / "old.json")
+    S.save_state(tmp_path / "s", np.ones((2, 3, 4)), step=2, t=0.2)
+    shutil.copy(tmp_path / "old.json", tmp_path / "s.json")
+    with pytest.raises(ValueError, match="SHA-256"):
+        S.load_state(tmp_path / "s")
