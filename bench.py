@@ -374,6 +374,38 @@ def size_1024(dev, peak, nst=500, ck=32, inner=8):
     return res
 
 
+def slab_line(dev, f, dt, eps, gamma, K, W, dist, barrier, maxrank):
+    """The box split into z slabs, one per rank (one slab with its own periodic halo at
+    N = 1): every step exchanges two halo planes with each neighbour (NCCL point-to-point
+    between ranks; device copies at N = 1) and updates the rank's owned planes with
+    cdi_step_planes.  Strong scaling of the one box."""
+    import torch
+    from paper_1803_01262_gb300 import slab as S
+    ws = dist.get_world_size() if dist is not None else 1
+    rank = dist.get_rank() if dist is not None else 0
+    T = [torch.from_numpy(x).to(dev, torch.float32) for x in (f.phi, f.u, f.v, f.w)]
+    d = S.SlabDomain(rank, ws, *T, f.h)
+    del T
+    run = S.SlabRun([d], S.DistTransport() if dist is not None else S.LocalTransport())
+    for i in range(W):
+        run.step(dt, eps, gamma, 1.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record()
+    for i in range(K):
+        run.step(dt, eps, gamma, math.cos(math.pi * i * dt / 3.0))
+    e1.record()
+    barrier()
+    ms = maxrank(e0.elapsed_time(e1))
+    st = run.stats()
+    cells = f.phi.size
+    return {"workload": f"cdi_step_deformation_{f.phi.shape[0]}^3 split into {ws} z slab(s), halo 2 planes",
+            "parallelism": f"slab{ws}", "scaling": "strong", "steps": K,
+            "value": cells * K / (ms * 1e-3) / 1e9, "unit": "Gcell-updates/s", "ms_per_step": ms / K,
+            "planes_per_rank": [b - a for a, b in d.slabs], "n_tol_last_step": st["n_tol"],
+            "exchange": "NCCL send/recv" if ws > 1 else "device copies (own periodic halo)"}
+
+
 def phase_line(dev):
     """Phase diagram of the (eps/dx, gamma/|u|) plane: 16 x 16 Table 2 drop boxes (50 x 50,
     FP64) advanced by one batched launch per step for at least one advection period each."""
@@ -542,6 +574,11 @@ def main():
     e2e_val = ws * cells * Ke / te / 1e9
     del g32, vel32, a32, b32
 
+    # ---- the same box as z slabs with halo exchange (one slab per rank) ----
+    slab = None
+    if not args.no_extra:
+        slab = slab_line(dev, f, dt, eps, gamma, max(10, min(K, 400)), W, dist, barrier, maxrank)
+
     # ---- batched boxes: 64 independent periodic boxes, edges ~U{32..160} ----
     batch = None
     if not args.no_extra:
@@ -671,6 +708,7 @@ def main():
                         "adj_over_fwd": avg_adj / avg_kernel_ms,
                         "achieved_gbs": BYTES_ADJ_F32 * cells / (avg_adj * 1e-3) / 1e9},
             "batch": batch,
+            "slab": slab,
             "size_512": big,
             "inverse_512": inverse,
             "size_1024": big1024,

@@ -151,6 +151,20 @@ CDI_API int cdi_run(cdi_grid *g, void *buf_a, void *buf_b, int nsteps, double t0
             double eps, double gamma, double period, int flags, int *final_in_b,
             void *stream);
 
+/* The Euler step of cdi_step restricted to the planes z_lo <= k < z_hi
+ * (0 <= z_lo < z_hi <= nz): those planes of phi_out are written, the others
+ * are left as they are; the stencil reads planes z_lo-2 .. z_hi+1 of phi_in
+ * (periodic in nz) and the w faces below each plane.  The statistics record
+ * covers the updated planes only (mass = dV * their sum) and counts as one
+ * step of the run accumulators.  This is the kernel of a z-slab domain
+ * decomposition: a rank holds its slab with two halo planes on each side
+ * (nz = slab planes + 4), fills the halos from its neighbours, and steps
+ * planes [2, nz - 2), where no periodic wrap is taken.  Centre-product
+ * sharpening only (CDI_ERR_ARG otherwise). */
+CDI_API int cdi_step_planes(cdi_grid *g, const void *phi_in, void *phi_out, int z_lo, int z_hi,
+                            double dt, double eps, double gamma, double vel_scale, int flags,
+                            void *stream);
+
 /* One step of a Runge-Kutta scheme of Section 2.3 from phi_in (left unchanged)
  * to phi_out, with velocity cos(pi t_s/period) (u, v, w) at each stage time
  * t_s (period <= 0: 1).  scheme: CDI_EULER (= cdi_step), CDI_RK2 (explicit

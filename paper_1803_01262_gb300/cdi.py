@@ -71,6 +71,7 @@ SIGNATURES = {
     "cdi_get_umax": [_V, _P(_Dbl)],
     "cdi_step": [_V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _I, _V],
     "cdi_run": [_V, _V, _V, _I, _Dbl, _Dbl, _Dbl, _Dbl, _Dbl, _I, _P(_I), _V],
+    "cdi_step_planes": [_V, _V, _V, _I, _I, _Dbl, _Dbl, _Dbl, _Dbl, _I, _V],
     "cdi_step_stats": [_V, _P(Stats), _V],
     "cdi_reset_run_stats": [_V, _V],
     "cdi_mass_and_bounds": [_V, _V, _P(Stats), _V],
@@ -259,6 +260,15 @@ class Grid:
         _ck(lib().cdi_step(self._h, self._arr(phi_in, "phi_in"), self._arr(phi_out, "phi_out"),
                            dt, eps, gamma, vel_scale, CDI_CHECK_CONDITION if check else 0,
                            _stream(stream)))
+        return phi_out
+
+    def step_planes(self, phi_in, phi_out, z_lo, z_hi, dt, eps, gamma, vel_scale=1.0, check=False,
+                    stream=None):
+        """The Euler step on planes [z_lo, z_hi) of phi_out only (cdi_step_planes); the
+        statistics record covers those planes."""
+        _ck(lib().cdi_step_planes(self._h, self._arr(phi_in, "phi_in"), self._arr(phi_out, "phi_out"),
+                                  int(z_lo), int(z_hi), dt, eps, gamma, vel_scale,
+                                  CDI_CHECK_CONDITION if check else 0, _stream(stream)))
         return phi_out
 
     def run(self, a, b, nsteps, dt, eps, gamma, period=0.0, t0=0.0, check=False, stream=None):

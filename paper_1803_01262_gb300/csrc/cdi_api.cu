@@ -773,6 +773,33 @@ int cdi_mass_and_bounds(cdi_grid *g, const void *phi, cdi_stats *out, void *stre
     return read_rec(g, g->rec2, out, s);
 }
 
+// Launch configuration of the z-range kernels (the slabs of the pipelined host
+// step, cdi_step_planes): tile 4 where nx allows, else 0; balanced shares.
+static int ensure_slab_cfg(cdi_grid *g)
+{
+    if (g->slab.nblocks != 0) return CDI_OK;
+    const int tile = g->nx % (16 / (int)esize(g)) == 0 ? 4 : 0;
+    return fwd_cfg(g, tile, 0, CDI_NCHUNKS_BALANCED, &g->slab, false, true);
+}
+
+int cdi_step_planes(cdi_grid *g, const void *phi_in, void *phi_out, int z_lo, int z_hi, double dt,
+                    double eps, double gamma, double vel_scale, int flags, void *stream)
+{
+    cdi::NvtxRange nvtx_("cdi_step_planes");
+    if (int rc = check_step_args(g, phi_in, phi_out, dt, eps, gamma, vel_scale)) return rc;
+    if (!(0 <= z_lo && z_lo < z_hi && z_hi <= g->nz))
+        return fail(CDI_ERR_ARG, "need 0 <= z_lo < z_hi <= nz (got %d, %d, nz %d)", z_lo, z_hi, g->nz);
+    if (g->sharpen != CDI_SHARPEN_CENTRE)
+        return fail(CDI_ERR_ARG, "cdi_step_planes takes the centre-product sharpening only");
+    if (flags & CDI_CHECK_CONDITION)
+        if (int rc = check_condition_flag(g, dt, eps, gamma, vel_scale)) return rc;
+    if (int rc = ensure_slab_cfg(g)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    return g->dtype == CDI_F64
+        ? step_t<double>(g, phi_in, phi_out, dt, eps, gamma, vel_scale, s, z_lo, z_hi, 0, 1)
+        : step_t<float>(g, phi_in, phi_out, dt, eps, gamma, vel_scale, s, z_lo, z_hi, 0, 1);
+}
+
 // cdi_step_host in S = 8 equal z slabs: the two planes of the periodic seam
 // (nz-2, nz-1) are copied in first, then slab j = [b_j, b_j+1) in order on
 // hs_in; slab j is stepped on the caller's stream as soon as the piece holding
@@ -802,10 +829,7 @@ static int step_host_pipelined(cdi_grid *g, const void *hin, void *hout, double 
         if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate");  // (process-lifetime leak only)
         g->pipe_ready = true;
     }
-    if (g->slab.nblocks == 0) {  // tile 4 where nx allows, else 0; balanced shares
-        const int tile = cdi::fwd_tile_is_vec(4) && g->nx % (16 / (int)esize(g)) == 0 ? 4 : 0;
-        if (int rc = fwd_cfg(g, tile, 0, CDI_NCHUNKS_BALANCED, &g->slab, false, true)) return rc;
-    }
+    if (int rc = ensure_slab_cfg(g)) return rc;
     const int S = 8, nz = g->nz;  // nz >= 16: every slab holds the two halo planes
     int b[S + 1];
     for (int j = 0; j <= S; ++j) b[j] = (int)((long long)j * nz / S);
