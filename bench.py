@@ -408,7 +408,9 @@ def slab_line(dev, f, dt, eps, gamma, K, W, dist, barrier, maxrank):
 
 def phase_line(dev):
     """Phase diagram of the (eps/dx, gamma/|u|) plane: 16 x 16 Table 2 drop boxes (50 x 50,
-    FP64) advanced by one batched launch per step for at least one advection period each."""
+    FP64) advanced by one batched launch per step for at least one advection period each,
+    with Section 2.2's centre-product sharpening and, as a second sweep, the face-product
+    form; the bounded points of both side by side."""
     import numpy as np
     import torch
     from paper_1803_01262_gb300 import phase as P
@@ -419,14 +421,31 @@ def phase_line(dev):
     rows, info = P.phase_diagram(pts)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    return {"workload": "phase diagram: 256 periodic 50x50 drop boxes (Table 2 setup), eps/dx 0.55..2,"
-                        " gamma/|u| 0.3..3, FP64 Euler, one batched launch per step",
-            "boxes": len(rows), "cells": info["cells"], "steps": info["nsteps"],
-            "run_ms": info["run_ms"], "value": info["cells"] * info["nsteps"] / (info["run_ms"] * 1e-3) / 1e9,
-            "unit": "Gcell-updates/s", "seconds_total_incl_setup_and_autotune": el,
-            "bounded": sum(r["bounded"] for r in rows), "sufficient": sum(r["sufficient"] for r in rows),
-            "sufficient_and_unbounded": sum(r["sufficient"] and not r["bounded"] for r in rows),
-            "launch": info["launch"]}
+    out = {"workload": "phase diagram: 256 periodic 50x50 drop boxes (Table 2 setup), eps/dx 0.55..2,"
+                       " gamma/|u| 0.3..3, FP64 Euler, one batched launch per step",
+           "boxes": len(rows), "cells": info["cells"], "steps": info["nsteps"],
+           "run_ms": info["run_ms"], "value": info["cells"] * info["nsteps"] / (info["run_ms"] * 1e-3) / 1e9,
+           "unit": "Gcell-updates/s", "seconds_total_incl_setup_and_autotune": el,
+           "bounded": sum(r["bounded"] for r in rows), "sufficient": sum(r["sufficient"] for r in rows),
+           "sufficient_and_unbounded": sum(r["sufficient"] and not r["bounded"] for r in rows),
+           "launch": info["launch"]}
+    del info
+    rows_f, info_f = P.phase_diagram(pts, sharpen="face")
+    out["face_product"] = {
+        "bounded": sum(r["bounded"] for r in rows_f),
+        "sufficient_and_unbounded": sum(r["sufficient"] and not r["bounded"] for r in rows_f),
+        "bounded_centre_not_face": sum(a["bounded"] and not b["bounded"] for a, b in zip(rows, rows_f)),
+        "bounded_face_not_centre": sum(b["bounded"] and not a["bounded"] for a, b in zip(rows, rows_f)),
+        "value": info_f["cells"] * info_f["nsteps"] / (info_f["run_ms"] * 1e-3) / 1e9,
+        "launch": info_f["launch"]}
+    grid = {}
+    for a, b in zip(rows, rows_f):
+        grid.setdefault(f"{a['eps_over_dx']:.3f}", []).append(
+            ("S" if a["sufficient"] else "-") + ("C" if a["bounded"] else ".") + ("F" if b["bounded"] else "."))
+    out["grid_by_eps_over_dx"] = {k: " ".join(v) for k, v in grid.items()}
+    out["grid_legend"] = ("per eps/dx row, gamma/|u| 0.3..3 left to right: S sufficient condition holds, "
+                          "C bounded with the centre form, F bounded with the face-product form")
+    return out
 
 
 def main():
@@ -539,7 +558,8 @@ def main():
     achieved = BYTES_F32 * cells / (avg_kernel_ms * 1e-3) / 1e9
     traffic = profiled_traffic()
 
-    # ---- FP64 fused step on the same box ----
+    # ---- FP64 fused step on the same box (bound by the FP64 pipe: its roof is measured) ----
+    fp64_fma_per_s = cdi.probe_fp64_rate()
     K64 = max(10, min(K // 4, 500))
     g64, vel64, a64, b64 = setup(torch.float64)
     t64, k64 = time_steps(fwd_stepper(g64, a64, b64), K64, W)
@@ -614,7 +634,7 @@ def main():
                  "cells": binfo["cells"], "units": binfo["units"], "blocks": binfo["nblocks"],
                  "value": ws * binfo["cells"] * Kb / (tb * 1e-3) / 1e9, "unit": "Gcell-updates/s",
                  "ms_per_step": tb / Kb, "steps": Kb, "launch": "one kernel per step, CUDA graph",
-                 "tile": ["32x8", "32x16", "64x8", "32x4"][blaunch["tile"]],
+                 "tile": ["32x8", "32x16", "64x8", "32x4", "whole plane", "row bands"][blaunch["tile"]],
                  "zdepth": blaunch["zdepth"],
                  "achieved_gbs": BYTES_F32 * binfo["cells"] / (tb / Kb * 1e-3) / 1e9,
                  "n_tol_run_total": int(sum(x["n_tol_run"] for x in bst))}
@@ -703,7 +723,15 @@ def main():
                      "kernel_ms": avg64, "steps": K64,
                      "achieved_gbs": BYTES_F64 * cells / (avg64 * 1e-3) / 1e9,
                      "gflops_fp64": FLOPS_PER_CELL * cells / (avg64 * 1e-3) / 1e9,
-                     "fp32_speedup": value / v64},
+                     "fp32_speedup": value / v64,
+                     "roofline": {"bound": "fp64",
+                                  "achieved": FLOPS_PER_CELL * cells / (avg64 * 1e-3) / 1e9,
+                                  "peak": 2.0 * fp64_fma_per_s / 1e9, "unit": "GFLOP/s",
+                                  "frac": FLOPS_PER_CELL * cells / (avg64 * 1e-3) / (2.0 * fp64_fma_per_s),
+                                  "flops_per_cell": FLOPS_PER_CELL,
+                                  "peak_kind": "measured: cdi_probe_fp64_rate (independent FP64 FMA chains "
+                                               "on every SM, 2 flops each), this run",
+                                  "traffic": None}},
             "adjoint": {"kernel_ms": avg_adj, "ms_per_step": ta / Ka, "steps": Ka,
                         "adj_over_fwd": avg_adj / avg_kernel_ms,
                         "achieved_gbs": BYTES_ADJ_F32 * cells / (avg_adj * 1e-3) / 1e9},

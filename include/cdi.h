@@ -299,6 +299,14 @@ CDI_API int cdi_batch_run(cdi_batch *b, int nsteps, void *stream);
 CDI_API int cdi_batch_stats(cdi_batch *b, cdi_stats *out, void *stream);
 CDI_API int cdi_batch_reset_run_stats(cdi_batch *b, void *stream);
 
+/* Sharpening form of every box of the batch (see cdi_set_sharpening):
+ * CDI_SHARPEN_CENTRE (Section 2.2, the default) or CDI_SHARPEN_FACE, the
+ * face-product form, which runs on batch tiles 0 and 4 only (setting it
+ * selects tile 0; cdi_batch_set_launch refuses other tiles and the autotuner
+ * skips them while it is set).  Rebuilds the work list. */
+CDI_API int cdi_batch_set_sharpening(cdi_batch *b, int mode);
+CDI_API int cdi_batch_get_sharpening(const cdi_batch *b, int *mode);
+
 /* Launch configuration of the batch (a performance control, not part of the
  * paper): tile 0..3 = 32x8, 32x16, 64x8, 32x4 cells per work unit (one cell
  * per thread), zdepth = about that many planes per unit (0: whole box depth).
@@ -308,6 +316,11 @@ CDI_API int cdi_batch_reset_run_stats(cdi_batch *b, void *stream);
  * and each cell's sharpening evaluated once; the results are those of tiles
  * 0..3 bit for bit (the statistics' sums to rounding).  CDI_ERR_ARG, with the
  * launch unchanged, where it does not apply; zdepth is ignored for it.
+ * Tile 5 = bands of whole rows (up to 1024 cells per band, 256 threads, several
+ * cells per thread), for batches that hold a 3D box and whose rows are at most
+ * 1024 cells wide: each plane's band and halo rows are one contiguous run of
+ * the array, staged by 16-byte copies whatever the row alignment; the fields
+ * are those of tiles 0..3 bit for bit.  CDI_ERR_ARG where it does not apply.
  * tile = -1 / zdepth = -1 restore the defaults (32x8, CDI_BATCH_DEFAULT_ZDEPTH).
  * Rebuilds the work list (synchronises the device; drops captured graphs). */
 #define CDI_BATCH_DEFAULT_ZDEPTH 32
@@ -316,7 +329,7 @@ CDI_API int cdi_batch_get_launch(const cdi_batch *b, int *tile, int *zdepth, int
                                  int *total_units);
 
 /* Time every tile x zdepth in {8, 16, 32, 64, whole} (a batch of 2D boxes: every
- * tile once, tile 4 where it applies) with reps launches each
+ * tile once, tile 4 where it applies; tile 5 where it applies) with reps launches each
  * (after one warm-up) and keep the fastest; *best_ms (nullable) gets its time
  * per launch.  The trial launches read the current state and write the other
  * buffer only, and the statistics records are restored, so the batch's state
@@ -332,8 +345,8 @@ CDI_API int cdi_batch_autotune(cdi_batch *b, int reps, float *best_ms, void *str
  * covered by the proof, and not stationary on the scheme's discrete
  * equilibrium.  It runs on forward tile 0 with explicit Euler steps only;
  * cdi_step_rk, cdi_run_rk and cdi_step_adjoint return CDI_ERR_ARG while it is
- * set, and batches always use the centre form.  Setting a mode resets the
- * forward launch configuration to the mode's default. */
+ * set (batches choose their own form: cdi_batch_set_sharpening).  Setting a
+ * mode resets the forward launch configuration to the mode's default. */
 enum { CDI_SHARPEN_CENTRE = 0, CDI_SHARPEN_FACE = 1 };
 CDI_API int cdi_set_sharpening(cdi_grid *g, int mode);
 CDI_API int cdi_get_sharpening(const cdi_grid *g, int *mode);
@@ -362,6 +375,13 @@ CDI_API int cdi_is_checked_build(void);
  * it), CDI_OK if nothing was recorded, CDI_ERR_STATE in a regular build.
  * Synchronises the stream. */
 CDI_API int cdi_probe_bounds_check(cdi_grid *g, void *stream);
+
+/* Measured FP64 fused multiply-add rate of the current device (FMA
+ * instructions per second, each 2 flops): a kernel of independent FMA chains
+ * on every SM, best of three timed launches after a warm-up.  The roof of the
+ * FP64 step, which is bound by the FP64 pipe rather than by memory (not part
+ * of the paper).  Synchronises the stream. */
+CDI_API int cdi_probe_fp64_rate(double *fma_per_s, void *stream);
 
 /* Kernels with a tunable launch configuration. */
 enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };

@@ -83,6 +83,7 @@ SIGNATURES = {
     "cdi_set_sharpening": [_V, _I],
     "cdi_probe_bounded_wait": [_V, _Dbl, _V],
     "cdi_is_checked_build": [],
+    "cdi_probe_fp64_rate": [_P(_Dbl), _V],
     "cdi_probe_bounds_check": [_V, _V],
     "cdi_get_sharpening": [_V, _P(_I)],
     "cdi_set_launch": [_V, _I, _I, _I, _I],
@@ -97,6 +98,8 @@ SIGNATURES = {
     "cdi_batch_stats": [_V, _V, _V],
     "cdi_batch_reset_run_stats": [_V, _V],
     "cdi_batch_set_launch": [_V, _I, _I],
+    "cdi_batch_set_sharpening": [_V, _I],
+    "cdi_batch_get_sharpening": [_V, _P(_I)],
     "cdi_batch_get_launch": [_V, _P(_I), _P(_I), _P(_I), _P(_I)],
     "cdi_batch_autotune": [_V, _I, _P(ctypes.c_float), _V],
     "cdi_step_rk": [_V, _V, _V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _Dbl, _I, _I, _V],
@@ -148,6 +151,13 @@ def _dtype_code(dtype):
     if dtype == torch.float64:
         return CDI_F64
     raise ValueError("dtype must be torch.float32 or torch.float64")
+
+
+def probe_fp64_rate(stream=None):
+    """Measured FP64 FMA instructions per second of the current device."""
+    out = ctypes.c_double()
+    _ck(lib().cdi_probe_fp64_rate(ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def is_checked_build():
@@ -450,8 +460,20 @@ class Batch:
 
     def set_launch(self, tile=-1, zdepth=-1):
         """Work-unit tile (0..3: 32x8, 32x16, 64x8, 32x4; 4: one unit per whole 2D box, for
-        batches of 2D boxes whose planes fit in shared memory) and planes per unit (0: whole box)."""
+        batches of 2D boxes whose planes fit in shared memory; 5: bands of whole rows, for
+        batches with 3D boxes of nx <= 1024) and planes per unit (0: whole box)."""
         _ck(lib().cdi_batch_set_launch(self._h, tile, zdepth))
+
+    def set_sharpening(self, mode):
+        """"centre" (Section 2.2, the default) or "face" (face-product sharpening; batch tiles 0
+        and 4 only)."""
+        _ck(lib().cdi_batch_set_sharpening(self._h, SHARPEN[mode]))
+
+    def get_sharpening(self):
+        """The sharpening form of the batch: "centre" or "face"."""
+        m = ctypes.c_int()
+        _ck(lib().cdi_batch_get_sharpening(self._h, ctypes.byref(m)))
+        return {v: k for k, v in SHARPEN.items()}[m.value]
 
     def get_launch(self):
         """The batch launch configuration: tile, z depth, blocks per launch, work units."""

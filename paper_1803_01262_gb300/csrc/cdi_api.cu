@@ -1032,6 +1032,63 @@ int cdi_probe_bounded_wait(cdi_grid *g, double limit_s, void *stream)
     return fail(CDI_ERR_TIMEOUT, "bounded device wait ran out (probe)");
 }
 
+// FP64 FMA throughput: every thread runs CHAINS independent fused multiply-add
+// chains of ITERS steps (no memory traffic inside the loop); the result is
+// stored only if it is negative, which it never is, so the work is kept.
+constexpr int kFp64Chains = 8;
+__global__ void __launch_bounds__(256) fp64_rate_kernel(int iters, double *sink)
+{
+    double a[kFp64Chains];
+#pragma unroll
+    for (int c = 0; c < kFp64Chains; ++c) a[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+    const double m = 0.999999, k = 1e-7;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int c = 0; c < kFp64Chains; ++c) a[c] = fma(a[c], m, k);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int c = 0; c < kFp64Chains; ++c) t += a[c];
+    if (t < 0.0) sink[blockIdx.x] = t;
+}
+
+int cdi_probe_fp64_rate(double *fma_per_s, void *stream)
+{
+    if (!fma_per_s) return fail(CDI_ERR_ARG, "fma_per_s is NULL");
+    int dev = 0, sms = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail(e, "device query");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    cudaEvent_t e0, e1;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+    if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_fail(e, "cudaEventCreate");
+    }
+    float best = 1e30f;
+    int rc = CDI_OK;
+    for (int rep = 0; rep < 4 && rc == CDI_OK; ++rep) {  // the first launch is a warm-up
+        cudaEventRecord(e0, s);
+        fp64_rate_kernel<<<blocks, threads, 0, s>>>(iters, nullptr);
+        cudaEventRecord(e1, s);
+        if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+            rc = cuda_fail(e, "fp64 rate kernel");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    *fma_per_s = (double)blocks * threads * iters * kFp64Chains / (best * 1e-3);
+    return CDI_OK;
+}
+
 // One thread tests an index one past the limit with the checked-build test.
 __global__ void probe_bounds_kernel(unsigned int *status, long long limit)
 {

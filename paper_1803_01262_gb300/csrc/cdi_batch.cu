@@ -19,11 +19,13 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <utility>
 #include <vector>
 
 #include "cdi.h"
+#include "cdi_band.cuh"
 #include "cdi_fwd_scalar.cuh"
 #include "cdi_internal.cuh"
 #include "cdi_nvtx.h"
@@ -36,6 +38,7 @@ struct BoxDev {
     FwdArgs<T> a;     // phi = phi_a, out = phi_b; coefficients for vel_scale = 1
     double dV;        // cell measure dx^D_f
     int tiles_x, ntiles, zc, unit0, nunits;
+    int bh;           // row-band body: rows per band
 };
 
 // Whole-plane unit body: the unit is a whole 2D box (nz == 1) whose phi and
@@ -44,8 +47,9 @@ struct BoxDev {
 // found by index arithmetic, so every lane holds a cell of the box (no tile
 // overhang) and each sharpening value is evaluated once (no ring around a
 // tile).  The arithmetic is flat_unit's, expression by expression, so the
-// result is the same bit for bit.
-template <typename T, int NT>
+// result is the same bit for bit (FACE: the face-product sharpening, the s
+// arrays holding the normals).
+template <typename T, int NT, bool FACE = false>
 __device__ __forceinline__ void plane_unit(const FwdArgs<T> &a, Acc<T> &acc, unsigned char *smem_raw)
 {
     const int nx = a.nx, ny = a.ny, P = nx * ny;
@@ -77,7 +81,8 @@ __device__ __forceinline__ void plane_unit(const FwdArgs<T> &a, Acc<T> &acc, uns
         const T g1 = sp[yp] - sp[ym];
         const T g2 = T(0);
         const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, NumLim<T>::tiny())));
-        const T wgt = p * (T(1) - p) * rsqrt_t(q);
+        const T inv = rsqrt_t(q);
+        const T wgt = FACE ? inv : p * (T(1) - p) * inv;
         ssx[l] = wgt * g0;
         ssy[l] = wgt * g1;
     }
@@ -97,7 +102,16 @@ __device__ __forceinline__ void plane_unit(const FwdArgs<T> &a, Acc<T> &acc, uns
         adv = fma(vc, pc + pyp, adv);
         adv = fma(-vm, pym + pc, adv);
         const T dif = fma(T(-4), pc, (pxm + pxp) + (pym + pyp));
-        const T shp = (sxp - sxm) + (syp - sym);
+        T shp;
+        if constexpr (FACE) {
+            const T nxc = ssx[l], nyc = ssy[l];
+            const T fxp = T(0.5) * (pc + pxp), fxm = T(0.5) * (pxm + pc);
+            const T fyp = T(0.5) * (pc + pyp), fym = T(0.5) * (pym + pc);
+            shp = (fxp * (T(1) - fxp) * (nxc + sxp) - fxm * (T(1) - fxm) * (sxm + nxc)) +
+                  (fyp * (T(1) - fyp) * (nyc + syp) - fym * (T(1) - fym) * (sym + nyc));
+        } else {
+            shp = (sxp - sxm) + (syp - sym);
+        }
         const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, T(0))));  // z faces: Fzp - Fzm = 0
         const T o = fma(-c_upd, div, pc);
         a.out[l] = o;
@@ -109,11 +123,13 @@ __device__ __forceinline__ void plane_unit(const FwdArgs<T> &a, Acc<T> &acc, uns
 // (e.g. a phase-diagram sweep of 2D boxes): the single-plane unit body, which
 // stages the plane once (flat_unit).  BODY 2: every box has nz == 1 and fits
 // in shared memory: one unit per box, the whole-plane body (plane_unit).
-template <typename T, int BX, int BY, int BODY = 0>
-__global__ void __launch_bounds__(BX * BY)
+// BODY 3: bands of whole rows (band_unit, cdi_band.cuh), slots of sizes bs.
+// FACE: the face-product sharpening (bodies 0, 1 and 2).
+template <typename T, int BX, int BY, int BODY = 0, bool FACE = false>
+__global__ void __launch_bounds__(BX * BY, BODY == 3 ? 2 : 1)
 batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_box,
              const int total_units, const int parity, const T vs, Partial *partials,
-             unsigned int *box_done, StatsRec *recs)
+             unsigned int *box_done, StatsRec *recs, const BandSlots bs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int fold;
@@ -130,14 +146,21 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
         Acc<T> acc;
         acc.init();
         if constexpr (BODY == 2) {
-            plane_unit<T, BX * BY>(a, acc, smem_raw);
+            plane_unit<T, BX * BY, FACE>(a, acc, smem_raw);
+        } else if constexpr (BODY == 3) {
+            const int lu = u - boxes[bi].unit0, nb = boxes[bi].ntiles, zc = boxes[bi].zc;
+            const int chunk = lu / nb, band = lu - chunk * nb;
+            const int y0 = band * boxes[bi].bh;
+            const int hb = min(boxes[bi].bh, a.ny - y0);
+            const int z0 = chunk * zc;
+            band_unit<T>(a, y0, hb, z0, min(a.nz, z0 + zc), bs, acc, smem_raw);
         } else {
             const int lu = u - boxes[bi].unit0;
             const Unit un = unit_of(lu, boxes[bi].ntiles, boxes[bi].tiles_x, BX, BY, boxes[bi].zc, a.nz);
             if constexpr (BODY == 1)
-                flat_unit<T, BX, BY>(a, un, acc, smem_raw);
+                flat_unit<T, BX, BY, FACE>(a, un, acc, smem_raw);
             else
-                scalar_unit<T, BX, BY>(a, un, acc, smem_raw);
+                scalar_unit<T, BX, BY, false, SCALAR_PF, FACE>(a, un, acc, smem_raw);
         }
         const Partial p = block_reduce(acc.partial());
         if (tid == 0) {
@@ -175,14 +198,17 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
 }
 
 // Batch tiles 0..3: the scalar tiles of the single-box kernel; tile 4: one
-// unit per whole 2D box (plane_unit, PLANE_NT threads).
-constexpr int BATCH_TILES = 5;
+// unit per whole 2D box (plane_unit, PLANE_NT threads); tile 5: bands of whole
+// rows (band_unit, BAND_NT threads).
+constexpr int BATCH_TILES = 6;
 constexpr int BATCH_TILE_PLANE = 4;
+constexpr int BATCH_TILE_BAND = 5;
 constexpr int PLANE_NT = 256;
 static const int batch_tile_dims[4][2] = {{32, 8}, {32, 16}, {64, 8}, {32, 4}};
 
 }  // namespace cdi
 
+using cdi::BandSlots;
 using cdi::BoxDev;
 using cdi::StatsRec;
 
@@ -191,6 +217,9 @@ struct cdi_batch {
     int tile, zdepth;          // launch configuration: batch tile, planes per unit (0: whole box)
     bool flat;                 // every box has nz == 1: the single-plane kernel
     size_t plane_bytes;        // shared memory of the whole-plane body: 3 nx ny values of the largest box
+    int sharpen;               // CDI_SHARPEN_CENTRE or CDI_SHARPEN_FACE (tiles 0 and 4 only)
+    BandSlots band;            // row-band body: slot sizes for the largest box
+    size_t band_bytes;         // its shared memory (0: the band body does not apply)
     std::vector<cdi_box_desc> desc;
     void *boxes_dev;           // BoxDev<T>[nbox]
     int *unit_box;             // [unit_cap]
@@ -205,14 +234,14 @@ struct cdi_batch {
     std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (nsteps, parity) -> exec
 };
 
-template <typename T, int BX, int BY, int BODY>
+template <typename T, int BX, int BY, int BODY, bool FACE = false>
 static cudaError_t batch_occ_one(int *resident, size_t smem)
 {
-    cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, BX, BY, BODY>,
+    cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, BX, BY, BODY, FACE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, BX, BY, BODY>, BX * BY,
-                                                         smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, BX, BY, BODY, FACE>,
+                                                         BX * BY, smem);
 }
 
 template <typename T, int BODY>
@@ -242,9 +271,45 @@ static size_t plane_limit()
     return ((size_t)optin - fa.sharedSizeBytes) & ~(size_t)15;
 }
 
+// Largest dynamic shared memory the band kernel can launch with.
+template <typename T>
+static size_t band_limit()
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, cdi::batch_kernel<T, cdi::BAND_NT, 1, 3>) != cudaSuccess ||
+        (size_t)optin <= fa.sharedSizeBytes)
+        return 0;
+    return ((size_t)optin - fa.sharedSizeBytes) & ~(size_t)15;
+}
+
 template <typename T>
 static cudaError_t batch_occ(const cdi_batch *b, int tile, int *resident)
 {
+    if (b->sharpen == CDI_SHARPEN_FACE) {  // face-product sharpening: tiles 0 and 4
+        if (tile == 0)
+            return b->flat ? batch_occ_one<T, 32, 8, 1, true>(resident, cdi::FwdSmem<T, 32, 8>::bytes)
+                           : batch_occ_one<T, 32, 8, 0, true>(resident, cdi::FwdSmem<T, 32, 8>::bytes);
+        if (tile != cdi::BATCH_TILE_PLANE) return cudaErrorInvalidValue;
+        const size_t lim = plane_limit<T>();
+        if (lim == 0 || b->plane_bytes > lim) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2, true>,
+                                                             cdi::PLANE_NT, b->plane_bytes);
+    }
+    if (tile == cdi::BATCH_TILE_BAND) {
+        const size_t lim = band_limit<T>();
+        if (lim == 0 || b->band_bytes == 0 || b->band_bytes > lim) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, cdi::BAND_NT, 1, 3>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, cdi::BAND_NT, 1, 3>,
+                                                             cdi::BAND_NT, b->band_bytes);
+    }
     if (tile == cdi::BATCH_TILE_PLANE) {
         // The attribute belongs to the kernel, shared by every batch: it is set
         // to the largest size any batch launches with, the occupancy taken at
@@ -280,6 +345,44 @@ static size_t plane_bytes(const cdi_batch *b)
     return b->dtype == CDI_F64 ? plane_bytes_t<double>(b) : plane_bytes_t<float>(b);
 }
 
+// Slot sizes of the row-band body for this batch (the largest region of each kind
+// over its boxes) and their shared memory; 0 bytes if the band body does not apply:
+// a batch of 2D boxes only (which has its own bodies), a row wider than a band, or
+// slots beyond the shared memory of one block.
+template <typename T>
+static size_t band_bytes_t(cdi_batch *b)
+{
+    if (b->flat) return 0;
+    const int vx = 16 / (int)sizeof(T);
+    int phi = 0, ur = 0, vr = 0, sx = 0, sy = 0;
+    for (const cdi_box_desc &x : b->desc) {
+        if (x.nx > cdi::BAND_CELLS) return 0;
+        const int hb = cdi::band_rows(x.nx, x.ny);
+        phi = std::max(phi, cdi::round_up((hb + 4) * x.nx + vx, vx));
+        ur = std::max(ur, cdi::round_up(hb * x.nx + vx, vx));
+        vr = std::max(vr, cdi::round_up((hb + 1) * x.nx + vx, vx));
+        sx = std::max(sx, cdi::round_up(hb * x.nx, vx));
+        sy = std::max(sy, cdi::round_up((hb + 2) * x.nx, vx));
+    }
+    BandSlots s;
+    s.phi = phi;
+    s.uo = 0;
+    s.vo = ur;
+    s.wo = ur + vr;
+    s.vel = 2 * ur + vr;
+    s.sx = sx;
+    s.sy = sy;
+    const size_t need = cdi::band_smem_bytes(s, sizeof(T));
+    if (need > band_limit<T>()) return 0;
+    b->band = s;
+    return need;
+}
+
+static size_t band_bytes(cdi_batch *b)
+{
+    return b->dtype == CDI_F64 ? band_bytes_t<double>(b) : band_bytes_t<float>(b);
+}
+
 static int batch_free(cdi_batch *b)
 {
     if (!b) return CDI_OK;
@@ -306,10 +409,14 @@ static void drop_graphs(cdi_batch *b)
 template <typename T>
 static int build_units(cdi_batch *b, int tile, int zdepth)
 {
-    const bool plane = tile == cdi::BATCH_TILE_PLANE;
+    const bool plane = tile == cdi::BATCH_TILE_PLANE, band = tile == cdi::BATCH_TILE_BAND;
     if (plane && b->plane_bytes == 0)
         return cdi::set_error(CDI_ERR_ARG, "batch tile 4 needs 2D boxes (nz = 1) whose planes fit in shared memory");
-    const int bw = plane ? 1 : cdi::batch_tile_dims[tile][0], bh = plane ? 1 : cdi::batch_tile_dims[tile][1];
+    if (band && b->band_bytes == 0)
+        return cdi::set_error(CDI_ERR_ARG, "batch tile 5 needs a batch with 3D boxes whose rows fit in a band "
+                                           "(nx <= %d) and whose band slots fit in shared memory", cdi::BAND_CELLS);
+    const int bw = plane || band ? 1 : cdi::batch_tile_dims[tile][0];
+    const int bh = plane || band ? 1 : cdi::batch_tile_dims[tile][1];
     std::vector<BoxDev<T>> tab;
     std::vector<int> ub;
     int unit = 0;
@@ -332,8 +439,12 @@ static int build_units(cdi_batch *b, int tile, int zdepth)
         e.a.red.status = b->status;
         const int Df = (x.nx > 1) + (x.ny > 1) + (x.nz > 1);
         e.dV = pow(x.dx, (double)Df);
-        e.tiles_x = plane ? 1 : (x.nx + bw - 1) / bw;
+        e.tiles_x = plane || band ? 1 : (x.nx + bw - 1) / bw;
         e.ntiles = plane ? 1 : e.tiles_x * ((x.ny + bh - 1) / bh);  // whole-plane body: one unit per box
+        if (band) {  // bands of whole rows
+            e.bh = cdi::band_rows(x.nx, x.ny);
+            e.ntiles = (x.ny + e.bh - 1) / e.bh;
+        }
         int nch = zdepth > 0 && !plane ? (x.nz + zdepth / 2) / zdepth : 1;  // about zdepth planes per unit
         if (nch < 1) nch = 1;
         e.zc = (x.nz + nch - 1) / nch;
@@ -387,22 +498,47 @@ static int rebuild(cdi_batch *b, int tile, int zdepth)
 template <typename T, int BX, int BY>
 static void batch_launch_one(cdi_batch *b, int parity, double vs, cudaStream_t s)
 {
+    if (BX == 32 && BY == 8 && b->sharpen == CDI_SHARPEN_FACE) {
+        if (b->flat)
+            cdi::batch_kernel<T, 32, 8, 1, true><<<b->nblocks, dim3(32, 8), cdi::FwdSmem<T, 32, 8>::bytes, s>>>(
+                (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
+                b->box_done, b->recs, b->band);
+        else
+            cdi::batch_kernel<T, 32, 8, 0, true><<<b->nblocks, dim3(32, 8), cdi::FwdSmem<T, 32, 8>::bytes, s>>>(
+                (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
+                b->box_done, b->recs, b->band);
+        return;
+    }
     if (b->flat)
         cdi::batch_kernel<T, BX, BY, 1><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
             (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-            b->box_done, b->recs);
+            b->box_done, b->recs, b->band);
     else
         cdi::batch_kernel<T, BX, BY, 0><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
             (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-            b->box_done, b->recs);
+            b->box_done, b->recs, b->band);
 }
 
 template <typename T>
 static void batch_launch_plane(cdi_batch *b, int parity, double vs, cudaStream_t s)
 {
+    if (b->sharpen == CDI_SHARPEN_FACE) {
+        cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2, true><<<b->nblocks, dim3(cdi::PLANE_NT, 1), b->plane_bytes, s>>>(
+            (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
+            b->recs, b->band);
+        return;
+    }
     cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2><<<b->nblocks, dim3(cdi::PLANE_NT, 1), b->plane_bytes, s>>>(
         (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-        b->recs);
+        b->recs, b->band);
+}
+
+template <typename T>
+static void batch_launch_band(cdi_batch *b, int parity, double vs, cudaStream_t s)
+{
+    cdi::batch_kernel<T, cdi::BAND_NT, 1, 3><<<b->nblocks, dim3(cdi::BAND_NT, 1), b->band_bytes, s>>>(
+        (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
+        b->recs, b->band);
 }
 
 template <typename T>
@@ -414,6 +550,7 @@ static int batch_launch(cdi_batch *b, int parity, double vs, cudaStream_t s)
     case 2: batch_launch_one<T, 64, 8>(b, parity, vs, s); break;
     case 3: batch_launch_one<T, 32, 4>(b, parity, vs, s); break;
     case cdi::BATCH_TILE_PLANE: batch_launch_plane<T>(b, parity, vs, s); break;
+    case cdi::BATCH_TILE_BAND: batch_launch_band<T>(b, parity, vs, s); break;
     default: return cdi::set_error(CDI_ERR_STATE, "bad batch tile");
     }
     cudaError_t e = cudaGetLastError();
@@ -455,6 +592,7 @@ int cdi_batch_create(cdi_batch **out, const cdi_box_desc *boxes, int nbox, int d
     b->flat = true;
     for (int i = 0; i < nbox; ++i) b->flat = b->flat && boxes[i].nz == 1;
     b->plane_bytes = plane_bytes(b);
+    b->band_bytes = band_bytes(b);
     cudaError_t e;
     int dev = 0;
     std::vector<StatsRec> hrec(nbox);
@@ -573,7 +711,30 @@ int cdi_batch_set_launch(cdi_batch *b, int tile, int zdepth)
     if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
     if (tile < -1 || tile >= cdi::BATCH_TILES) return cdi::set_error(CDI_ERR_ARG, "batch tile %d out of range", tile);
     if (zdepth < -1) return cdi::set_error(CDI_ERR_ARG, "zdepth must be >= -1");
+    if (b->sharpen == CDI_SHARPEN_FACE && tile != 0 && tile != cdi::BATCH_TILE_PLANE && tile != -1)
+        return cdi::set_error(CDI_ERR_ARG, "face-product sharpening runs on batch tiles 0 and 4 only");
     return rebuild(b, tile < 0 ? 0 : tile, zdepth < 0 ? CDI_BATCH_DEFAULT_ZDEPTH : zdepth);
+}
+
+int cdi_batch_set_sharpening(cdi_batch *b, int mode)
+{
+    if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
+    if (mode != CDI_SHARPEN_CENTRE && mode != CDI_SHARPEN_FACE)
+        return cdi::set_error(CDI_ERR_ARG, "sharpening mode %d", mode);
+    const int old = b->sharpen;
+    b->sharpen = mode;
+    if (int rc = rebuild(b, 0, b->zdepth)) {
+        b->sharpen = old;
+        return rc;
+    }
+    return CDI_OK;
+}
+
+int cdi_batch_get_sharpening(const cdi_batch *b, int *mode)
+{
+    if (!b || !mode) return cdi::set_error(CDI_ERR_ARG, "NULL argument");
+    *mode = b->sharpen;
+    return CDI_OK;
 }
 
 int cdi_batch_get_launch(const cdi_batch *b, int *tile, int *zdepth, int *nblocks, int *total_units)
@@ -614,6 +775,8 @@ int cdi_batch_autotune(cdi_batch *b, int reps, float *best_ms, void *stream)
     float best_t = 1e30f;
     for (int tile = 0; tile < cdi::BATCH_TILES && rc == CDI_OK; ++tile) {
         if (tile == cdi::BATCH_TILE_PLANE && b->plane_bytes == 0) continue;
+        if (tile == cdi::BATCH_TILE_BAND && b->band_bytes == 0) continue;
+        if (b->sharpen == CDI_SHARPEN_FACE && tile != 0 && tile != cdi::BATCH_TILE_PLANE) continue;
         for (int zi = 0; zi < nz_opts && rc == CDI_OK; ++zi) {
             if ((rc = rebuild(b, tile, zopts[zi])) != CDI_OK) break;
             if ((rc = launch_any(b, b->parity, 1.0, s)) != CDI_OK) break;  // warm-up

@@ -294,8 +294,9 @@ __device__ __forceinline__ void scalar_unit(const FwdArgs<T> &a, const Unit &un,
 // velocities are staged once and the sharpening is evaluated once, where the
 // 3D body stages five copies of the plane and evaluates three planes of
 // sharpening.  The arithmetic of the remaining terms is the 3D body's
-// expression by expression, so the result is the same bit for bit.
-template <typename T, int BX, int BY>
+// expression by expression, so the result is the same bit for bit.  FACE: the
+// face-product sharpening (the s arrays then hold the normals), as in scalar_unit.
+template <typename T, int BX, int BY, bool FACE = false>
 __device__ __forceinline__ void flat_unit(const FwdArgs<T> &a, const Unit &un, Acc<T> &acc,
                                           unsigned char *smem_raw)
 {
@@ -338,7 +339,8 @@ __device__ __forceinline__ void flat_unit(const FwdArgs<T> &a, const Unit &un, A
         const T g1 = sp[0][Y + 1][X] - sp[0][Y - 1][X];
         const T g2 = T(0);
         const T q = fma(g2, g2, fma(g1, g1, fma(g0, g0, NumLim<T>::tiny())));
-        const T wgt = p * (T(1) - p) * rsqrt_t(q);
+        const T inv = rsqrt_t(q);
+        const T wgt = FACE ? inv : p * (T(1) - p) * inv;
         s0 = wgt * g0;
         s1 = wgt * g1;
     };
@@ -374,7 +376,16 @@ __device__ __forceinline__ void flat_unit(const FwdArgs<T> &a, const Unit &un, A
         adv = fma(vc, pc + pyp, adv);
         adv = fma(-vm, pym + pc, adv);
         const T dif = fma(T(-4), pc, (pxm + pxp) + (pym + pyp));
-        const T shp = (sxp - sxm) + (syp - sym);
+        T shp;
+        if constexpr (FACE) {
+            const T nxc = sx[0][ty][tx + 1], nyc = sy[0][ty + 1][tx];
+            const T fxp = T(0.5) * (pc + pxp), fxm = T(0.5) * (pxm + pc);
+            const T fyp = T(0.5) * (pc + pyp), fym = T(0.5) * (pym + pc);
+            shp = (fxp * (T(1) - fxp) * (nxc + sxp) - fxm * (T(1) - fxm) * (sxm + nxc)) +
+                  (fyp * (T(1) - fyp) * (nyc + syp) - fym * (T(1) - fym) * (sym + nyc));
+        } else {
+            shp = (sxp - sxm) + (syp - sym);
+        }
         const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, T(0))));  // z faces: Fzp - Fzm = 0
         const T o = fma(-c_upd, div, pc);
         a.out[wrapi(y0 + ty, ny) * nx + wrapi(x0 + tx, nx)] = o;

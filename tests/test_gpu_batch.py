@@ -69,7 +69,7 @@ def test_batch_graph_run_equals_steps():
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("tile", [0, 1, 2, 3])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 5])
 @pytest.mark.parametrize("zdepth", [0, 5, 32])
 def test_batch_every_launch_configuration(dtype, tile, zdepth):
     """Each work-unit tile and z depth gives the oracle's steps (ragged tiles and chunks)."""
@@ -102,7 +102,7 @@ def test_batch_autotune_keeps_state_and_records():
     ms = b.autotune(reps=1)
     assert ms > 0
     cfg = b.get_launch()
-    assert 0 <= cfg["tile"] < 4 and cfg["units"] > 0
+    assert cfg["tile"] in (0, 1, 2, 3, 5) and cfg["units"] > 0
     assert b.info()["parity"] == 1
     for i in range(len(boxes)):
         assert torch.equal(b.current(i), state[i])
@@ -241,3 +241,72 @@ def test_whole_plane_batches_of_different_sizes():
             f = x["fields"]
             ref = oracle.run(f.phi, f.u, f.v, f.w, f.h, x["dt"], x["eps"], x["gamma"], 2)
             assert np.abs(bt.current(i).cpu().numpy() - ref).max() <= 1e-12, i
+
+
+def odd_boxes(dtype, shapes, seed):
+    """3D (and 2D) boxes of the given (nz, ny, nx) shapes with random smooth fields."""
+    boxes = []
+    for i, shape in enumerate(shapes):
+        h = 1.0 / max(shape)
+        phi = I.random_phi(shape, seed + i, smooth=True)
+        u, v, w = I.random_velocity(shape, h, 8, 3, seed + 70 + i)
+        eps, gamma = 1.2 * h, 1.0
+        Df = sum(1 for q in shape if q > 1)
+        dt = 0.8 * h * h / (2 * max(Df, 1) * gamma * eps)
+        f = I.Fields(phi, u, v, w, h, I.face_umax(u, v, w))
+        boxes.append(dict(dx=h, dt=dt, eps=eps, gamma=gamma, u=dev(u, dtype), v=dev(v, dtype),
+                          w=dev(w, dtype), phi_a=dev(phi, dtype),
+                          phi_b=torch.empty(shape, dtype=dtype, device="cuda"), fields=f))
+    return boxes
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("zdepth", [0, 3, 16])
+def test_band_tile_bit_for_bit(dtype, zdepth):
+    """Batch tile 5 (bands of whole rows, 16-byte staging at any row alignment) gives the
+    one-cell-per-thread tiles' fields bit for bit and the oracle's steps: rows of one cell,
+    one row, rows wider than a band of several rows (one row per band), bands that wrap in y
+    several times, a 2D box among 3D ones, stepped one launch at a time and as a graph run."""
+    shapes = [(5, 7, 9), (9, 17, 33), (4, 1, 45), (6, 3, 1), (3, 2, 2), (7, 40, 150), (2, 5, 400),
+              (1, 23, 50), (11, 19, 70), (8, 64, 16), (3, 1, 1)]
+    boxes = odd_boxes(dtype, shapes, 31)
+    twins = [dict(x, phi_a=x["phi_a"].clone(), phi_b=torch.empty_like(x["phi_b"])) for x in boxes]
+    bb, bt = cdi.Batch(boxes), cdi.Batch(twins)
+    bb.set_launch(5, zdepth)
+    bt.set_launch(0, zdepth)
+    assert bb.get_launch()["tile"] == 5
+    for i in range(3):
+        bb.step(0.9)
+        bt.step(0.9)
+    sb, st = bb.stats(), bt.stats()
+    t = np.float64 if dtype == torch.float64 else np.float32
+    tol = 1e-12 if dtype == torch.float64 else 3e-6
+    for i, x in enumerate(boxes):
+        ours = bb.current(i)
+        assert torch.equal(ours, bt.current(i)), (i, shapes[i])
+        same_stats(sb[i], st[i], dtype)
+        f = x["fields"]
+        rin = [np.asarray(a, t).astype(np.float64) for a in (f.phi, f.u, f.v, f.w)]
+        ref = rin[0]
+        for _ in range(3):
+            ref = oracle.step(ref, *rin[1:], f.h, x["dt"], x["eps"], x["gamma"], 0.9)
+        assert np.abs(ours.double().cpu().numpy() - ref).max() <= tol, (i, shapes[i])
+    bb.run(4)
+    bt.run(4)
+    for i, (a, b) in enumerate(zip(bb.stats(), bt.stats())):
+        assert torch.equal(bb.current(i), bt.current(i)), i
+        same_stats(a, b, dtype)
+
+
+def test_band_tile_refusals():
+    """Tile 5 is refused for a batch of 2D boxes only and for rows wider than a band (the
+    launch stays as it was)."""
+    flat = cdi.Batch(flat_boxes(torch.float32, [(7, 9), (16, 64)], 3))
+    with pytest.raises(cdi.CDIError):
+        flat.set_launch(5, 0)
+    assert flat.get_launch()["tile"] == 0
+    wide = cdi.Batch(odd_boxes(torch.float32, [(3, 4, 1100)], 5))
+    with pytest.raises(cdi.CDIError):
+        wide.set_launch(5, 0)
+    wide.autotune(reps=1)
+    assert wide.get_launch()["tile"] != 5

@@ -70,3 +70,41 @@ def test_fp32_sweep_matches_fp64_classification_above_the_line():
     pts = [(float(a), float(b)) for a in np.linspace(0.6, 2.0, 6) for b in np.linspace(0.5, 3.0, 6)]
     rows, _ = P.phase_diagram(pts, dtype=torch.float32)
     assert all(r["bounded"] for r in rows if r["sufficient"])
+
+
+def test_face_product_sweep_matches_the_oracle():
+    """The face-product sharpening in the batched sweep: a few points on and around the
+    crossover line replayed by the oracle's face-product step give the same classification
+    over 300 steps, and the same fields to 1e-10 over the first 30; the whole-plane tile and
+    tile 0 give the same fields bit for bit.  (Each step agrees with the oracle to 1e-12,
+    tests/test_gpu_face.py; over hundreds of steps the bulk, where the unit normal follows
+    rounding-level gradients and the face form's sharpening does not vanish with them,
+    amplifies rounding differences of the two evaluation orders to ~1e-6.)"""
+    pts = [(1.5, 0.5), (1.0, 1.0), (0.9, 0.9), (0.7, 0.7), (2.0, 3.0)]
+    rows, info = P.phase_diagram(pts, nsteps=300, autotune=False, sharpen="face")
+    assert info["batch"].get_sharpening() == "face"
+    tol = np.finfo(np.float64).eps
+    for i, (r, (e, g)) in enumerate(zip(rows, pts)):
+        f, _ = I.drop_2d_uniform(e)
+        p, bad = f.phi, 0
+        for _ in range(300):
+            p = oracle.step(p, f.u, f.v, f.w, f.h, r["dt"], e * f.h, g, sharpen="face")
+            bad += int(((p < -tol) | (p > 1 + tol)).sum())
+        assert (bad == 0) == r["bounded"], (e, g, bad, r["n_tol_run"])
+    # the first 30 steps field by field; tile 0 and the whole-plane tile bit for bit
+    from paper_1803_01262_gb300 import cdi
+    boxes = P.phase_boxes(pts)
+    twins = [dict(x, phi_a=x["phi_a"].clone(), phi_b=torch.empty_like(x["phi_b"])) for x in boxes]
+    b0, b4 = cdi.Batch(boxes), cdi.Batch(twins)
+    for b, tile in ((b0, 0), (b4, 4)):
+        b.set_sharpening("face")
+        b.set_launch(tile, 0)
+        b.run(30)
+    for i, (e, g) in enumerate(pts):
+        assert torch.equal(b0.current(i), b4.current(i)), i
+        f, _ = I.drop_2d_uniform(e)
+        x = boxes[i]
+        ref = oracle.run(f.phi, f.u, f.v, f.w, f.h, x["dt"], x["eps"], x["gamma"], 30, sharpen="face")
+        assert np.abs(b0.current(i).cpu().numpy() - ref).max() <= 1e-10, (e, g)
+    with pytest.raises(cdi.CDIError):
+        b0.set_launch(1, 0)   # the face form runs on tiles 0 and 4 only
