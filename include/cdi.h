@@ -407,10 +407,26 @@ CDI_API int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, 
 /* Current launch configuration (any pointer may be NULL). */
 CDI_API int cdi_get_launch(const cdi_grid *g, int which, int *tile, int *nblocks, int *nchunks);
 
+/* Steps per pass of cdi_run (not part of the paper: temporal blocking, a
+ * performance control).  depth 1: one launch per step.  depth 2: two Euler
+ * steps per launch -- each block evaluates the first step on its tile grown
+ * by the second step's two-cell halo, keeps those phi values in shared
+ * memory, and evaluates the second step from them, so phi is read and written
+ * and the face velocities read once per two steps; each step's statistics are
+ * still reduced, the record holds the last step's and the run accumulators
+ * count both.  The results are those of depth 1 on forward tile 4 bit for
+ * bit.  Needs nx % (16/sizeof(element)) == 0 and the centre-product
+ * sharpening (CDI_ERR_ARG otherwise); an odd step count ends with one single
+ * step.  nchunks: the work split as in cdi_set_launch. */
+CDI_API int cdi_set_run_depth(cdi_grid *g, int depth, int nchunks);
+CDI_API int cdi_get_run_depth(const cdi_grid *g, int *depth, int *nblocks, int *nchunks);
+
 /* Time every forward launch configuration on phi_a/phi_b (device, contents
  * overwritten) with CUDA events on the stream (one warm-up + reps launches
- * each), keep the fastest, and return its mean time in *best_ms (may be
- * NULL).  Synchronises the stream. */
+ * each) and keep the fastest for cdi_step; then time the two-steps-per-pass
+ * kernel (where it applies) and set the run depth of cdi_run to 2 if it is
+ * faster per step than that, else to 1.  *best_ms (may be NULL) gets the time
+ * per step of what cdi_run will use.  Synchronises the stream. */
 CDI_API int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps,
                          double gamma, int reps, double *best_ms, void *stream);
 

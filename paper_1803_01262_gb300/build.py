@@ -24,11 +24,12 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libcdi.so")
 LIB_CHECKED = os.path.join(OUT_DIR, "libcdi_checked.so")
-SOURCES = ["cdi_fwd.cu", "cdi_fwd_tma.cu", "cdi_adj.cu", "cdi_batch.cu", "cdi_api.cu", "cdi_noalloc.cu"]
+SOURCES = ["cdi_fwd.cu", "cdi_fwd_tma.cu", "cdi_fwd_tb.cu", "cdi_adj.cu", "cdi_batch.cu", "cdi_api.cu",
+           "cdi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # The forward step flushes FP32 denormals (values below 1.2e-38) to zero; this
 # removes denormal handling around rsqrtf and is far below every tolerance.
-PER_FILE = {"cdi_fwd.cu": ["-ftz=true"], "cdi_fwd_tma.cu": ["-ftz=true"]}
+PER_FILE = {"cdi_fwd.cu": ["-ftz=true"], "cdi_fwd_tma.cu": ["-ftz=true"], "cdi_fwd_tb.cu": ["-ftz=true"]}
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", INCLUDE, "-I", CSRC]
 

@@ -87,6 +87,8 @@ SIGNATURES = {
     "cdi_probe_bounds_check": [_V, _V],
     "cdi_get_sharpening": [_V, _P(_I)],
     "cdi_set_launch": [_V, _I, _I, _I, _I],
+    "cdi_set_run_depth": [_V, _I, _I],
+    "cdi_get_run_depth": [_V, _P(_I), _P(_I), _P(_I)],
     "cdi_get_launch": [_V, _I, _P(_I), _P(_I), _P(_I)],
     "cdi_autotune": [_V, _V, _V, _Dbl, _Dbl, _Dbl, _I, _P(_Dbl), _V],
     "cdi_step_noalloc": [_I, _I, _I, _Dbl, _I, _V, _V, _V, _V, _V, _Dbl, _Dbl, _Dbl, _Dbl, _V, _V],
@@ -368,6 +370,16 @@ class Grid:
         t, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _ck(lib().cdi_get_launch(self._h, which, ctypes.byref(t), ctypes.byref(b), ctypes.byref(c)))
         return dict(tile=t.value, nblocks=b.value, nchunks=c.value)
+
+    def set_run_depth(self, depth, nchunks=0):
+        """Steps per pass of run(): 1, or 2 (two Euler steps per launch, temporal blocking)."""
+        _ck(lib().cdi_set_run_depth(self._h, int(depth), int(nchunks)))
+
+    def get_run_depth(self):
+        """The run depth and the two-steps-per-pass launch: depth, blocks, z chunks."""
+        d, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _ck(lib().cdi_get_run_depth(self._h, ctypes.byref(d), ctypes.byref(b), ctypes.byref(c)))
+        return dict(depth=d.value, nblocks=b.value, nchunks=c.value)
 
     def autotune(self, a, b, dt, eps, gamma, reps=5, stream=None):
         """Time all forward configurations on scratch buffers a, b; keep the fastest."""

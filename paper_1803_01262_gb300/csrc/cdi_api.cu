@@ -69,6 +69,8 @@ struct cdi_grid {
     LaunchCfg fwd, adj;
     LaunchCfg rk;  // Runge-Kutta stage kernels (set on first use; nblocks 0 = unset)
     LaunchCfg slab;  // z slabs of the pipelined host step (set on first use; nblocks 0 = unset)
+    LaunchCfg tb;    // two steps per pass (cdi_run with depth 2; nblocks 0 = unset)
+    int run_depth;   // steps per pass of cdi_run: 1, or 2 (temporal blocking)
     int sharpen;   // CDI_SHARPEN_CENTRE (Section 2.2) or CDI_SHARPEN_FACE
     // staging for cdi_step_host (owned, allocated on first use), and the copy
     // streams and events of its slab pipeline (created on first use)
@@ -269,6 +271,7 @@ int cdi_create_grid(cdi_grid **out, int nx, int ny, int nz, double dx, int dtype
     g->nx = nx; g->ny = ny; g->nz = nz; g->dx = dx; g->dtype = dtype;
     g->Df = (nx > 1) + (ny > 1) + (nz > 1);
     g->n = (long long)nx * ny * nz;
+    g->run_depth = 1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { delete g; return cuda_fail(e, "cudaGetDevice"); }
@@ -534,6 +537,88 @@ static int step_t(cdi_grid *g, const void *in, void *out, double dt, double eps,
     return CDI_OK;
 }
 
+// Launch configuration of the two-steps-per-pass kernel: one block per SM (or as
+// many as fit), tiles of W x 16 cells, the work split as for the forward kernel
+// (nchunks >= 1 z chunks, CDI_NCHUNKS_BALANCED equal shares, 0 the cost model with
+// the kernel's longer prologue: five planes of the first step per unit).
+static int tb_cfg(const cdi_grid *g, int nchunks, LaunchCfg *c)
+{
+    const int es = (int)esize(g);
+    if (g->nx % (16 / es) != 0) return fail(CDI_ERR_ARG, "two steps per pass need nx %% %d == 0", 16 / es);
+    if (g->sharpen != CDI_SHARPEN_CENTRE)
+        return fail(CDI_ERR_ARG, "two steps per pass take the centre-product sharpening only");
+    int resident = 0;
+    cudaError_t e = g->dtype == CDI_F64 ? cdi::tb2_occupancy<double>(&resident) : cdi::tb2_occupancy<float>(&resident);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query (two steps per pass)");
+    if (resident < 1) return fail(CDI_ERR_CUDA, "the two-steps-per-pass kernel does not fit on an SM");
+    const long long G = (long long)resident * g->sm_count;
+    int bw, bh;
+    cdi::tb2_tile_dims(es, &bw, &bh);
+    const long long tiles = (long long)((g->nx + bw - 1) / bw) * ((g->ny + bh - 1) / bh);
+    const int nz = g->nz;
+    if (nchunks < 0 && nchunks != CDI_NCHUNKS_BALANCED) return fail(CDI_ERR_ARG, "nchunks %d", nchunks);
+    if (nchunks == 0) {
+        double best = 1e300;
+        for (int nc = 1; nc <= nz; ++nc) {
+            const int zc = (nz + nc - 1) / nc;
+            if (nc > 1 && zc == (nz + nc - 2) / (nc - 1)) continue;
+            const long long units = tiles * ((nz + zc - 1) / zc);
+            const double rounds = (double)((units + G - 1) / G);
+            const double cost = fmax(rounds * (zc + 6.0), (double)units * (zc + 5.0) / (double)G);
+            if (cost < best * (1.0 - 1e-9)) {
+                best = cost;
+                nchunks = nc;
+            }
+        }
+        const long long P = (tiles * nz + G - 1) / G;
+        const double bal = (double)P + 6.0 * (double)((P + nz - 1) / nz + 1);
+        if (bal < best * (1.0 - 1e-9) && tiles * nz < (1LL << 31)) nchunks = CDI_NCHUNKS_BALANCED;
+    }
+    long long nb;
+    if (nchunks == CDI_NCHUNKS_BALANCED) {
+        const long long T = tiles * nz;
+        if (T >= (1LL << 31)) return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
+        nb = G < T ? G : T;
+    } else {
+        if (nchunks > nz) nchunks = nz;
+        const int zc = (nz + nchunks - 1) / nchunks;
+        const long long units = tiles * ((nz + zc - 1) / zc);
+        nb = G < units ? G : units;
+    }
+    if (2 * nb > g->capacity) nb = g->capacity / 2;  // two partial slots per block
+    c->tile = 0;
+    c->zchunk = 0;
+    c->nblocks = (int)nb;
+    c->nchunks = nchunks;
+    return CDI_OK;
+}
+
+// Two Euler steps in one pass: vel_scale vs1 for the first, vs2 for the second.
+template <typename T>
+static int step2_t(cdi_grid *g, const void *in, void *out, double dt, double eps, double gamma, double vs1,
+                   double vs2, cudaStream_t s)
+{
+    if (g->tb.nblocks == 0)
+        if (int rc = tb_cfg(g, 0, &g->tb)) return rc;
+    cdi::FwdArgs<T> a;
+    a.phi = (const T *)in;
+    a.out = (T *)out;
+    a.u = (const T *)g->u;
+    a.v = (const T *)(g->v ? g->v : g->u);
+    a.w = (const T *)(g->w ? g->w : g->u);
+    a.nx = g->nx; a.ny = g->ny; a.nz = g->nz;
+    a.c = coefs<T>(g, dt, eps, gamma, vs1);
+    a.red = scratch(g, g->rec, 1);
+    a.rk_base = nullptr;
+    a.rk_q = nullptr;
+    a.rk_qout = nullptr;
+    a.rk_alpha = a.rk_delta = a.rk_mu = a.rk_beta = T(0);
+    if (2 * g->tb.nblocks > g->capacity) return fail(CDI_ERR_STATE, "launch configuration exceeds the reduction scratch");
+    cudaError_t e = cdi::launch_fwd_tb2<T>(a, (T)(0.5 * vs2), g->tb.nblocks, g->tb.nchunks, s);
+    if (e != cudaSuccess) return cuda_fail(e, "two-steps-per-pass launch");
+    return CDI_OK;
+}
+
 // One Runge-Kutta stage: evaluates r = dt * RHS(in) and writes
 //   out = (base ? base : in) + alpha r + (q ? delta q : 0),  qout = mu (q ? q : in) + beta r.
 // Uses the RK variant of the configured tile's kernel family (vector 16x16, or
@@ -693,11 +778,21 @@ int cdi_run(cdi_grid *g, void *buf_a, void *buf_b, int nsteps, double t0, double
         if (int rc = check_condition_flag(g, dt, eps, gamma, 1.0)) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     void *src = buf_a, *dst = buf_b;
-    for (int i = 0; i < nsteps; ++i) {
+    const bool two = g->run_depth == 2 && g->sharpen == CDI_SHARPEN_CENTRE;
+    for (int i = 0; i < nsteps;) {
         const double t = t0 + i * dt;
         const double vs = period > 0 ? cos(M_PI * t / period) : 1.0;
-        int rc = g->dtype == CDI_F64 ? step_t<double>(g, src, dst, dt, eps, gamma, vs, s)
+        int rc;
+        if (two && i + 1 < nsteps) {  // steps i and i+1 in one pass
+            const double vs2 = period > 0 ? cos(M_PI * (t0 + (i + 1) * dt) / period) : 1.0;
+            rc = g->dtype == CDI_F64 ? step2_t<double>(g, src, dst, dt, eps, gamma, vs, vs2, s)
+                                     : step2_t<float>(g, src, dst, dt, eps, gamma, vs, vs2, s);
+            i += 2;
+        } else {
+            rc = g->dtype == CDI_F64 ? step_t<double>(g, src, dst, dt, eps, gamma, vs, s)
                                      : step_t<float>(g, src, dst, dt, eps, gamma, vs, s);
+            i += 1;
+        }
         if (rc) return rc;
         void *tmp = src;
         src = dst;
@@ -1135,6 +1230,7 @@ int cdi_set_sharpening(cdi_grid *g, int mode)
     }
     g->fwd = c;
     g->rk.nblocks = 0;
+    if (mode != CDI_SHARPEN_CENTRE) g->run_depth = 1;  // two steps per pass: centre form only
     return CDI_OK;
 }
 
@@ -1143,6 +1239,28 @@ int cdi_get_sharpening(const cdi_grid *g, int *mode)
     if (int rc = check_grid(g)) return rc;
     if (!mode) return fail(CDI_ERR_ARG, "mode is NULL");
     *mode = g->sharpen;
+    return CDI_OK;
+}
+
+int cdi_set_run_depth(cdi_grid *g, int depth, int nchunks)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (depth != 1 && depth != 2) return fail(CDI_ERR_ARG, "run depth must be 1 or 2 (got %d)", depth);
+    if (depth == 2) {
+        LaunchCfg c;
+        if (int rc = tb_cfg(g, nchunks, &c)) return rc;
+        g->tb = c;
+    }
+    g->run_depth = depth;
+    return CDI_OK;
+}
+
+int cdi_get_run_depth(const cdi_grid *g, int *depth, int *nblocks, int *nchunks)
+{
+    if (int rc = check_grid(g)) return rc;
+    if (depth) *depth = g->run_depth;
+    if (nblocks) *nblocks = g->tb.nblocks;
+    if (nchunks) *nchunks = g->tb.nchunks;
     return CDI_OK;
 }
 
@@ -1210,10 +1328,46 @@ int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps, d
             }
         }
     }
+    // Depth of cdi_run: two steps per pass where that kernel applies and is faster
+    // per step than the best single-step configuration.
+    float best2 = 1e30f;
+    LaunchCfg best_tb = g->tb;
+    const bool tb_ok = rc == CDI_OK && g->sharpen == CDI_SHARPEN_CENTRE && g->nx % (16 / (int)esize(g)) == 0;
+    const int tb_opts[] = {CDI_NCHUNKS_BALANCED, 0, 1, 2, 4, 8};
+    for (int oi = 0; tb_ok && rc == CDI_OK && oi < (int)(sizeof(tb_opts) / sizeof(int)); ++oi) {
+        if (tb_opts[oi] > g->nz) continue;
+        LaunchCfg c;
+        if (tb_cfg(g, tb_opts[oi], &c) != CDI_OK) continue;
+        g->tb = c;
+        void *src = phi_a, *dst = phi_b;
+        for (int i = 0; i <= reps && rc == CDI_OK; ++i) {  // warm-up pass, then reps passes
+            if (i == 1 && (e = cudaEventRecord(e0, s)) != cudaSuccess) rc = cuda_fail(e, "event");
+            if (rc == CDI_OK)
+                rc = g->dtype == CDI_F64 ? step2_t<double>(g, src, dst, dt, eps, gamma, 1.0, 1.0, s)
+                                         : step2_t<float>(g, src, dst, dt, eps, gamma, 1.0, 1.0, s);
+            void *t = src; src = dst; dst = t;
+        }
+        if (rc != CDI_OK) break;
+        if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
+            rc = cuda_fail(e, "event");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 2 * reps;  // per step
+        if (ms < best2) {
+            best2 = ms;
+            best_tb = c;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     g->fwd = rc == CDI_OK ? best : saved;
     g->rk.nblocks = 0;
-    if (rc == CDI_OK && best_ms) *best_ms = best_t;
+    if (rc == CDI_OK) {
+        g->tb = best_tb;
+        g->run_depth = best2 < best_t ? 2 : 1;
+        if (best_ms) *best_ms = best2 < best_t ? best2 : best_t;
+    }
     return rc;
 }

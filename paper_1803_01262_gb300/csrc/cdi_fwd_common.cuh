@@ -16,10 +16,14 @@ template <> struct NumLim<double> {
     __device__ __forceinline__ static double tiny() { return 2.2250738585072014e-308; }  // DBL_MIN
 };
 
+// Face flux F = cadv_u (pl + pr) - cdif (pr - pl) + cshp (sl + sr).  The order of
+// evaluation is fixed by explicit fused multiply-adds rather than left to the
+// compiler's choice of which product to fuse, which could differ between the
+// kernels that share this expression.
 template <typename T>
 __device__ __forceinline__ T flux(T cadv_u, T cdif, T cshp, T pl, T pr, T sl, T sr)
 {
-    return cadv_u * (pl + pr) - cdif * (pr - pl) + cshp * (sl + sr);
+    return fma(cshp, sl + sr, fma(cadv_u, pl + pr, -(cdif * (pr - pl))));
 }
 
 // 16-byte vector of T.

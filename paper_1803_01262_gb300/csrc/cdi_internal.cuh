@@ -104,6 +104,15 @@ long long fwd_tiles_xy(int tile, int esize, int nx, int ny);
 template <typename T>
 cudaError_t fwd_occupancy(int tile, bool rk, int *resident, bool face = false, bool slab = false);
 
+// Two steps per pass (cdi_fwd_tb.cu): W x 16 tiles (W = 16 * 16/sizeof(T)), one
+// block per SM; needs nx % (16/sizeof(T)) == 0.  c_adv2: the advective
+// coefficient of the second step (a.c.c_adv that of the first).
+template <typename T>
+cudaError_t tb2_occupancy(int *resident);
+template <typename T>
+cudaError_t launch_fwd_tb2(const FwdArgs<T> &a, T c_adv2, int nblocks, int nchunks, cudaStream_t s);
+void tb2_tile_dims(int esize, int *bw, int *bh);
+
 // Tile 6: tensor-memory-accelerator staging (cdi_fwd_tma.cu); needs
 // nx % W == 0 and ny % 16 == 0 with W = 16 * 16 / sizeof(T).
 bool tma_eligible(int esize, int nx, int ny, int nz);

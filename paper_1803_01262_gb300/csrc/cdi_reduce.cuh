@@ -296,4 +296,54 @@ __device__ __forceinline__ void reduce_and_finish(Partial p, const RedScratch &r
     }
 }
 
+// Two steps' partials of one launch (a temporally blocked pass): each is
+// block-reduced and stored (step 1 in slots [0, nb), step 2 in [nb, 2 nb)); the
+// last block to finish combines both in index order, writes the second step's
+// statistics to red.rec and folds both steps into the run accumulators.
+__device__ __forceinline__ void reduce_and_finish2(Partial p1, Partial p2, const RedScratch &red)
+{
+    __shared__ int is_last2;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    const Partial q1 = block_reduce(p1);
+    const Partial q2 = block_reduce(p2);
+    if (tid == 0) {
+        red.partials[bid] = q1;
+        red.partials[nb + bid] = q2;
+        __threadfence();
+        const unsigned prev = atomicAdd(red.counter, 1u);
+        is_last2 = (prev == (unsigned)(nb - 1));
+    }
+    __syncthreads();
+    if (!is_last2) return;
+    __threadfence();
+    Partial a1 = pidentity(), a2 = pidentity();
+    for (int i = tid; i < nb; i += nthr) {
+        a1 = pcombine(a1, load_partial_cg(red.partials + i));
+        a2 = pcombine(a2, load_partial_cg(red.partials + nb + i));
+    }
+    a1 = block_reduce(a1);
+    a2 = block_reduce(a2);
+    if (tid == 0) {
+        StatsRec *r = red.rec;
+        r->sum = a2.sum;
+        r->mn = a2.mn;
+        r->mx = a2.mx;
+        r->ns = a2.ns;
+        r->nt = a2.nt;
+        r->mass = red.dV * a2.sum;
+        if (red.update_run) {
+            r->mn_run = fmin(r->mn_run, fmin(a1.mn, a2.mn));
+            r->mx_run = fmax(r->mx_run, fmax(a1.mx, a2.mx));
+            r->ns_run += a1.ns + a2.ns;
+            r->nt_run += a1.nt + a2.nt;
+            r->steps_run += 2;
+        }
+        __threadfence();
+        *red.counter = 0u;
+    }
+}
+
 }  // namespace cdi
