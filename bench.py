@@ -665,7 +665,29 @@ def main():
         big = {"workload": "cdi_step_deformation_512^3", "value": ws * 512 ** 3 * Kbig / (tbig * 1e-3) / 1e9,
                "unit": "Gcell-updates/s", "kernel_ms": avg_big, "steps": Kbig,
                "achieved_gbs": BYTES_F32 * 512 ** 3 / (avg_big * 1e-3) / 1e9,
-               "frac": BYTES_F32 * 512 ** 3 / (avg_big * 1e-3) / 1e9 / peak}
+               "frac": BYTES_F32 * 512 ** 3 / (avg_big * 1e-3) / 1e9 / peak,
+               "run_depth_autotuned": gb.get_run_depth()["depth"]}
+        # temporal blocking: cdi_run at depth 1 and at depth 2 (two steps per launch, which
+        # reads phi, u, v, w and writes phi once per two steps: 20 B per launch and cell)
+        depth_cmp = {}
+        for depth in (1, 2):
+            gb.set_run_depth(depth, 0)
+            gb.run(ab, bb, 4, dtb, 1.0 / 512, gb.U, period=T)
+            barrier()
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            Kd = max(4, min(K, 200)) // 2 * 2
+            r0.record()
+            gb.run(ab, bb, Kd, dtb, 1.0 / 512, gb.U, period=T)
+            r1.record()
+            barrier()
+            msd = maxrank(r0.elapsed_time(r1)) / Kd
+            launch_ms = msd * depth
+            depth_cmp[f"depth{depth}"] = {
+                "ms_per_step": msd, "value": ws * 512 ** 3 / (msd * 1e-3) / 1e9, "steps": Kd,
+                "bytes_per_cell_step_algorithmic": BYTES_F32 / depth,
+                "achieved_gbs": BYTES_F32 * 512 ** 3 / (launch_ms * 1e-3) / 1e9,
+                "frac": BYTES_F32 * 512 ** 3 / (launch_ms * 1e-3) / 1e9 / peak}
+        big["temporal_blocking"] = depth_cmp
         del gb, vb, ab, bb, buf
 
     # ---- inverse problem through the adjoint, 512^3 ----

@@ -443,6 +443,7 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
         return p * (T(1) - p) * inv * fma(sb0, floor_part(inv), n1 * x2_ - n2 * x1_);
     };
 
+    bool dep_waited = false;  // the previous grid on the stream has completed
     UnitIter<W, H> units(ntiles, nz, nchunks);
     Unit un;
     while (units.next(un, ntiles, tiles_x, nz, nchunks)) {
@@ -513,11 +514,11 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
         };
 
         // Ring slot of plane z: (z - z0 + 2) mod 5; velocity slot: (z - z0) mod 3.
+        // The face velocities are staged (and w below plane z0 loaded) before
+        // waiting for the previous grid on the stream; phi, lam' and the
+        // accumulated velocity gradients, which it may write, only after.
         __syncthreads();  // the previous unit's readers are done with every slot
-        for (int d = 0; d < 5; ++d) issue_pl(z0 - 2 + d, d);  // planes z0-2 .. z0+2
         issue_vel(z0, 0);
-        cp_async_commit();
-
         const int own_x = x0 + tx * VX, own_y = y0 + ty;
         const bool writes = is_own && own_x < nx && own_y < ny;
         const long long own_off = (long long)wrapi(own_y, ny) * nx + wrapi(own_x, nx);
@@ -527,6 +528,12 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
 #pragma unroll
             for (int i = 0; i < VX; ++i) wlo[i] = __ldg(src + i);
         }
+        if (!dep_waited) {
+            grid_dep_wait();
+            dep_waited = true;
+        }
+        for (int d = 0; d < 5; ++d) issue_pl(z0 - 2 + d, d);  // planes z0-2 .. z0+2
+        cp_async_commit();
         cp_async_wait<0>();
         __syncthreads();
 
@@ -674,6 +681,8 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
         }
         cp_async_wait<0>();
     }
+    if (!dep_waited) grid_dep_wait();
+    grid_dep_launch();
 }
 
 // Adjoint tiles: 0..2 one cell per thread (32x8, 32x16, 32x4 cells, one block per tile
@@ -737,8 +746,19 @@ static cudaError_t launch_adj_vec(const AdjArgs<T> &a, cudaStream_t s)
     }
     long long nb = (long long)resident * sms;
     if (nb > units) nb = units;
-    adj_vec_kernel<T, 16, 8><<<(int)nb, C::NT, C::bytes, s>>>(a, nchunks);
-    return cudaGetLastError();
+    // programmatic stream serialisation: the launch may overlap the previous grid's
+    // end (the kernel waits for it before touching anything it may write)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nb);
+    cfg.blockDim = dim3(C::NT);
+    cfg.dynamicSmemBytes = C::bytes;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, adj_vec_kernel<T, 16, 8>, a, nchunks);
 }
 
 template <typename T, int BX, int BY>

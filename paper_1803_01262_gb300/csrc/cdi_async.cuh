@@ -105,4 +105,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsig
     return false;
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may start while the previous grid on the stream is finishing;
+// grid_dep_wait() returns once that grid has completed and its memory
+// operations are visible (at once if there is none), so only work that reads
+// nothing the previous grid writes may come before it.  grid_dep_launch() lets
+// the next such grid start: called by every block after its last access that a
+// dependent could disturb.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 }  // namespace cdi

@@ -134,6 +134,7 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
 
     Acc<T> acc;
     acc.init();
+    bool dep_waited = false;  // the previous grid on the stream has completed
 
     // planes [z_lo, z_hi) with ZR, else all of them
     const int zlo = ZR ? a.z_lo : 0, zr = ZR ? a.z_hi - a.z_lo : nz;
@@ -208,10 +209,11 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
 
         // phi slot of plane z: (z - z0 + 2) mod 5; velocity slot: (z - z0) mod 3.
         __syncthreads();  // the previous unit's readers are done with every slot
-        for (int d = 0; d < 5; ++d) issue_phi(z0 - 2 + d, d);  // planes z0-2 .. z0+2
+        // The face velocities are never written by a step: staged (and the w below
+        // plane z0 loaded) before waiting for the previous grid on the stream,
+        // whose outputs -- phi, the Runge-Kutta operands, the reduction scratch --
+        // are touched only after it.
         issue_vel(z0, 0);
-        cp_async_commit();
-
         const int own_x = x0 + tx * VX, own_y = y0 + ty;
         const bool writes = is_own && own_x < nx && own_y < ny;
         const long long own_off = (long long)wrapi(own_y, ny) * nx + wrapi(own_x, nx);
@@ -222,6 +224,12 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
 #pragma unroll
             for (int i = 0; i < VX; ++i) wlo[i] = __ldg(src + i);
         }
+        if (!dep_waited) {
+            grid_dep_wait();
+            dep_waited = true;
+        }
+        for (int d = 0; d < 5; ++d) issue_phi(z0 - 2 + d, d);  // planes z0-2 .. z0+2
+        cp_async_commit();
         cp_async_wait<0>();
         __syncthreads();
 
@@ -373,6 +381,8 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
         }
         cp_async_wait<0>();
     }
+    if (!dep_waited) grid_dep_wait();
+    grid_dep_launch();  // the next step may start staging its velocities
     reduce_and_finish<ZR>(acc.partial(), a.red);
 }
 
@@ -480,6 +490,25 @@ cudaError_t fwd_occupancy(int tile, bool rk, int *resident, bool face, bool slab
 template cudaError_t fwd_occupancy<float>(int, bool, int *, bool, bool);
 template cudaError_t fwd_occupancy<double>(int, bool, int *, bool, bool);
 
+// Launch with programmatic stream serialisation: the kernel may start while
+// the previous grid on the stream finishes (it waits in grid_dep_wait before
+// touching anything that grid may write).
+template <typename K, typename... Args>
+static cudaError_t launch_dependent(K kernel, int nblocks, int threads, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename T>
 cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, bool rk, cudaStream_t s,
                        bool face)
@@ -517,11 +546,11 @@ cudaError_t launch_fwd(const FwdArgs<T> &a, int tile, int nblocks, int nchunks, 
     case 2: fwd_kernel<T, 64, 8, false><<<nblocks, dim3(64, 8), FwdSmem<T, 64, 8>::bytes, s>>>(a, nchunks); break;
     case 3: fwd_kernel<T, 32, 4, false><<<nblocks, dim3(32, 4), FwdSmem<T, 32, 4>::bytes, s>>>(a, nchunks); break;
     case 4:
-        fwd_vec_kernel<T, 16, 16, false><<<nblocks, VecCfg<T, 16, 16>::NT, VecCfg<T, 16, 16>::bytes, s>>>(a, nchunks);
-        break;
+        return launch_dependent(fwd_vec_kernel<T, 16, 16, false>, nblocks, VecCfg<T, 16, 16>::NT,
+                                VecCfg<T, 16, 16>::bytes, s, a, nchunks);
     case 5:
-        fwd_vec_kernel<T, 16, 8, false><<<nblocks, VecCfg<T, 16, 8>::NT, VecCfg<T, 16, 8>::bytes, s>>>(a, nchunks);
-        break;
+        return launch_dependent(fwd_vec_kernel<T, 16, 8, false>, nblocks, VecCfg<T, 16, 8>::NT,
+                                VecCfg<T, 16, 8>::bytes, s, a, nchunks);
     case 6: return launch_fwd_tma<T>(a, nblocks, nchunks, s);
     default: return cudaErrorInvalidValue;
     }
