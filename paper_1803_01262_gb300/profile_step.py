@@ -7,7 +7,8 @@ configuration set explicitly so that a profiler capture is deterministic:
 
     python -m paper_1803_01262_gb300.profile_step --n 256 --dtype f32 --tile 4 --nchunks 9 --steps 3
 
-``--kernel batch`` runs the 64-box batch workload of the benchmark instead
+``--depth 2`` runs the forward steps as ``cdi_run`` at run depth 2 (two steps per launch,
+``--nchunks`` its work split).  ``--kernel batch`` runs the 64-box batch workload of the benchmark instead
 (edges U{32..160}, seed 0), with ``--tile`` / ``--zdepth`` as its work-unit
 tile and planes per unit (``--tile -1``: the autotuner's choice);
 ``--kernel phase`` the benchmark's phase-diagram sweep (256 FP64 boxes of
@@ -34,6 +35,7 @@ def main():
     ap.add_argument("--tile", type=int, default=-1)
     ap.add_argument("--nchunks", type=int, default=0)
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--depth", type=int, default=1, help="forward: steps per launch (cdi_run)")
     args = ap.parse_args()
     dtype = torch.float32 if args.dtype == "f32" else torch.float64
     if args.kernel == "batch":
@@ -51,6 +53,12 @@ def main():
     b = torch.empty_like(a)
     dt, eps, gamma = 0.1 * f.h / f.U, f.h, f.U
     lam = torch.ones_like(a) if args.kernel == "adjoint" else None
+    if args.kernel == "forward" and args.depth == 2:
+        g.set_run_depth(2, args.nchunks)
+        g.run(a, b, 2 * args.steps, dt, eps, gamma, period=3.0)
+        torch.cuda.synchronize()
+        print("run depth", g.get_run_depth())
+        return
     for i in range(args.steps):
         vs = math.cos(math.pi * i * dt / 3.0)
         if args.kernel == "forward":

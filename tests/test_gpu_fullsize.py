@@ -120,7 +120,10 @@ def test_batch_64_boxes_full_workload():
     for i, x in enumerate(boxes):
         cur = b.current(i)
         assert st[i]["steps_run"] == nsteps and st[i]["n_tol_run"] == 0
-        assert abs(st[i]["sum"] - cur.double().sum().item()) <= 1e-9 * abs(st[i]["sum"])
+        # the fused sum: compensated FP32 per thread, FP64 across threads (a few units of
+        # FP32 rounding in the worst case, ~1e-9 typically; the tile decides how many cells
+        # each thread's compensated partial holds)
+        assert abs(st[i]["sum"] - cur.double().sum().item()) <= 1e-7 * abs(st[i]["sum"])
     order = sorted(range(len(boxes)), key=lambda i: boxes[i]["fields"].phi.size)[:3]
     for i in order:
         x = boxes[i]
