@@ -316,10 +316,20 @@ __device__ __forceinline__ void band_unit(const FwdArgs<T> &a, int y0, int hb, i
         if (k + 2 < z1) issue_vel(k + 2, vkm);
         cp_async_commit();
 
-        // sharpening at plane k+1 (buffer (k+1)&1; the fluxes below read buffer k&1)
-        const T *Pk = phi_ptr(pk, zk), *Pk1 = phi_ptr(pk1, zk1);
-        T szn[CPT];
-        sharp_plane(k + 1, Pk1, Pk, phi_ptr(pk2, zk2), szn);
+        // sharpening at plane k+1 (buffer (k+1)&1; the fluxes below read buffer k&1):
+        // the ring rows first, then cell by cell together with the cell's update at
+        // plane k, so that the chains of a thread's cells overlap
+        const T *Pk = phi_ptr(pk, zk), *Pk1 = phi_ptr(pk1, zk1), *Pk2 = phi_ptr(pk2, zk2);
+        T *const sxw = ssx + ((k + 1) & 1) * S.sx;
+        T *const syw = ssy + ((k + 1) & 1) * S.sy;
+        for (int l = tid; l < 2 * nx; l += NT) {  // ring rows -1 and hb: s_y only
+            const int top = l >= nx;
+            const int x = l - top * nx;
+            const int yl = top ? hb : -1;
+            T s0, s1, s2;
+            sharp(Pk1, Pk, Pk2, (yl + 2) * nx + x, x == 0 ? nx - 1 : -1, x == nx - 1 ? 1 - nx : 1, s0, s1, s2);
+            syw[(yl + 1) * nx + x] = s1;
+        }
 
         // fluxes and update at plane k
         const T *sx = ssx + (k & 1) * S.sx, *sy = ssy + (k & 1) * S.sy;
@@ -333,6 +343,13 @@ __device__ __forceinline__ void band_unit(const FwdArgs<T> &a, int y0, int hb, i
         for (int i = 0; i < CPT; ++i) {
             if (!owns(i)) continue;
             const int c = ci[i], p = c + 2 * nx, dm = dmi(i), dp = dpi(i);
+            T szn;
+            {
+                T s0, s1;
+                sharp(Pk1, Pk, Pk2, p, dm, dp, s0, s1, szn);
+                sxw[c] = s0;
+                syw[c + nx] = s1;
+            }
             const T pc = Pk[p];
             const T pxm = Pk[p + dm], pxp = Pk[p + dp];
             const T pym = Pk[p - nx], pyp = Pk[p + nx];
@@ -348,13 +365,13 @@ __device__ __forceinline__ void band_unit(const FwdArgs<T> &a, int y0, int hb, i
             adv = fma(-vm, pym + pc, adv);
             const T dif = fma(T(-4), pc, (pxm + pxp) + (pym + pyp));
             const T shp = (sxp - sxm) + (syp - sym);
-            const T Fzp = flux(c_adv * wc, c_dif, c_shp, pc, pzp, szc[i], szn[i]);
+            const T Fzp = flux(c_adv * wc, c_dif, c_shp, pc, pzp, szc[i], szn);
             const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, Fzp - Fzm[i])));
             const T o = fma(-c_upd, div, pc);
             outp[CDI_CHK(c, plane - obase, st)] = o;
             acc.add(o, a.c.tol);
             Fzm[i] = Fzp;
-            szc[i] = szn[i];
+            szc[i] = szn;
         }
         pk = pk1;
         vk = vk == 2 ? 0 : vk + 1;

@@ -84,7 +84,13 @@ __device__ __forceinline__ Unit unit_of(int u, int ntiles, int tiles_x, int bw, 
 //     [b T / B, (b + 1) T / B) of the T = ntiles * nz tile-planes in
 //     tile-major order (T < 2^31, checked by the host), cut where a tile's
 //     column ends: every block gets the same number of planes (+-1) in one or
-//     two units (more only when a share exceeds a column).
+//     two units (more only when a share exceeds a column).  Each tile's column
+//     is visited rotated, starting at plane nz - e_t, where e_t is the offset
+//     of the first share that begins inside that column: the shares that begin
+//     inside any column then begin at the same planes (0, P, 2P, ... to
+//     rounding, P = T / B) for every tile, so the blocks on neighbouring tiles
+//     march through the same planes at the same time and the halo rows they
+//     share meet in L2, as with chunk-major units.
 template <int BW, int BH>
 struct UnitIter {
     int p;  // next unit, or next tile-plane (the only state: the rest is recomputed
@@ -103,16 +109,22 @@ struct UnitIter {
             p += gridDim.x;
             return true;
         }
-        const int q = (int)((long long)ntiles * nz * (blockIdx.x + 1) / gridDim.x);
+        const long long T = (long long)ntiles * nz;
+        const int q = (int)(T * (blockIdx.x + 1) / gridDim.x);
         if (p >= q) return false;
         const int tile = p / nz;
-        const int z0 = p - tile * nz;
-        const int z1 = min(nz, z0 + (q - p));
+        const int j = p - tile * nz;             // position in the tile's column
+        const int je = min(nz, j + (q - p));
+        // offset e of the first share beginning inside this column
+        const long long col = (long long)tile * nz;
+        const long long bs = (col * gridDim.x + T - 1) / T;
+        const long long qs = T * bs / gridDim.x;
+        const int e = qs < col + nz ? (int)(qs - col) : 0;
         r.x0 = (tile % tiles_x) * BW;
         r.y0 = (tile / tiles_x) * BH;
-        r.z0 = z0;
-        r.z1 = z1;
-        p += z1 - z0;
+        r.z0 = j >= e ? j - e : nz - e + j;      // the column rotated by e
+        r.z1 = r.z0 + (je - j);
+        p += je - j;
         return true;
     }
 };
