@@ -386,8 +386,12 @@ CDI_API int cdi_probe_fp64_rate(double *fma_per_s, void *stream);
 /* Kernels with a tunable launch configuration. */
 enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
 
-/* Forward work split of cdi_set_launch: equal contiguous shares per block. */
+/* Forward work split of cdi_set_launch: equal contiguous shares per block;
+ * the same shares with each tile's column visited rotated so that the blocks on
+ * neighbouring tiles work on the same planes at the same time (their shared
+ * halo rows then come from L2 rather than memory). */
 #define CDI_NCHUNKS_BALANCED (-1)
+#define CDI_NCHUNKS_ROTATED (-2)
 
 /* Choose the launch configuration of a kernel of this grid (not part of the
  * paper: a performance control).  Forward tiles: 0..3 one cell per thread
@@ -397,9 +401,12 @@ enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
  * split: nchunks >= 1 cuts every tile column into that many z chunks, taken
  * round-robin by the persistent blocks; CDI_NCHUNKS_BALANCED gives every block
  * an equal contiguous share of the tile-planes (tile-major, cut at column
- * ends); 0 picks one of these from a cost model.  Adjoint
+ * ends), CDI_NCHUNKS_ROTATED the same shares with rotated columns; 0 picks
+ * chunks or CDI_NCHUNKS_BALANCED from a cost model.  Adjoint
  * tiles: 0..2 (32x8, 32x16, 32x4 cells) and 3 (vector), nchunks sets the z
- * chunking (CDI_NCHUNKS_BALANCED: balanced shares, tile 3 only).  Every
+ * chunking (CDI_NCHUNKS_BALANCED / CDI_NCHUNKS_ROTATED: balanced shares, tile 3
+ * only; the vector adjoint's default takes the rotated shares where the cost
+ * model favours balanced ones).  Every
  * configuration computes the same result up to the order of the reduction
  * partials. */
 CDI_API int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchunks);

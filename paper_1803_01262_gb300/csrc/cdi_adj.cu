@@ -732,12 +732,12 @@ static cudaError_t launch_adj_vec(const AdjArgs<T> &a, cudaStream_t s)
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    // zchunk < 0: balanced shares of the tile-planes (UnitIter); else z chunks
+    // zchunk < 0: balanced shares of the tile-planes (UnitIter; -2 rotated); else z chunks
     const long long tiles = (long long)((a.nx + C::W - 1) / C::W) * ((a.ny + C::H - 1) / C::H);
     int nchunks;
     long long units;
     if (a.zchunk < 0) {
-        nchunks = -1;
+        nchunks = a.zchunk == -2 ? -2 : -1;
         units = tiles * a.nz;
     } else {
         nchunks = (a.nz + a.zchunk - 1) / a.zchunk;

@@ -143,7 +143,8 @@ static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, 
     const long long G = (long long)resident * g->sm_count;
     const long long tiles = cdi::fwd_tiles_xy(tile, es, g->nx, g->ny);
     const int nz = g->nz;
-    if (nchunks < 0 && nchunks != CDI_NCHUNKS_BALANCED) return fail(CDI_ERR_ARG, "nchunks %d", nchunks);
+    if (nchunks < 0 && nchunks != CDI_NCHUNKS_BALANCED && nchunks != CDI_NCHUNKS_ROTATED)
+        return fail(CDI_ERR_ARG, "nchunks %d", nchunks);
     if (nchunks == 0) {
         double best = 1e300;
         for (int nc = 1; nc <= nz; ++nc) {
@@ -162,7 +163,7 @@ static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, 
         if (bal < best * (1.0 - 1e-9) && tiles * nz < (1LL << 31)) nchunks = CDI_NCHUNKS_BALANCED;
     }
     long long nb;
-    if (nchunks == CDI_NCHUNKS_BALANCED) {
+    if (nchunks == CDI_NCHUNKS_BALANCED || nchunks == CDI_NCHUNKS_ROTATED) {
         const long long T = tiles * nz;
         if (T >= (1LL << 31)) return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
         nb = G < T ? G : T;
@@ -219,7 +220,7 @@ static int adj_vec_zchunk(const cdi_grid *g)
     }
     const long long P = (tiles * nz + G - 1) / G;
     const double bal = (double)P + 3.0 * (double)((P + nz - 1) / nz + 1);
-    if (bal < best * (1.0 - 1e-9) && tiles * nz < (1LL << 31)) return -1;
+    if (bal < best * (1.0 - 1e-9) && tiles * nz < (1LL << 31)) return CDI_NCHUNKS_ROTATED;
     return (nz + nch - 1) / nch;
 }
 
@@ -556,7 +557,8 @@ static int tb_cfg(const cdi_grid *g, int nchunks, LaunchCfg *c)
     cdi::tb2_tile_dims(es, &bw, &bh);
     const long long tiles = (long long)((g->nx + bw - 1) / bw) * ((g->ny + bh - 1) / bh);
     const int nz = g->nz;
-    if (nchunks < 0 && nchunks != CDI_NCHUNKS_BALANCED) return fail(CDI_ERR_ARG, "nchunks %d", nchunks);
+    if (nchunks < 0 && nchunks != CDI_NCHUNKS_BALANCED && nchunks != CDI_NCHUNKS_ROTATED)
+        return fail(CDI_ERR_ARG, "nchunks %d", nchunks);
     if (nchunks == 0) {
         double best = 1e300;
         for (int nc = 1; nc <= nz; ++nc) {
@@ -575,7 +577,7 @@ static int tb_cfg(const cdi_grid *g, int nchunks, LaunchCfg *c)
         if (bal < best * (1.0 - 1e-9) && tiles * nz < (1LL << 31)) nchunks = CDI_NCHUNKS_BALANCED;
     }
     long long nb;
-    if (nchunks == CDI_NCHUNKS_BALANCED) {
+    if (nchunks == CDI_NCHUNKS_BALANCED || nchunks == CDI_NCHUNKS_ROTATED) {
         const long long T = tiles * nz;
         if (T >= (1LL << 31)) return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
         nb = G < T ? G : T;
@@ -1076,13 +1078,13 @@ int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchu
         if (cdi::adj_tile_is_vec(tile) && !cdi::adj_tile_is_vec(c.tile)) c.zchunk = adj_vec_zchunk(g);
         c.tile = tile;
         if (nchunks > 0) c.zchunk = (g->nz + nchunks - 1) / nchunks;
-        if (nchunks == CDI_NCHUNKS_BALANCED) {
+        if (nchunks == CDI_NCHUNKS_BALANCED || nchunks == CDI_NCHUNKS_ROTATED) {
             if (!cdi::adj_tile_is_vec(tile)) return fail(CDI_ERR_ARG, "balanced split: vector adjoint tile only");
             int bw, bh;
             cdi::adj_vec_tile_dims((int)esize(g), &bw, &bh);
             if ((long long)((g->nx + bw - 1) / bw) * ((g->ny + bh - 1) / bh) * g->nz >= (1LL << 31))
                 return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
-            c.zchunk = -1;
+            c.zchunk = nchunks;
         } else if (nchunks < 0) {
             return fail(CDI_ERR_ARG, "nchunks %d", nchunks);
         }
@@ -1273,7 +1275,7 @@ int cdi_get_launch(const cdi_grid *g, int which, int *tile, int *nblocks, int *n
     if (nblocks) *nblocks = c->nblocks;
     if (nchunks)
         *nchunks = which == CDI_KERNEL_FORWARD ? c->nchunks
-                   : c->zchunk < 0           ? CDI_NCHUNKS_BALANCED
+                   : c->zchunk < 0           ? c->zchunk
                                              : (g->nz + c->zchunk - 1) / c->zchunk;
     return CDI_OK;
 }
@@ -1296,7 +1298,8 @@ int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps, d
     LaunchCfg best = saved;
     float best_t = 1e30f;
     int rc = CDI_OK;
-    const int chunk_opts[] = {CDI_NCHUNKS_BALANCED, 0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 20, 24, 32};
+    const int chunk_opts[] = {CDI_NCHUNKS_BALANCED, CDI_NCHUNKS_ROTATED, 0, 1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14,
+                              16, 20, 24, 32};
     for (int tile = 0; tile < cdi::fwd_num_tiles() && rc == CDI_OK; ++tile) {
         if (cdi::fwd_tile_is_vec(tile) && g->nx % (16 / (int)esize(g)) != 0) continue;
         if (g->sharpen == CDI_SHARPEN_FACE && tile != 0) continue;
@@ -1333,7 +1336,7 @@ int cdi_autotune(cdi_grid *g, void *phi_a, void *phi_b, double dt, double eps, d
     float best2 = 1e30f;
     LaunchCfg best_tb = g->tb;
     const bool tb_ok = rc == CDI_OK && g->sharpen == CDI_SHARPEN_CENTRE && g->nx % (16 / (int)esize(g)) == 0;
-    const int tb_opts[] = {CDI_NCHUNKS_BALANCED, 0, 1, 2, 4, 8};
+    const int tb_opts[] = {CDI_NCHUNKS_BALANCED, CDI_NCHUNKS_ROTATED, 0, 1, 2, 4, 8};
     for (int oi = 0; tb_ok && rc == CDI_OK && oi < (int)(sizeof(tb_opts) / sizeof(int)); ++oi) {
         if (tb_opts[oi] > g->nz) continue;
         LaunchCfg c;

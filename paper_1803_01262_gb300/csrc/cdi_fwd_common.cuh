@@ -84,9 +84,10 @@ __device__ __forceinline__ Unit unit_of(int u, int ntiles, int tiles_x, int bw, 
 //     [b T / B, (b + 1) T / B) of the T = ntiles * nz tile-planes in
 //     tile-major order (T < 2^31, checked by the host), cut where a tile's
 //     column ends: every block gets the same number of planes (+-1) in one or
-//     two units (more only when a share exceeds a column).  Each tile's column
-//     is visited rotated, starting at plane nz - e_t, where e_t is the offset
-//     of the first share that begins inside that column: the shares that begin
+//     two units (more only when a share exceeds a column).
+//   nchunks == -2 (balanced, rotated): the same shares, each tile's column
+//     visited rotated, starting at plane nz - e_t, where e_t is the offset of
+//     the first share that begins inside that column: the shares that begin
 //     inside any column then begin at the same planes (0, P, 2P, ... to
 //     rounding, P = T / B) for every tile, so the blocks on neighbouring tiles
 //     march through the same planes at the same time and the halo rows they
@@ -116,10 +117,13 @@ struct UnitIter {
         const int j = p - tile * nz;             // position in the tile's column
         const int je = min(nz, j + (q - p));
         // offset e of the first share beginning inside this column
-        const long long col = (long long)tile * nz;
-        const long long bs = (col * gridDim.x + T - 1) / T;
-        const long long qs = T * bs / gridDim.x;
-        const int e = qs < col + nz ? (int)(qs - col) : 0;
+        int e = 0;
+        if (nchunks == -2) {
+            const long long col = (long long)tile * nz;
+            const long long bs = (col * gridDim.x + T - 1) / T;
+            const long long qs = T * bs / gridDim.x;
+            e = qs < col + nz ? (int)(qs - col) : 0;
+        }
         r.x0 = (tile % tiles_x) * BW;
         r.y0 = (tile / tiles_x) * BH;
         r.z0 = j >= e ? j - e : nz - e + j;      // the column rotated by e

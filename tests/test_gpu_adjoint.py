@@ -138,7 +138,8 @@ def test_adjoint_floor_regime(dtype, tile):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 @pytest.mark.parametrize("shape", [(64, 64, 256), (9, 21, 68), (2, 17, 132), (20, 9, 64)])
 @pytest.mark.parametrize("with_vel", [False, True])
-def test_adjoint_balanced_split(dtype, shape, with_vel):
+@pytest.mark.parametrize("split", [cdi.CDI_NCHUNKS_BALANCED, cdi.CDI_NCHUNKS_ROTATED])
+def test_adjoint_balanced_split(dtype, shape, with_vel, split):
     """The vector adjoint with equal contiguous tile-plane shares per block (shares cut
     inside a column and one-plane shares) gives the oracle's adjoint step."""
     phi, u, v, w, lam, h = case(shape, 13 + shape[0], dtype == torch.float32)
@@ -148,8 +149,8 @@ def test_adjoint_balanced_split(dtype, shape, with_vel):
     nz, ny, nx = shape
     g = cdi.Grid(nx, ny, nz, h, dtype)
     g.set_velocity(*[dev(x, dtype) for x in (u, v, w)])
-    g.set_launch(cdi.CDI_KERNEL_ADJOINT, 3, 0, cdi.CDI_NCHUNKS_BALANCED)
-    assert g.get_launch(cdi.CDI_KERNEL_ADJOINT)["nchunks"] == cdi.CDI_NCHUNKS_BALANCED
+    g.set_launch(cdi.CDI_KERNEL_ADJOINT, 3, 0, split)
+    assert g.get_launch(cdi.CDI_KERNEL_ADJOINT)["nchunks"] == split
     out = torch.empty(shape, dtype=dtype, device="cuda")
     grads = None
     if with_vel:
@@ -169,7 +170,7 @@ def test_adjoint_balanced_split(dtype, shape, with_vel):
             s2 = max(1.0, np.abs(rg).max())
             assert np.abs(gd.double().cpu().numpy() - (base + rg)).max() <= tol * s2 * 4
     with pytest.raises(cdi.CDIError):
-        g.set_launch(cdi.CDI_KERNEL_ADJOINT, 0, 0, cdi.CDI_NCHUNKS_BALANCED)
+        g.set_launch(cdi.CDI_KERNEL_ADJOINT, 0, 0, split)
 
 
 def test_adjoint_constant_lambda_gpu():

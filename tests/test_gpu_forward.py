@@ -304,15 +304,17 @@ def test_every_launch_configuration(dtype, tile, shape, nchunks):
                                             ((2, 512, 512), 4, 1), ((2, 512, 512), 1, 1),
                                             ((9, 21, 68), 4, 0), ((9, 21, 68), 3, 0),
                                             ((5, 7, 4), 0, 0), ((16, 32, 128), 6, 1)])
-def test_balanced_split(dtype, shape, tile, bps):
-    """Equal contiguous shares of the tile-planes per block (CDI_NCHUNKS_BALANCED): shares
-    cut inside a tile column, shares spanning many short columns, one-plane shares."""
+@pytest.mark.parametrize("split", [cdi.CDI_NCHUNKS_BALANCED, cdi.CDI_NCHUNKS_ROTATED])
+def test_balanced_split(dtype, shape, tile, bps, split):
+    """Equal contiguous shares of the tile-planes per block (CDI_NCHUNKS_BALANCED, and rotated
+    columns, CDI_NCHUNKS_ROTATED): shares cut inside a tile column, shares spanning many short
+    columns, one-plane shares."""
     f = random_fields(shape, 17 + shape[0], True, smooth=True)
     eps, gamma = 1.1 * f.h, 0.9
     dt = 0.12 * f.h * f.h / (gamma * eps)
     g, vel = make_grid(f, dtype)
-    g.set_launch(cdi.CDI_KERNEL_FORWARD, tile, bps, cdi.CDI_NCHUNKS_BALANCED)
-    assert g.get_launch()["nchunks"] == cdi.CDI_NCHUNKS_BALANCED
+    g.set_launch(cdi.CDI_KERNEL_FORWARD, tile, bps, split)
+    assert g.get_launch()["nchunks"] == split
     a = dev(f.phi, dtype)
     b = torch.empty_like(a)
     g.step(a, b, dt, eps, gamma, 0.8)

@@ -32,7 +32,7 @@ def _setup(shape, dtype, seed):
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("shape", [(20, 24, 64), (9, 21, 68), (33, 20, 72), (5, 7, 8), (1, 40, 128),
                                    (40, 16, 128), (2, 33, 36), (64, 32, 64)])
-@pytest.mark.parametrize("nchunks", [-1, 0, 3])
+@pytest.mark.parametrize("nchunks", [-1, -2, 0, 3])
 def test_two_steps_per_pass_bit_for_bit(dtype, shape, nchunks):
     g, vel, f, h = _setup(shape, dtype, 7 + shape[0])
     eps, gamma = 1.2 * h, 1.0
