@@ -402,7 +402,7 @@ enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
  * round-robin by the persistent blocks; CDI_NCHUNKS_BALANCED gives every block
  * an equal contiguous share of the tile-planes (tile-major, cut at column
  * ends), CDI_NCHUNKS_ROTATED the same shares with rotated columns; 0 picks
- * chunks or CDI_NCHUNKS_BALANCED from a cost model.  Adjoint
+ * chunks or CDI_NCHUNKS_ROTATED from a cost model.  Adjoint
  * tiles: 0..2 (32x8, 32x16, 32x4 cells) and 3 (vector), nchunks sets the z
  * chunking (CDI_NCHUNKS_BALANCED / CDI_NCHUNKS_ROTATED: balanced shares, tile 3
  * only; the vector adjoint's default takes the rotated shares where the cost

@@ -580,24 +580,26 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
             if (k + 2 < z1) issue_vel(k + 2, vk2);
             cp_async_commit();
 
-            // B: gbar at plane k+1 (buffer (k+1)&1; phase C reads buffer k&1).
+            // B: gbar at plane k+1 (buffer (k+1)&1; phase C reads buffer k&1).  An own
+            // thread runs B and C in one block, so that the compiler may overlap them.
             const int b1 = (k + 1) & 1;
-            T gzp[VX], tp[VX];
-            if (is_own) {
-                T b0[VX], bb1[VX];
-                gbar_group(pk1, pk, pk2, tx, ty, b0, bb1, gzp, tp);
-                VV::st(sgx + b1 * C::SXS + ty * SXP + VX + tx * VX, b0);
-                VV::st(sgy + b1 * C::SYS + (ty + 1) * W + tx * VX, bb1);
-            } else if (is_yring) {
+            if (is_yring) {
                 T b0[VX], bb1[VX], b2[VX], t_[VX];
                 gbar_group(pk1, pk, pk2, ry_col, ry_row, b0, bb1, b2, t_);
                 VV::st(sgy + b1 * C::SYS + (ry_row + 1) * W + ry_col * VX, bb1);
             } else if (is_xring) {
                 sgx[b1 * C::SXS + rx_row * SXP + VX + rx_col] = gbar_x_cell(pk1, pk, pk2, rx_col, rx_row);
             }
-
-            // C: lam at plane k.
             if (is_own) {
+                T gzp[VX], tp[VX];
+                {
+                    T b0[VX], bb1[VX];
+                    gbar_group(pk1, pk, pk2, tx, ty, b0, bb1, gzp, tp);
+                    VV::st(sgx + b1 * C::SXS + ty * SXP + VX + tx * VX, b0);
+                    VV::st(sgy + b1 * C::SYS + (ty + 1) * W + tx * VX, bb1);
+                }
+
+                // C: lam at plane k.
                 const int b = k & 1;
                 const int po = (ty + 2) * PP + VX + tx * VX;
                 const T *Lk = slam + pk * C::PHI, *Lk1 = slam + pk1 * C::PHI;
