@@ -387,9 +387,11 @@ CDI_API int cdi_probe_fp64_rate(double *fma_per_s, void *stream);
 enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
 
 /* Forward work split of cdi_set_launch: equal contiguous shares per block;
- * the same shares with each tile's column visited rotated so that the blocks on
- * neighbouring tiles work on the same planes at the same time (their shared
- * halo rows then come from L2 rather than memory). */
+ * near-equal shares, a share that starts a second tile column being 4 planes
+ * shorter to pay for that column's prologue, with each tile's column visited
+ * rotated so that the blocks on neighbouring tiles work on the same planes at
+ * the same time (their shared halo rows then come from L2 rather than memory).
+ * The rotated split needs tiles * (nz + 4) < 2^31 (else CDI_ERR_DIM). */
 #define CDI_NCHUNKS_BALANCED (-1)
 #define CDI_NCHUNKS_ROTATED (-2)
 

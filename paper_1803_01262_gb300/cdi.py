@@ -28,11 +28,13 @@ CDI_EULER, CDI_RK2, CDI_RK3, CDI_RK4 = 0, 1, 2, 3
 CDI_CHECK_CONDITION = 1
 CDI_KERNEL_FORWARD, CDI_KERNEL_ADJOINT = 0, 1
 CDI_NCHUNKS_BALANCED = -1   # forward work split: equal contiguous shares per block
-CDI_NCHUNKS_ROTATED = -2    # the same shares, tile columns rotated so neighbours share halos in L2
+CDI_NCHUNKS_ROTATED = -2    # near-equal shares (column starts weighted), columns rotated so
+                            # neighbouring tiles share their halo rows in L2
 CDI_SHARPEN_CENTRE, CDI_SHARPEN_FACE = 0, 1
 SHARPEN = {"centre": CDI_SHARPEN_CENTRE, "face": CDI_SHARPEN_FACE}
 FWD_TILES = 7
 ADJ_TILES = 4
+BATCH_TILES = 6
 
 _ERRNAMES = {-1: "CDI_ERR_ARG", -2: "CDI_ERR_DIM", -3: "CDI_ERR_CUDA", -4: "CDI_ERR_CONDITION",
              -5: "CDI_ERR_NAN", -6: "CDI_ERR_TIMEOUT", -7: "CDI_ERR_STATE", -8: "CDI_ERR_BOUNDS"}

@@ -113,13 +113,28 @@ static void reset_run_host(StatsRec *r)
     r->mx_run = -INFINITY;
 }
 
+// The rotated balanced split (shares cut from a cost line where each tile column
+// counts kSharePrologue planes more than its nz): its critical path in planes,
+// every share's cost plus its own prologue of `pro` planes, and whether its
+// cost line fits the kernels' 32-bit positions.  A share longer than a column
+// runs through several tiles one after another, out of step with the blocks on
+// the neighbouring tiles, whose halo rows then come from memory twice: the
+// model does not offer the split there (measured at 1024^3: 4.70 ms per step
+// against 4.14 ms with 6 z chunks).
+static double rotated_cost(long long tiles, int nz, long long G, double pro)
+{
+    const long long share = (tiles * (nz + cdi::kSharePrologue) + G - 1) / G;
+    return share > nz ? 1e300 : (double)share + pro;
+}
+static bool rotated_fits(long long tiles, int nz) { return tiles * (nz + cdi::kSharePrologue) < (1LL << 31); }
+
 // Forward launch: a tile shape, as many blocks as fit on the GPU at once, and
 // the work split.  nchunks >= 1: z chunks per tile column, (chunk, tile) units
 // taken round-robin; CDI_NCHUNKS_BALANCED: equal contiguous shares of the
 // tile-planes per block; 0: the split minimising the per-block critical path
 // in planes, 3 planes of prologue per unit:
 //   chunks: max(rounds * (planes per unit + 3), units * (planes per unit + 1) / blocks)
-//   balanced: P + 3 (ceil(P / nz) + 1), P = ceil(tiles * nz / blocks).
+//   rotated balanced: ceil(tiles * (nz + kSharePrologue) / blocks) + 3.
 static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, LaunchCfg *c,
                    bool rk = false, bool slab = false)
 {
@@ -158,16 +173,16 @@ static int fwd_cfg(const cdi_grid *g, int tile, int blocks_per_sm, int nchunks, 
                 nchunks = nc;
             }
         }
-        const long long P = (tiles * nz + G - 1) / G;
-        const double bal = (double)P + 3.0 * (double)((P + nz - 1) / nz + 1);
         // balanced shares with rotated columns where they win: neighbouring tiles then share
         // their halo rows in L2 (measured: 256^3 79.5 vs 80.6 us, 512^3 521 vs 584 us)
-        if (bal < best * (1.0 - 1e-9) && tiles * nz < (1LL << 31)) nchunks = CDI_NCHUNKS_ROTATED;
+        if (rotated_cost(tiles, nz, G, 3.0) < best * (1.0 - 1e-9) && rotated_fits(tiles, nz))
+            nchunks = CDI_NCHUNKS_ROTATED;
     }
     long long nb;
     if (nchunks == CDI_NCHUNKS_BALANCED || nchunks == CDI_NCHUNKS_ROTATED) {
         const long long T = tiles * nz;
-        if (T >= (1LL << 31)) return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
+        if (T >= (1LL << 31) || (nchunks == CDI_NCHUNKS_ROTATED && !rotated_fits(tiles, nz)))
+            return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
         nb = G < T ? G : T;
     } else {
         if (nchunks > nz) nchunks = nz;
@@ -220,9 +235,8 @@ static int adj_vec_zchunk(const cdi_grid *g)
             nch = nc;
         }
     }
-    const long long P = (tiles * nz + G - 1) / G;
-    const double bal = (double)P + 3.0 * (double)((P + nz - 1) / nz + 1);
-    if (bal < best * (1.0 - 1e-9) && tiles * nz < (1LL << 31)) return CDI_NCHUNKS_ROTATED;
+    if (rotated_cost(tiles, nz, G, 3.0) < best * (1.0 - 1e-9) && rotated_fits(tiles, nz))
+        return CDI_NCHUNKS_ROTATED;
     return (nz + nch - 1) / nch;
 }
 
@@ -574,14 +588,14 @@ static int tb_cfg(const cdi_grid *g, int nchunks, LaunchCfg *c)
                 nchunks = nc;
             }
         }
-        const long long P = (tiles * nz + G - 1) / G;
-        const double bal = (double)P + 6.0 * (double)((P + nz - 1) / nz + 1);
-        if (bal < best * (1.0 - 1e-9) && tiles * nz < (1LL << 31)) nchunks = CDI_NCHUNKS_ROTATED;
+        if (rotated_cost(tiles, nz, G, 6.0) < best * (1.0 - 1e-9) && rotated_fits(tiles, nz))
+            nchunks = CDI_NCHUNKS_ROTATED;
     }
     long long nb;
     if (nchunks == CDI_NCHUNKS_BALANCED || nchunks == CDI_NCHUNKS_ROTATED) {
         const long long T = tiles * nz;
-        if (T >= (1LL << 31)) return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
+        if (T >= (1LL << 31) || (nchunks == CDI_NCHUNKS_ROTATED && !rotated_fits(tiles, nz)))
+            return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
         nb = G < T ? G : T;
     } else {
         if (nchunks > nz) nchunks = nz;
@@ -1084,7 +1098,8 @@ int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchu
             if (!cdi::adj_tile_is_vec(tile)) return fail(CDI_ERR_ARG, "balanced split: vector adjoint tile only");
             int bw, bh;
             cdi::adj_vec_tile_dims((int)esize(g), &bw, &bh);
-            if ((long long)((g->nx + bw - 1) / bw) * ((g->ny + bh - 1) / bh) * g->nz >= (1LL << 31))
+            const long long tiles = (long long)((g->nx + bw - 1) / bw) * ((g->ny + bh - 1) / bh);
+            if (tiles * g->nz >= (1LL << 31) || (nchunks == CDI_NCHUNKS_ROTATED && !rotated_fits(tiles, g->nz)))
                 return fail(CDI_ERR_DIM, "balanced split needs fewer than 2^31 tile-planes");
             c.zchunk = nchunks;
         } else if (nchunks < 0) {

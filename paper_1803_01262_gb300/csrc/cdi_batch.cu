@@ -162,7 +162,7 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
             else
                 scalar_unit<T, BX, BY, false, SCALAR_PF, FACE>(a, un, acc, smem_raw);
         }
-        const Partial p = block_reduce(acc.partial());
+        const Partial p = block_partial(acc);
         if (tid == 0) {
             partials[u] = p;
             __threadfence();
@@ -174,9 +174,7 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
         if (fb >= 0) {  // this block completed box fb: fold its slots in unit order
             __threadfence();
             const int u0 = boxes[fb].unit0, nu = boxes[fb].nunits;
-            Partial q = pidentity();
-            for (int i = tid; i < nu; i += BX * BY) q = pcombine(q, load_partial_cg(partials + u0 + i));
-            q = block_reduce(q);
+            const Partial q = combine_partials<IsF32<Acc<T>>::value>(partials + u0, nu);
             if (tid == 0) {
                 StatsRec *r = recs + fb;
                 r->mass = boxes[fb].dV * q.sum;

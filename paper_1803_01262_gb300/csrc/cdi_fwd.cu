@@ -383,7 +383,7 @@ fwd_vec_kernel(const FwdArgs<T> a, const int nchunks)
     }
     if (!dep_waited) grid_dep_wait();
     grid_dep_launch();  // the next step may start staging its velocities
-    reduce_and_finish<ZR>(acc.partial(), a.red);
+    reduce_and_finish<ZR>(acc, a.red);
 }
 
 // ===========================================================================
@@ -409,7 +409,7 @@ fwd_kernel(const FwdArgs<T> a, const int nchunks)
         else
             scalar_unit<T, BX, BY, RK, SCALAR_PF, FACE>(a, un, acc, smem_raw);
     }
-    reduce_and_finish<ZR>(acc.partial(), a.red);
+    reduce_and_finish<ZR>(acc, a.red);
 }
 
 // ===========================================================================
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(256) stats_kernel(const T *__restrict__ phi, l
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
         acc.add(phi[i], tol);
-    reduce_and_finish(acc.partial(), red);
+    reduce_and_finish(acc, red);
 }
 
 template <typename T>

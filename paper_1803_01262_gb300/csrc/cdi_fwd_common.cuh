@@ -85,13 +85,16 @@ __device__ __forceinline__ Unit unit_of(int u, int ntiles, int tiles_x, int bw, 
 //     tile-major order (T < 2^31, checked by the host), cut where a tile's
 //     column ends: every block gets the same number of planes (+-1) in one or
 //     two units (more only when a share exceeds a column).
-//   nchunks == -2 (balanced, rotated): the same shares, each tile's column
-//     visited rotated, starting at plane nz - e_t, where e_t is the offset of
-//     the first share that begins inside that column: the shares that begin
-//     inside any column then begin at the same planes (0, P, 2P, ... to
-//     rounding, P = T / B) for every tile, so the blocks on neighbouring tiles
-//     march through the same planes at the same time and the halo rows they
-//     share meet in L2, as with chunk-major units.
+//   nchunks == -2 (balanced, rotated, prologue-weighted): the shares are cut
+//     from a cost line on which each column counts kSharePrologue (in
+//     cdi_internal.cuh) planes more than its nz (its first piece's prologue), so a share that crosses
+//     into a new column, and pays a second prologue there, gets that many
+//     planes fewer; and each tile's column is visited rotated, starting at
+//     plane nz - e_t, where e_t is the offset of the first share that begins
+//     inside that column: the shares that begin inside any column then begin
+//     at the same planes (0, P, 2P, ... to rounding) for every tile, so the
+//     blocks on neighbouring tiles march through the same planes at the same
+//     time and the halo rows they share meet in L2, as with chunk-major units.
 template <int BW, int BH>
 struct UnitIter {
     int p;  // next unit, or next tile-plane (the only state: the rest is recomputed
@@ -99,7 +102,8 @@ struct UnitIter {
     __device__ __forceinline__ UnitIter(int ntiles, int nz, int nchunks)
     {
         p = nchunks >= 1 ? (int)blockIdx.x
-                         : (int)((long long)ntiles * nz * blockIdx.x / gridDim.x);
+                         : (int)((long long)ntiles * (nz + (nchunks == -2 ? kSharePrologue : 0)) *
+                                 blockIdx.x / gridDim.x);
     }
     __device__ __forceinline__ bool next(Unit &r, int ntiles, int tiles_x, int nz, int nchunks)
     {
@@ -110,25 +114,34 @@ struct UnitIter {
             p += gridDim.x;
             return true;
         }
-        const long long T = (long long)ntiles * nz;
-        const int q = (int)(T * (blockIdx.x + 1) / gridDim.x);
-        if (p >= q) return false;
-        const int tile = p / nz;
-        const int j = p - tile * nz;             // position in the tile's column
-        const int je = min(nz, j + (q - p));
+        // the cost line: each column is w prologue slots, then its nz planes
+        const int w = nchunks == -2 ? kSharePrologue : 0;
+        const long long L = (long long)nz + w;
+        const long long T = (long long)ntiles * L;
+        const long long q = T * (blockIdx.x + 1) / gridDim.x;
+        int tile, j, je;
+        long long cs;
+        for (;;) {
+            if (p >= q) return false;
+            tile = (int)(p / L);
+            cs = (long long)tile * L;
+            const long long ce = q < cs + L ? q : cs + L;
+            j = (int)(p - cs - w > 0 ? p - cs - w : 0);     // position in the tile's column
+            je = (int)(ce - cs - w > 0 ? ce - cs - w : 0);
+            p = (int)ce;
+            if (je > j) break;                               // else only prologue slots
+        }
         // offset e of the first share beginning inside this column
         int e = 0;
         if (nchunks == -2) {
-            const long long col = (long long)tile * nz;
-            const long long bs = (col * gridDim.x + T - 1) / T;
+            const long long bs = (cs * gridDim.x + T - 1) / T;
             const long long qs = T * bs / gridDim.x;
-            e = qs < col + nz ? (int)(qs - col) : 0;
+            e = qs < cs + L && qs - cs - w > 0 ? (int)(qs - cs - w) : 0;
         }
         r.x0 = (tile % tiles_x) * BW;
         r.y0 = (tile / tiles_x) * BH;
         r.z0 = j >= e ? j - e : nz - e + j;      // the column rotated by e
         r.z1 = r.z0 + (je - j);
-        p += je - j;
         return true;
     }
 };

@@ -420,7 +420,7 @@ fwd_tb2_kernel(const FwdArgs<T> a, const T c_adv2, const int nchunks)
         }
         cp_async_wait<0>();
     }
-    reduce_and_finish2(acc1.partial(), acc2.partial(), a.red);
+    reduce_and_finish2(acc1, acc2, a.red);
 }
 
 template <typename T>

@@ -354,7 +354,7 @@ fwd_tma_kernel(const FwdArgs<T> a, const __grid_constant__ TmaMaps maps, const i
         for (int id = waited_hi; id < issued_hi; ++id)
             if (!mbar_wait_bounded(bars + (id & 3), (unsigned)((id >> 2) & 1), a.red.status)) break;
     }
-    reduce_and_finish(acc.partial(), a.red);
+    reduce_and_finish(acc, a.red);
 }
 
 // ---------------------------------------------------------------------------

@@ -1,6 +1,8 @@
 // Fused reductions of the CDI step: discrete mass (double sum), min, max and
 // two violation counts, reduced per block and finished by the last block to
 // arrive (fixed combination order, so results are reproducible run to run).
+// The FP32 kernels reduce in FP32 arithmetic (the sum as a float pair), the
+// FP64 kernels in double; partials are stored in double either way.
 #pragma once
 
 #include <math.h>
@@ -42,6 +44,99 @@ __device__ __forceinline__ Partial warp_reduce(Partial p)
         p = pcombine(p, q);
     }
     return p;
+}
+
+// FP32 form of a partial, for the FP32 kernels' block and grid reductions: the
+// sum as an unevaluated pair hi + lo of floats (|lo| <= ulp(hi) / 2), min and
+// max as floats (exact: they are FP32 values), counts of type C.  Combining two
+// such partials costs a handful of FP32 adds (Knuth's two-sum of the high parts,
+// then renormalisation), so a block reduction stays off GB300's narrow FP64 pipe;
+// the pair keeps about 48 significant bits, against the 53 of a double sum of
+// the same partials.
+template <typename C>
+struct PartialF {
+    float hi, lo, mn, mx;
+    C ns, nt;
+};
+
+template <typename C>
+__device__ __forceinline__ PartialF<C> pidentity_f()
+{
+    PartialF<C> p;
+    p.hi = 0.f;
+    p.lo = 0.f;
+    p.mn = INFINITY;
+    p.mx = -INFINITY;
+    p.ns = 0;
+    p.nt = 0;
+    return p;
+}
+
+// hi + lo = a + b exactly (two-sum), then the pair (hi, lo) = s + e renormalised;
+// a non-finite sum is carried in hi alone.
+__device__ __forceinline__ void sum_pair(float a, float b, float e_in, float &hi, float &lo)
+{
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = ((a - (s - bb)) + (b - bb)) + e_in;
+    const float h = s + e;
+    const bool fin = isfinite(s);
+    hi = fin ? h : s;
+    lo = fin ? e - (h - s) : 0.f;
+}
+
+template <typename C>
+__device__ __forceinline__ PartialF<C> pcombine_f(PartialF<C> a, const PartialF<C> &b)
+{
+    sum_pair(a.hi, b.hi, a.lo + b.lo, a.hi, a.lo);
+    a.mn = fminf(a.mn, b.mn);
+    a.mx = fmaxf(a.mx, b.mx);
+    a.ns += b.ns;
+    a.nt += b.nt;
+    return a;
+}
+
+template <typename C>
+__device__ __forceinline__ PartialF<C> warp_reduce_f(PartialF<C> p)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        PartialF<C> q;
+        q.hi = __shfl_down_sync(0xffffffffu, p.hi, o);
+        q.lo = __shfl_down_sync(0xffffffffu, p.lo, o);
+        q.mn = __shfl_down_sync(0xffffffffu, p.mn, o);
+        q.mx = __shfl_down_sync(0xffffffffu, p.mx, o);
+        q.ns = __shfl_down_sync(0xffffffffu, p.ns, o);
+        q.nt = __shfl_down_sync(0xffffffffu, p.nt, o);
+        p = pcombine_f(p, q);
+    }
+    return p;
+}
+
+template <typename C>
+__device__ __forceinline__ Partial to_partial(const PartialF<C> &q)
+{
+    Partial r;
+    r.sum = (double)q.hi + (double)q.lo;
+    r.mn = (double)q.mn;
+    r.mx = (double)q.mx;
+    r.ns = (long long)q.ns;
+    r.nt = (long long)q.nt;
+    return r;
+}
+
+// A stored partial of an FP32 kernel back in FP32 form (exact for min and max,
+// which came from floats; the sum to within the pair's precision).
+__device__ __forceinline__ PartialF<unsigned long long> from_partial(const Partial &p)
+{
+    PartialF<unsigned long long> r;
+    r.hi = (float)p.sum;
+    r.lo = isfinite(r.hi) ? (float)(p.sum - (double)r.hi) : 0.f;
+    r.mn = (float)p.mn;
+    r.mx = (float)p.mx;
+    r.ns = (unsigned long long)p.ns;
+    r.nt = (unsigned long long)p.nt;
+    return r;
 }
 
 // Per-thread accumulator.  FP32 keeps a compensated (Kahan) float sum so the
@@ -113,6 +208,17 @@ struct Acc<float> {
         r.mx = (double)mx;
         r.ns = ns;
         r.nt = nt;
+        return r;
+    }
+    // the compensated sum s - c as a renormalised pair
+    __device__ __forceinline__ PartialF<unsigned> partial_f() const
+    {
+        PartialF<unsigned> r;
+        sum_pair(s, -c, 0.f, r.hi, r.lo);
+        r.mn = mn;
+        r.mx = mx;
+        r.ns = (unsigned)ns;
+        r.nt = (unsigned)nt;
         return r;
     }
 };
@@ -226,89 +332,129 @@ __device__ __forceinline__ Partial block_reduce(Partial p)
     return q;
 }
 
-// Block-reduce p (every thread of the block must call this), store the block
-// partial, and let the last block to finish combine all partials in index
-// order into red.rec.  The block size must be a multiple of 32.
-// COMBINE: the launch may be a further z slab of a step (red.combine); only the
-// slab kernels are built with it.
-template <bool COMBINE = false>
-__device__ __forceinline__ void reduce_and_finish(Partial p, const RedScratch &red)
+// The same for the FP32 form; the result, valid in thread 0, is converted to
+// the stored (double) form.
+template <typename C>
+__device__ __forceinline__ Partial block_reduce_f(PartialF<C> p)
 {
-    __shared__ Partial wsum[32];
-    __shared__ int is_last;
+    __shared__ PartialF<C> wsum_f[32];
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     const int nthr = blockDim.x * blockDim.y * blockDim.z;
     const int lane = tid & 31, wid = tid >> 5, nw = nthr >> 5;
+    p = warp_reduce_f(p);
+    if (lane == 0) wsum_f[wid] = p;
+    __syncthreads();
+    Partial r = pidentity();
+    if (wid == 0) {
+        PartialF<C> q = lane < nw ? wsum_f[lane] : pidentity_f<C>();
+        q = warp_reduce_f(q);
+        if (lane == 0) r = to_partial(q);
+    }
+    __syncthreads();
+    return r;
+}
+
+// The block's partial of a per-thread accumulator, valid in thread 0: FP32
+// kernels reduce in the FP32 form, FP64 kernels in double.
+__device__ __forceinline__ Partial block_partial(const Acc<float> &acc) { return block_reduce_f(acc.partial_f()); }
+__device__ __forceinline__ Partial block_partial(const Acc<double> &acc) { return block_reduce(acc.partial()); }
+__device__ __forceinline__ Partial block_partial(const Partial &p) { return block_reduce(p); }
+
+// Combine the stored partials parts[0, n) with a fixed tree (every thread of
+// the block takes part; the result is valid in thread 0): in the FP32 form for
+// an FP32 kernel's partials, else in double.
+template <bool F32>
+__device__ __forceinline__ Partial combine_partials(const Partial *parts, int n)
+{
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    if constexpr (F32) {
+        PartialF<unsigned long long> a = pidentity_f<unsigned long long>();
+        for (int i = tid; i < n; i += nthr) a = pcombine_f(a, from_partial(load_partial_cg(parts + i)));
+        return block_reduce_f(a);
+    } else {
+        Partial a = pidentity();
+        for (int i = tid; i < n; i += nthr) a = pcombine(a, load_partial_cg(parts + i));
+        return block_reduce(a);
+    }
+}
+
+template <typename A> struct IsF32 { static constexpr bool value = false; };
+template <> struct IsF32<Acc<float>> { static constexpr bool value = true; };
+
+// Store the block's partial p (valid in thread 0) and let the last block to
+// finish combine all partials in index order into red.rec.  Every thread of
+// the block calls this; the block size must be a multiple of 32.
+// COMBINE: the launch may be a further z slab of a step (red.combine); only the
+// slab kernels are built with it.
+template <bool COMBINE, bool F32>
+__device__ __forceinline__ void finish_partial(const Partial &p, const RedScratch &red)
+{
+    __shared__ int is_last;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int nb = gridDim.x * gridDim.y * gridDim.z;
-
-    p = warp_reduce(p);
-    if (lane == 0) wsum[wid] = p;
-    __syncthreads();
-    if (wid == 0) {
-        Partial q = lane < nw ? wsum[lane] : pidentity();
-        q = warp_reduce(q);
-        if (lane == 0) {
-            red.partials[bid] = q;
-            __threadfence();
-            unsigned prev = atomicAdd(red.counter, 1u);
-            is_last = (prev == (unsigned)(nb - 1));
-        }
+    if (tid == 0) {
+        red.partials[bid] = p;
+        __threadfence();
+        const unsigned prev = atomicAdd(red.counter, 1u);
+        is_last = (prev == (unsigned)(nb - 1));
     }
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    Partial acc = pidentity();
-    for (int i = tid; i < nb; i += nthr) acc = pcombine(acc, load_partial_cg(red.partials + i));
-    acc = warp_reduce(acc);
-    __syncthreads();
-    if (lane == 0) wsum[wid] = acc;
-    __syncthreads();
-    if (wid == 0) {
-        Partial q = lane < nw ? wsum[lane] : pidentity();
-        q = warp_reduce(q);
-        if (lane == 0) {
-            StatsRec *r = red.rec;
-            if (COMBINE && red.combine) {  // a further z slab of the same step
-                r->sum += q.sum;
-                r->mn = fmin(r->mn, q.mn);
-                r->mx = fmax(r->mx, q.mx);
-                r->ns += q.ns;
-                r->nt += q.nt;
-            } else {
-                r->sum = q.sum;
-                r->mn = q.mn;
-                r->mx = q.mx;
-                r->ns = q.ns;
-                r->nt = q.nt;
-            }
-            r->mass = red.dV * r->sum;
-            if (red.update_run) {
-                r->mn_run = fmin(r->mn_run, r->mn);
-                r->mx_run = fmax(r->mx_run, r->mx);
-                r->ns_run += r->ns;
-                r->nt_run += r->nt;
-                r->steps_run += 1;
-            }
-            __threadfence();
-            *red.counter = 0u;
+    const Partial q = combine_partials<F32>(red.partials, nb);
+    if (tid == 0) {
+        StatsRec *r = red.rec;
+        if (COMBINE && red.combine) {  // a further z slab of the same step
+            r->sum += q.sum;
+            r->mn = fmin(r->mn, q.mn);
+            r->mx = fmax(r->mx, q.mx);
+            r->ns += q.ns;
+            r->nt += q.nt;
+        } else {
+            r->sum = q.sum;
+            r->mn = q.mn;
+            r->mx = q.mx;
+            r->ns = q.ns;
+            r->nt = q.nt;
         }
+        r->mass = red.dV * r->sum;
+        if (red.update_run) {
+            r->mn_run = fmin(r->mn_run, r->mn);
+            r->mx_run = fmax(r->mx_run, r->mx);
+            r->ns_run += r->ns;
+            r->nt_run += r->nt;
+            r->steps_run += 1;
+        }
+        __threadfence();
+        *red.counter = 0u;
     }
+}
+
+// Block-reduce the accumulator (or an already formed per-thread Partial, in
+// double), store the block partial, and let the last block to finish combine
+// all partials into red.rec.
+template <bool COMBINE = false, typename A>
+__device__ __forceinline__ void reduce_and_finish(const A &acc, const RedScratch &red)
+{
+    finish_partial<COMBINE, IsF32<A>::value>(block_partial(acc), red);
 }
 
 // Two steps' partials of one launch (a temporally blocked pass): each is
 // block-reduced and stored (step 1 in slots [0, nb), step 2 in [nb, 2 nb)); the
 // last block to finish combines both in index order, writes the second step's
 // statistics to red.rec and folds both steps into the run accumulators.
-__device__ __forceinline__ void reduce_and_finish2(Partial p1, Partial p2, const RedScratch &red)
+template <typename A>
+__device__ __forceinline__ void reduce_and_finish2(const A &acc1, const A &acc2, const RedScratch &red)
 {
+    constexpr bool F32 = IsF32<A>::value;
     __shared__ int is_last2;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const int nthr = blockDim.x * blockDim.y * blockDim.z;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int nb = gridDim.x * gridDim.y * gridDim.z;
-    const Partial q1 = block_reduce(p1);
-    const Partial q2 = block_reduce(p2);
+    const Partial q1 = block_partial(acc1);
+    const Partial q2 = block_partial(acc2);
     if (tid == 0) {
         red.partials[bid] = q1;
         red.partials[nb + bid] = q2;
@@ -319,13 +465,8 @@ __device__ __forceinline__ void reduce_and_finish2(Partial p1, Partial p2, const
     __syncthreads();
     if (!is_last2) return;
     __threadfence();
-    Partial a1 = pidentity(), a2 = pidentity();
-    for (int i = tid; i < nb; i += nthr) {
-        a1 = pcombine(a1, load_partial_cg(red.partials + i));
-        a2 = pcombine(a2, load_partial_cg(red.partials + nb + i));
-    }
-    a1 = block_reduce(a1);
-    a2 = block_reduce(a2);
+    const Partial a1 = combine_partials<F32>(red.partials, nb);
+    const Partial a2 = combine_partials<F32>(red.partials + nb, nb);
     if (tid == 0) {
         StatsRec *r = red.rec;
         r->sum = a2.sum;
