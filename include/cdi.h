@@ -408,8 +408,9 @@ enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
  * tiles: 0..2 (32x8, 32x16, 32x4 cells) and 3 (vector), nchunks sets the z
  * chunking (CDI_NCHUNKS_BALANCED / CDI_NCHUNKS_ROTATED: balanced shares, tile 3
  * only; the vector adjoint's default takes the rotated shares where the cost
- * model favours balanced ones).  Every
- * configuration computes the same result up to the order of the reduction
+ * model favours balanced ones).  Every forward configuration (and the batch
+ * and two-steps-per-pass paths) computes the same field bit for bit; the
+ * statistics' sum may differ in its last bits with the order of the block
  * partials. */
 CDI_API int cdi_set_launch(cdi_grid *g, int which, int tile, int blocks_per_sm, int nchunks);
 

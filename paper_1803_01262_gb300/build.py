@@ -27,11 +27,21 @@ LIB_CHECKED = os.path.join(OUT_DIR, "libcdi_checked.so")
 SOURCES = ["cdi_fwd.cu", "cdi_fwd_tma.cu", "cdi_fwd_tb.cu", "cdi_adj.cu", "cdi_batch.cu", "cdi_api.cu",
            "cdi_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# The forward step flushes FP32 denormals (values below 1.2e-38) to zero; this
-# removes denormal handling around rsqrtf and is far below every tolerance.
-PER_FILE = {"cdi_fwd.cu": ["-ftz=true"], "cdi_fwd_tma.cu": ["-ftz=true"], "cdi_fwd_tb.cu": ["-ftz=true"]}
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
-         "-I", INCLUDE, "-I", CSRC]
+# The step kernels (single grid and batch) flush FP32 denormals (values below
+# 1.2e-38) to zero; this removes denormal handling around rsqrtf and is far below
+# every tolerance.
+PER_FILE = {"cdi_fwd.cu": ["-ftz=true"], "cdi_fwd_tma.cu": ["-ftz=true"], "cdi_fwd_tb.cu": ["-ftz=true"],
+            "cdi_batch.cu": ["-ftz=true"]}
+# No contraction of a product and a sum into a fused multiply-add beyond the fma()
+# calls the sources write: the compiler's choice differs between the places an
+# expression is inlined (a work unit's prologue and the steady plane loop, one
+# tile shape and another), so with contraction the same cell came out one unit
+# in the last place apart under different tiles and work splits; without it every
+# configuration computes the same bits (and runs as fast).  The adjoint, whose
+# configurations promise no such agreement, keeps contraction (4% faster with it).
+CONTRACT = {"cdi_adj.cu"}
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler",
+         "-fvisibility=hidden", "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:
@@ -74,7 +84,8 @@ def build(force: bool = False, ptxas_verbose: bool = False, verbose: bool = Fals
 
     def compile_one(src):
         obj = os.path.join(obj_dir, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *defs, *PER_FILE.get(src, []), *extra, "-c", os.path.join(CSRC, src),
+        fmad = "-fmad=true" if src in CONTRACT else "-fmad=false"
+        cmd = [cc, *ARCH, *FLAGS, fmad, *defs, *PER_FILE.get(src, []), *extra, "-c", os.path.join(CSRC, src),
                "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         return src, obj, r

@@ -403,31 +403,49 @@ __device__ __forceinline__ void finish_partial(const Partial &p, const RedScratc
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    const Partial q = combine_partials<F32>(red.partials, nb);
+    // The record's fields that are read back, fetched before the combination so
+    // that their latency overlaps it.  (The grid's completion publishes the
+    // record and the counter reset to the next launch; no fence is needed.)
+    StatsRec *r = red.rec;
+    StatsRec o;
     if (tid == 0) {
-        StatsRec *r = red.rec;
-        if (COMBINE && red.combine) {  // a further z slab of the same step
-            r->sum += q.sum;
-            r->mn = fmin(r->mn, q.mn);
-            r->mx = fmax(r->mx, q.mx);
-            r->ns += q.ns;
-            r->nt += q.nt;
-        } else {
-            r->sum = q.sum;
-            r->mn = q.mn;
-            r->mx = q.mx;
-            r->ns = q.ns;
-            r->nt = q.nt;
+        if (COMBINE && red.combine) {
+            o.sum = __ldcg(&r->sum);
+            o.mn = __ldcg(&r->mn);
+            o.mx = __ldcg(&r->mx);
+            o.ns = __ldcg(&r->ns);
+            o.nt = __ldcg(&r->nt);
         }
-        r->mass = red.dV * r->sum;
         if (red.update_run) {
-            r->mn_run = fmin(r->mn_run, r->mn);
-            r->mx_run = fmax(r->mx_run, r->mx);
-            r->ns_run += r->ns;
-            r->nt_run += r->nt;
-            r->steps_run += 1;
+            o.mn_run = __ldcg(&r->mn_run);
+            o.mx_run = __ldcg(&r->mx_run);
+            o.ns_run = __ldcg(&r->ns_run);
+            o.nt_run = __ldcg(&r->nt_run);
+            o.steps_run = __ldcg(&r->steps_run);
         }
-        __threadfence();
+    }
+    Partial q = combine_partials<F32>(red.partials, nb);
+    if (tid == 0) {
+        if (COMBINE && red.combine) {  // a further z slab of the same step
+            q.sum += o.sum;
+            q.mn = fmin(o.mn, q.mn);
+            q.mx = fmax(o.mx, q.mx);
+            q.ns += o.ns;
+            q.nt += o.nt;
+        }
+        r->sum = q.sum;
+        r->mn = q.mn;
+        r->mx = q.mx;
+        r->ns = q.ns;
+        r->nt = q.nt;
+        r->mass = red.dV * q.sum;
+        if (red.update_run) {
+            r->mn_run = fmin(o.mn_run, q.mn);
+            r->mx_run = fmax(o.mx_run, q.mx);
+            r->ns_run = o.ns_run + q.ns;
+            r->nt_run = o.nt_run + q.nt;
+            r->steps_run = o.steps_run + 1;
+        }
         *red.counter = 0u;
     }
 }
@@ -465,10 +483,18 @@ __device__ __forceinline__ void reduce_and_finish2(const A &acc1, const A &acc2,
     __syncthreads();
     if (!is_last2) return;
     __threadfence();
+    StatsRec *r = red.rec;
+    StatsRec o;
+    if (tid == 0 && red.update_run) {  // fetched early, as in finish_partial
+        o.mn_run = __ldcg(&r->mn_run);
+        o.mx_run = __ldcg(&r->mx_run);
+        o.ns_run = __ldcg(&r->ns_run);
+        o.nt_run = __ldcg(&r->nt_run);
+        o.steps_run = __ldcg(&r->steps_run);
+    }
     const Partial a1 = combine_partials<F32>(red.partials, nb);
     const Partial a2 = combine_partials<F32>(red.partials + nb, nb);
     if (tid == 0) {
-        StatsRec *r = red.rec;
         r->sum = a2.sum;
         r->mn = a2.mn;
         r->mx = a2.mx;
@@ -476,13 +502,12 @@ __device__ __forceinline__ void reduce_and_finish2(const A &acc1, const A &acc2,
         r->nt = a2.nt;
         r->mass = red.dV * a2.sum;
         if (red.update_run) {
-            r->mn_run = fmin(r->mn_run, fmin(a1.mn, a2.mn));
-            r->mx_run = fmax(r->mx_run, fmax(a1.mx, a2.mx));
-            r->ns_run += a1.ns + a2.ns;
-            r->nt_run += a1.nt + a2.nt;
-            r->steps_run += 2;
+            r->mn_run = fmin(o.mn_run, fmin(a1.mn, a2.mn));
+            r->mx_run = fmax(o.mx_run, fmax(a1.mx, a2.mx));
+            r->ns_run = o.ns_run + a1.ns + a2.ns;
+            r->nt_run = o.nt_run + a1.nt + a2.nt;
+            r->steps_run = o.steps_run + 2;
         }
-        __threadfence();
         *red.counter = 0u;
     }
 }
