@@ -522,12 +522,22 @@ static cdi::StepCoef<T> coefs(const cdi_grid *g, double dt, double eps, double g
     return c;
 }
 
+// Deferred finish of consecutive steps of a run: the step's block partials go to
+// scratch slot `slot` (two slots of nblocks partials); with `defer` they are
+// left for the next step, whose block 0 finishes them (`finish_prev`: the other
+// slot's partials, of the previous step) while the next step's blocks work.
+struct DeferCfg {
+    int slot;
+    bool defer;
+    bool finish_prev;
+};
+
 // One forward step, or (z_hi > 0) its planes [z_lo, z_hi) folded into the record:
 // combine adds to the record's per-step fields, update_run closes the step.
 template <typename T>
 static int step_t(cdi_grid *g, const void *in, void *out, double dt, double eps, double gamma,
                   double vs, cudaStream_t s, int z_lo = 0, int z_hi = 0, int combine = 0,
-                  int update_run = 1)
+                  int update_run = 1, const DeferCfg *dfr = nullptr)
 {
     cdi::FwdArgs<T> a;
     a.phi = (const T *)in;
@@ -548,6 +558,17 @@ static int step_t(cdi_grid *g, const void *in, void *out, double dt, double eps,
     const LaunchCfg &c = z_hi > 0 ? g->slab : g->fwd;
     if (c.nblocks > g->capacity)
         return fail(CDI_ERR_STATE, "launch configuration exceeds the reduction scratch");
+    if (dfr) {
+        if (2 * c.nblocks > g->capacity)
+            return fail(CDI_ERR_STATE, "deferred finish needs two partial slots per block");
+        a.red.partials = g->partials + (size_t)dfr->slot * c.nblocks;
+        a.red.defer = dfr->defer;
+        if (dfr->finish_prev) {
+            a.red.prev = g->partials + (size_t)(1 - dfr->slot) * c.nblocks;
+            a.red.prev_nb = c.nblocks;
+            a.red.prev_update_run = update_run;
+        }
+    }
     cudaError_t e = cdi::launch_fwd<T>(a, c.tile, c.nblocks, c.nchunks, false, s,
                                        g->sharpen == CDI_SHARPEN_FACE);
     if (e != cudaSuccess) return cuda_fail(e, "forward step launch");
@@ -797,6 +818,10 @@ int cdi_run(cdi_grid *g, void *buf_a, void *buf_b, int nsteps, double t0, double
     cudaStream_t s = (cudaStream_t)stream;
     void *src = buf_a, *dst = buf_b;
     const bool two = g->run_depth == 2 && g->sharpen == CDI_SHARPEN_CENTRE;
+    // one step per launch: each step's statistics are finished by the next step's
+    // block 0 (the last step finishes its own), taking the combination of the block
+    // partials off the end of every step but the last
+    const bool defer = !two && nsteps > 1 && 2 * g->fwd.nblocks <= g->capacity;
     for (int i = 0; i < nsteps;) {
         const double t = t0 + i * dt;
         const double vs = period > 0 ? cos(M_PI * t / period) : 1.0;
@@ -807,8 +832,10 @@ int cdi_run(cdi_grid *g, void *buf_a, void *buf_b, int nsteps, double t0, double
                                      : step2_t<float>(g, src, dst, dt, eps, gamma, vs, vs2, s);
             i += 2;
         } else {
-            rc = g->dtype == CDI_F64 ? step_t<double>(g, src, dst, dt, eps, gamma, vs, s)
-                                     : step_t<float>(g, src, dst, dt, eps, gamma, vs, s);
+            const DeferCfg d = {i & 1, i + 1 < nsteps, i > 0};
+            const DeferCfg *dp = defer ? &d : nullptr;
+            rc = g->dtype == CDI_F64 ? step_t<double>(g, src, dst, dt, eps, gamma, vs, s, 0, 0, 0, 1, dp)
+                                     : step_t<float>(g, src, dst, dt, eps, gamma, vs, s, 0, 0, 0, 1, dp);
             i += 1;
         }
         if (rc) return rc;

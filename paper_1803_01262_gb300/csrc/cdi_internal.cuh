@@ -40,6 +40,13 @@ struct RedScratch {
     unsigned int *status;   // nullable: the status words (kStatusWords, below)
     int combine = 0;        // 1: add this launch's result to the record's per-step fields
                             //    (a step done in several launches over z slabs)
+    // Deferred finish (consecutive steps of a run): a launch with defer = 1 only
+    // stores its block partials; the next launch's block 0 combines them into the
+    // record (prev, prev_nb, prev_update_run), off the critical path of both.
+    int defer = 0;
+    const Partial *prev = nullptr;
+    int prev_nb = 0;
+    int prev_update_run = 0;
 };
 
 // Coefficients of one step, precomputed on the host in double and cast.

@@ -382,30 +382,17 @@ __device__ __forceinline__ Partial combine_partials(const Partial *parts, int n)
 template <typename A> struct IsF32 { static constexpr bool value = false; };
 template <> struct IsF32<Acc<float>> { static constexpr bool value = true; };
 
-// Store the block's partial p (valid in thread 0) and let the last block to
-// finish combine all partials in index order into red.rec.  Every thread of
-// the block calls this; the block size must be a multiple of 32.
-// COMBINE: the launch may be a further z slab of a step (red.combine); only the
-// slab kernels are built with it.
+// Combine parts[0, n) (every thread of the block; fixed order) into red.rec:
+// the step's fields (added to the record's with COMBINE and red.combine, a
+// further z slab of the same step), and with update_run the run accumulators.
 template <bool COMBINE, bool F32>
-__device__ __forceinline__ void finish_partial(const Partial &p, const RedScratch &red)
+__device__ __forceinline__ void finish_record(const Partial *parts, int n, const RedScratch &red,
+                                              int update_run)
 {
-    __shared__ int is_last;
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-    const int nb = gridDim.x * gridDim.y * gridDim.z;
-    if (tid == 0) {
-        red.partials[bid] = p;
-        __threadfence();
-        const unsigned prev = atomicAdd(red.counter, 1u);
-        is_last = (prev == (unsigned)(nb - 1));
-    }
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
     // The record's fields that are read back, fetched before the combination so
     // that their latency overlaps it.  (The grid's completion publishes the
-    // record and the counter reset to the next launch; no fence is needed.)
+    // record to the next launch; no fence is needed.)
     StatsRec *r = red.rec;
     StatsRec o;
     if (tid == 0) {
@@ -416,7 +403,7 @@ __device__ __forceinline__ void finish_partial(const Partial &p, const RedScratc
             o.ns = __ldcg(&r->ns);
             o.nt = __ldcg(&r->nt);
         }
-        if (red.update_run) {
+        if (update_run) {
             o.mn_run = __ldcg(&r->mn_run);
             o.mx_run = __ldcg(&r->mx_run);
             o.ns_run = __ldcg(&r->ns_run);
@@ -424,9 +411,9 @@ __device__ __forceinline__ void finish_partial(const Partial &p, const RedScratc
             o.steps_run = __ldcg(&r->steps_run);
         }
     }
-    Partial q = combine_partials<F32>(red.partials, nb);
+    Partial q = combine_partials<F32>(parts, n);
     if (tid == 0) {
-        if (COMBINE && red.combine) {  // a further z slab of the same step
+        if (COMBINE && red.combine) {
             q.sum += o.sum;
             q.mn = fmin(o.mn, q.mn);
             q.mx = fmax(o.mx, q.mx);
@@ -439,15 +426,47 @@ __device__ __forceinline__ void finish_partial(const Partial &p, const RedScratc
         r->ns = q.ns;
         r->nt = q.nt;
         r->mass = red.dV * q.sum;
-        if (red.update_run) {
+        if (update_run) {
             r->mn_run = fmin(o.mn_run, q.mn);
             r->mx_run = fmax(o.mx_run, q.mx);
             r->ns_run = o.ns_run + q.ns;
             r->nt_run = o.nt_run + q.nt;
             r->steps_run = o.steps_run + 1;
         }
-        *red.counter = 0u;
     }
+}
+
+// Store the block's partial p (valid in thread 0) and let the last block to
+// finish combine all partials in index order into red.rec.  Every thread of
+// the block calls this; the block size must be a multiple of 32.
+// COMBINE: the launch may be a further z slab of a step (red.combine); only the
+// slab kernels are built with it.  With red.prev, block 0 first finishes the
+// previous launch's deferred partials (whose grid has completed: every kernel
+// reaches this point after its dependency wait); with red.defer the partials
+// are only stored, for the next launch to finish.
+template <bool COMBINE, bool F32>
+__device__ __forceinline__ void finish_partial(const Partial &p, const RedScratch &red)
+{
+    __shared__ int is_last;
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (red.prev && bid == 0) finish_record<false, F32>(red.prev, red.prev_nb, red, red.prev_update_run);
+    if (red.defer) {
+        if (tid == 0) red.partials[bid] = p;
+        return;
+    }
+    if (tid == 0) {
+        red.partials[bid] = p;
+        __threadfence();  // also orders block 0's record writes above before its arrival
+        const unsigned prev = atomicAdd(red.counter, 1u);
+        is_last = (prev == (unsigned)(nb - 1));
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    finish_record<COMBINE, F32>(red.partials, nb, red, red.update_run);
+    if (tid == 0) *red.counter = 0u;
 }
 
 // Block-reduce the accumulator (or an already formed per-thread Partial, in

@@ -97,3 +97,39 @@ def test_batch_box_sums_are_exact():
         for i, p in enumerate(ps):
             assert torch.equal(b.current(i).cpu(), torch.from_numpy(p).float()), (tile, i)
             check_exact(st[i], p)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("tile,nchunks", [(4, cdi.CDI_NCHUNKS_ROTATED), (4, 3), (0, 1), (6, 0)])
+@pytest.mark.parametrize("nsteps", [1, 2, 3, 6])
+def test_run_statistics_equal_stepwise(dtype, tile, nchunks, nsteps):
+    """cdi_run finishes each step's statistics in the next step's launch (the last step its
+    own); the record and the run accumulators equal those of the same steps taken one
+    cdi_step at a time, bit for bit.  Planted values outside [0, 1] make the violation
+    counts take part."""
+    shape = (24, 32, 128)
+    nz, ny, nx = shape
+    h = 1.0 / max(shape)
+    p0 = I.random_phi(shape, 8, smooth=True)
+    p0[2:7, 4:9, 6:11], p0[17:22, 26:31, 97:102] = -0.3, 1.4   # blocks outlive a few steps
+    phi = torch.from_numpy(p0).to("cuda", dtype)
+    vel = [torch.from_numpy(x).to("cuda", dtype) for x in I.random_velocity(shape, h, 8, 3, 9)]
+    g = cdi.Grid(nx, ny, nz, h, dtype)
+    g.set_velocity(*vel)
+    g.set_launch(cdi.CDI_KERNEL_FORWARD, tile, 0, nchunks)
+    eps, gamma = h, 1.0
+    dt = 0.1 * h * h / (gamma * eps)
+    g.reset_run_stats()
+    out_run = g.run(phi.clone(), torch.empty_like(phi), nsteps, dt, eps, gamma, period=0.7, t0=0.05).clone()
+    s_run = g.stats()
+    g.reset_run_stats()
+    p, q = phi.clone(), torch.empty_like(phi)
+    for i in range(nsteps):
+        g.step(p, q, dt, eps, gamma, float(np.cos(np.pi * (0.05 + i * dt) / 0.7)))
+        p, q = q, p
+    s_steps = g.stats()
+    assert torch.equal(out_run, p)
+    assert s_steps["n_strict_run"] > 0
+    for k in ("mass", "sum", "min", "max", "n_strict", "n_tol", "min_run", "max_run", "n_strict_run",
+              "n_tol_run", "steps_run"):
+        assert s_run[k] == s_steps[k], (k, s_run[k], s_steps[k])
