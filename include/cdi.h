@@ -321,6 +321,15 @@ CDI_API int cdi_batch_get_sharpening(const cdi_batch *b, int *mode);
  * 1024 cells wide: each plane's band and halo rows are one contiguous run of
  * the array, staged by 16-byte copies whatever the row alignment; the fields
  * are those of tiles 0..3 bit for bit.  CDI_ERR_ARG where it does not apply.
+ * Tile 6 = bands of whole rows of the batch's own padded copy of every box
+ * (rows padded to 16-byte multiples with periodic ghost cells at both ends,
+ * allocated on first use: 5 arrays of the padded box size): 16-byte copies and
+ * 16-byte shared loads of four (FP32) or two (FP64) cells per thread whatever
+ * nx is.  Each step or run call first copies the caller's current state into
+ * the padded copy and its last step also writes the caller's array, so the
+ * caller's buffers behave as for the other tiles; rows of at most 400 (FP32)
+ * or 200 (FP64) cells.  Centre-form sharpening only; the fields
+ * are those of tiles 0..3 bit for bit.
  * tile = -1 / zdepth = -1 restore the defaults (32x8, CDI_BATCH_DEFAULT_ZDEPTH).
  * Rebuilds the work list (synchronises the device; drops captured graphs). */
 #define CDI_BATCH_DEFAULT_ZDEPTH 32

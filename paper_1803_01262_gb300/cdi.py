@@ -34,7 +34,7 @@ CDI_SHARPEN_CENTRE, CDI_SHARPEN_FACE = 0, 1
 SHARPEN = {"centre": CDI_SHARPEN_CENTRE, "face": CDI_SHARPEN_FACE}
 FWD_TILES = 7
 ADJ_TILES = 4
-BATCH_TILES = 6
+BATCH_TILES = 7
 
 _ERRNAMES = {-1: "CDI_ERR_ARG", -2: "CDI_ERR_DIM", -3: "CDI_ERR_CUDA", -4: "CDI_ERR_CONDITION",
              -5: "CDI_ERR_NAN", -6: "CDI_ERR_TIMEOUT", -7: "CDI_ERR_STATE", -8: "CDI_ERR_BOUNDS"}
@@ -476,7 +476,8 @@ class Batch:
     def set_launch(self, tile=-1, zdepth=-1):
         """Work-unit tile (0..3: 32x8, 32x16, 64x8, 32x4; 4: one unit per whole 2D box, for
         batches of 2D boxes whose planes fit in shared memory; 5: bands of whole rows, for
-        batches with 3D boxes of nx <= 1024) and planes per unit (0: whole box)."""
+        batches with 3D boxes of nx <= 1024; 6: bands of whole rows of the batch's padded
+        copies, 16-byte vectors of cells per thread) and planes per unit (0: whole box)."""
         _ck(lib().cdi_batch_set_launch(self._h, tile, zdepth))
 
     def set_sharpening(self, mode):

@@ -26,6 +26,7 @@
 
 #include "cdi.h"
 #include "cdi_band.cuh"
+#include "cdi_vband.cuh"
 #include "cdi_fwd_scalar.cuh"
 #include "cdi_internal.cuh"
 #include "cdi_nvtx.h"
@@ -38,7 +39,12 @@ struct BoxDev {
     FwdArgs<T> a;     // phi = phi_a, out = phi_b; coefficients for vel_scale = 1
     double dV;        // cell measure dx^D_f
     int tiles_x, ntiles, zc, unit0, nunits;
-    int bh;           // row-band body: rows per band
+    int bh;           // row-band bodies: rows per band
+    // vector row-band body: the batch's padded copies (pitch P, cdi_vband.cuh):
+    // the state by parity, and the face velocities
+    T *pad[2];
+    const T *pu, *pv, *pw;
+    int pitch;
 };
 
 // Whole-plane unit body: the unit is a whole 2D box (nz == 1) whose phi and
@@ -124,12 +130,15 @@ __device__ __forceinline__ void plane_unit(const FwdArgs<T> &a, Acc<T> &acc, uns
 // stages the plane once (flat_unit).  BODY 2: every box has nz == 1 and fits
 // in shared memory: one unit per box, the whole-plane body (plane_unit).
 // BODY 3: bands of whole rows (band_unit, cdi_band.cuh), slots of sizes bs.
+// BODY 4: bands of whole rows of the padded copies (vband_unit, cdi_vband.cuh),
+// slots of sizes vbs; final_write: the step also writes the caller's arrays.
 // FACE: the face-product sharpening (bodies 0, 1 and 2).
 template <typename T, int BX, int BY, int BODY = 0, bool FACE = false>
-__global__ void __launch_bounds__(BX * BY, BODY == 3 ? 2 : 1)
+__global__ void __launch_bounds__(BX * BY, BODY >= 3 ? 2 : 1)
 batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_box,
              const int total_units, const int parity, const T vs, Partial *partials,
-             unsigned int *box_done, StatsRec *recs, const BandSlots bs)
+             unsigned int *box_done, StatsRec *recs, const BandSlots bs, const VbandSlots vbs,
+             const int final_write)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int fold;
@@ -154,6 +163,13 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
             const int hb = min(boxes[bi].bh, a.ny - y0);
             const int z0 = chunk * zc;
             band_unit<T>(a, y0, hb, z0, min(a.nz, z0 + zc), bs, acc, smem_raw);
+        } else if constexpr (BODY == 4) {
+            const BoxDev<T> &bx = boxes[bi];
+            const int lu = u - bx.unit0, nb = bx.ntiles, zc = bx.zc;
+            const int chunk = lu / nb, band = lu - chunk * nb;
+            const int z0 = chunk * zc;
+            vband_unit<T>(a, bx.pad[parity], bx.pad[parity ^ 1], bx.pu, bx.pv, bx.pw, bx.pitch, final_write != 0,
+                          band * bx.bh, bx.bh, z0, min(a.nz, z0 + zc), vbs, acc, smem_raw);
         } else {
             const int lu = u - boxes[bi].unit0;
             const Unit un = unit_of(lu, boxes[bi].ntiles, boxes[bi].tiles_x, BX, BY, boxes[bi].zc, a.nz);
@@ -195,12 +211,30 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
     }
 }
 
+// Fill a box's padded copy (cdi_vband.cuh) from a caller's array: position p of
+// a padded row holds the row's cell (p - VX) mod nx.  blockIdx.y: the box.
+// which: 0, 1 the state of that parity (from phi_a / phi_b), 2, 3, 4 u, v, w.
+template <typename T>
+__global__ void __launch_bounds__(256) vband_pack(const BoxDev<T> *__restrict__ boxes, int which)
+{
+    constexpr int VX = 16 / sizeof(T);
+    const BoxDev<T> &bx = boxes[blockIdx.y];
+    const FwdArgs<T> &a = bx.a;
+    const T *src = which == 0 ? a.phi : which == 1 ? a.out : which == 2 ? a.u : which == 3 ? a.v : a.w;
+    T *dst = which <= 1 ? bx.pad[which] : const_cast<T *>(which == 2 ? bx.pu : which == 3 ? bx.pv : bx.pw);
+    const int nx = a.nx, P = bx.pitch;
+    const long long rows = (long long)a.ny * a.nz;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x)
+        for (int p = threadIdx.x; p < P; p += 256) dst[row * P + p] = src[row * nx + wrapi(p - VX, nx)];
+}
+
 // Batch tiles 0..3: the scalar tiles of the single-box kernel; tile 4: one
 // unit per whole 2D box (plane_unit, PLANE_NT threads); tile 5: bands of whole
 // rows (band_unit, BAND_NT threads).
-constexpr int BATCH_TILES = 6;
+constexpr int BATCH_TILES = 7;
 constexpr int BATCH_TILE_PLANE = 4;
 constexpr int BATCH_TILE_BAND = 5;
+constexpr int BATCH_TILE_VBAND = 6;
 constexpr int PLANE_NT = 256;
 static const int batch_tile_dims[4][2] = {{32, 8}, {32, 16}, {64, 8}, {32, 4}};
 
@@ -218,6 +252,10 @@ struct cdi_batch {
     int sharpen;               // CDI_SHARPEN_CENTRE or CDI_SHARPEN_FACE (tiles 0 and 4 only)
     BandSlots band;            // row-band body: slot sizes for the largest box
     size_t band_bytes;         // its shared memory (0: the band body does not apply)
+    cdi::VbandSlots vband;     // vector row-band body (tile 6): slot sizes for the largest box
+    size_t vband_bytes;        // its shared memory (0: it does not apply)
+    void *padbuf;              // tile 6: the padded copies of every box (allocated on first use)
+    bool vel_packed;           // the padded face velocities are filled
     std::vector<cdi_box_desc> desc;
     void *boxes_dev;           // BoxDev<T>[nbox]
     int *unit_box;             // [unit_cap]
@@ -283,6 +321,20 @@ static size_t band_limit()
     return ((size_t)optin - fa.sharedSizeBytes) & ~(size_t)15;
 }
 
+// Largest dynamic shared memory the vector band kernel can launch with.
+template <typename T>
+static size_t vband_limit()
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, cdi::batch_kernel<T, cdi::VBAND_NT, 1, 4>) != cudaSuccess ||
+        (size_t)optin <= fa.sharedSizeBytes)
+        return 0;
+    return ((size_t)optin - fa.sharedSizeBytes) & ~(size_t)15;
+}
+
 template <typename T>
 static cudaError_t batch_occ(const cdi_batch *b, int tile, int *resident)
 {
@@ -298,6 +350,15 @@ static cudaError_t batch_occ(const cdi_batch *b, int tile, int *resident)
         if (e != cudaSuccess) return e;
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2, true>,
                                                              cdi::PLANE_NT, b->plane_bytes);
+    }
+    if (tile == cdi::BATCH_TILE_VBAND) {
+        const size_t lim = vband_limit<T>();
+        if (lim == 0 || b->vband_bytes == 0 || b->vband_bytes > lim) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(cdi::batch_kernel<T, cdi::VBAND_NT, 1, 4>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, cdi::batch_kernel<T, cdi::VBAND_NT, 1, 4>,
+                                                             cdi::VBAND_NT, b->vband_bytes);
     }
     if (tile == cdi::BATCH_TILE_BAND) {
         const size_t lim = band_limit<T>();
@@ -381,6 +442,43 @@ static size_t band_bytes(cdi_batch *b)
     return b->dtype == CDI_F64 ? band_bytes_t<double>(b) : band_bytes_t<float>(b);
 }
 
+// Slot sizes of the vector band body for this batch (each slot field the largest
+// over its boxes, the velocity regions laid out one after another) and their
+// shared memory; 0 if they exceed the shared memory of one block.
+template <typename T>
+static size_t vband_bytes_t(cdi_batch *b)
+{
+    const int vx = 16 / (int)sizeof(T);
+    int phi = 0, ur = 0, vr = 0, sx = 0, sy = 0;
+    for (const cdi_box_desc &x : b->desc) {
+        if ((x.nx + vx - 1) / vx > cdi::VBAND_NT) return 0;  // a row has more groups than the block threads
+        const int P = cdi::vband_pitch(x.nx, vx), hb = cdi::vband_rows(x.nx, x.ny, vx);
+        if (hb < 1) return 0;  // a padded row too wide for the staging plan
+        const cdi::VbandSlots t = cdi::vband_slots(P, hb);
+        phi = std::max(phi, t.phi);
+        ur = std::max(ur, hb * P);
+        vr = std::max(vr, (hb + 1) * P);
+        sx = std::max(sx, t.sx);
+        sy = std::max(sy, t.sy);
+    }
+    cdi::VbandSlots s;
+    s.phi = phi;
+    s.vo = ur;
+    s.wo = ur + vr;
+    s.vel = 2 * ur + vr;
+    s.sx = sx;
+    s.sy = sy;
+    const size_t need = cdi::vband_smem_bytes(s, sizeof(T));
+    if (need > vband_limit<T>()) return 0;
+    b->vband = s;
+    return need;
+}
+
+static size_t vband_bytes(cdi_batch *b)
+{
+    return b->dtype == CDI_F64 ? vband_bytes_t<double>(b) : vband_bytes_t<float>(b);
+}
+
 static int batch_free(cdi_batch *b)
 {
     if (!b) return CDI_OK;
@@ -392,6 +490,7 @@ static int batch_free(cdi_batch *b)
     cudaFree(b->box_done);
     cudaFree(b->recs);
     cudaFree(b->status);
+    cudaFree(b->padbuf);
     delete b;
     return CDI_OK;
 }
@@ -408,13 +507,31 @@ template <typename T>
 static int build_units(cdi_batch *b, int tile, int zdepth)
 {
     const bool plane = tile == cdi::BATCH_TILE_PLANE, band = tile == cdi::BATCH_TILE_BAND;
+    const bool vband = tile == cdi::BATCH_TILE_VBAND;
+    constexpr int VX = 16 / sizeof(T);
     if (plane && b->plane_bytes == 0)
         return cdi::set_error(CDI_ERR_ARG, "batch tile 4 needs 2D boxes (nz = 1) whose planes fit in shared memory");
     if (band && b->band_bytes == 0)
         return cdi::set_error(CDI_ERR_ARG, "batch tile 5 needs a batch with 3D boxes whose rows fit in a band "
                                            "(nx <= %d) and whose band slots fit in shared memory", cdi::BAND_CELLS);
-    const int bw = plane || band ? 1 : cdi::batch_tile_dims[tile][0];
-    const int bh = plane || band ? 1 : cdi::batch_tile_dims[tile][1];
+    if (vband && b->vband_bytes == 0)
+        return cdi::set_error(CDI_ERR_ARG, "batch tile 6 needs padded rows of at most %d vectors and band "
+                                           "slots that fit in the shared memory of a block",
+                                           cdi::VBAND_CPY * cdi::VBAND_NT / 5);
+    cudaError_t e;
+    if (vband && !b->padbuf) {  // the padded copies: state x 2, u, v, w per box
+        size_t n = 0;
+        for (const cdi_box_desc &x : b->desc) n += 5 * (size_t)cdi::vband_pitch(x.nx, VX) * x.ny * x.nz;
+        if ((e = cudaMalloc(&b->padbuf, n * sizeof(T))) != cudaSuccess) {
+            b->padbuf = nullptr;
+            return cdi::set_error(CDI_ERR_CUDA, "batch padded copies (%zu bytes): %s", n * sizeof(T),
+                                  cudaGetErrorString(e));
+        }
+        b->vel_packed = false;
+    }
+    const int bw = plane || band || vband ? 1 : cdi::batch_tile_dims[tile][0];
+    const int bh = plane || band || vband ? 1 : cdi::batch_tile_dims[tile][1];
+    T *pad = (T *)b->padbuf;
     std::vector<BoxDev<T>> tab;
     std::vector<int> ub;
     int unit = 0;
@@ -437,11 +554,25 @@ static int build_units(cdi_batch *b, int tile, int zdepth)
         e.a.red.status = b->status;
         const int Df = (x.nx > 1) + (x.ny > 1) + (x.nz > 1);
         e.dV = pow(x.dx, (double)Df);
-        e.tiles_x = plane || band ? 1 : (x.nx + bw - 1) / bw;
+        e.tiles_x = plane || band || vband ? 1 : (x.nx + bw - 1) / bw;
         e.ntiles = plane ? 1 : e.tiles_x * ((x.ny + bh - 1) / bh);  // whole-plane body: one unit per box
         if (band) {  // bands of whole rows
             e.bh = cdi::band_rows(x.nx, x.ny);
             e.ntiles = (x.ny + e.bh - 1) / e.bh;
+        }
+        if (vband) {  // bands of whole padded rows
+            e.bh = cdi::vband_rows(x.nx, x.ny, VX);
+            e.ntiles = (x.ny + e.bh - 1) / e.bh;
+        }
+        if (pad) {  // the padded copies (laid out box after box)
+            e.pitch = cdi::vband_pitch(x.nx, VX);
+            const size_t n = (size_t)e.pitch * x.ny * x.nz;
+            e.pad[0] = pad;
+            e.pad[1] = pad + n;
+            e.pu = pad + 2 * n;
+            e.pv = pad + 3 * n;
+            e.pw = pad + 4 * n;
+            pad += 5 * n;
         }
         int nch = zdepth > 0 && !plane ? (x.nz + zdepth / 2) / zdepth : 1;  // about zdepth planes per unit
         if (nch < 1) nch = 1;
@@ -455,7 +586,7 @@ static int build_units(cdi_batch *b, int tile, int zdepth)
         tab.push_back(e);
     }
     int resident = 0;
-    cudaError_t e = batch_occ<T>(b, tile, &resident);
+    e = batch_occ<T>(b, tile, &resident);
     if (e != cudaSuccess) return cdi::set_error(CDI_ERR_CUDA, "batch occupancy: %s", cudaGetErrorString(e));
     if (resident < 1) return cdi::set_error(CDI_ERR_CUDA, "batch kernel does not fit on an SM");
     if (ub.size() > b->unit_cap) {
@@ -476,6 +607,13 @@ static int build_units(cdi_batch *b, int tile, int zdepth)
         (e = cudaMemcpy(b->boxes_dev, tab.data(), sizeof(BoxDev<T>) * b->nbox, cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(b->unit_box, ub.data(), sizeof(int) * ub.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return cdi::set_error(CDI_ERR_CUDA, "batch tables: %s", cudaGetErrorString(e));
+    if (vband && !b->vel_packed) {  // the face velocities do not change: padded once
+        for (int which = 2; which <= 4; ++which)
+            cdi::vband_pack<T><<<dim3(256, b->nbox), 256>>>((const BoxDev<T> *)b->boxes_dev, which);
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess)
+            return cdi::set_error(CDI_ERR_CUDA, "batch padded velocities: %s", cudaGetErrorString(e));
+        b->vel_packed = true;
+    }
     long long nb = (long long)resident * b->sms;
     if (nb > unit) nb = unit;
     if (nb < 1) nb = 1;
@@ -500,21 +638,21 @@ static void batch_launch_one(cdi_batch *b, int parity, double vs, cudaStream_t s
         if (b->flat)
             cdi::batch_kernel<T, 32, 8, 1, true><<<b->nblocks, dim3(32, 8), cdi::FwdSmem<T, 32, 8>::bytes, s>>>(
                 (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-                b->box_done, b->recs, b->band);
+                b->box_done, b->recs, b->band, b->vband, 0);
         else
             cdi::batch_kernel<T, 32, 8, 0, true><<<b->nblocks, dim3(32, 8), cdi::FwdSmem<T, 32, 8>::bytes, s>>>(
                 (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-                b->box_done, b->recs, b->band);
+                b->box_done, b->recs, b->band, b->vband, 0);
         return;
     }
     if (b->flat)
         cdi::batch_kernel<T, BX, BY, 1><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
             (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-            b->box_done, b->recs, b->band);
+            b->box_done, b->recs, b->band, b->vband, 0);
     else
         cdi::batch_kernel<T, BX, BY, 0><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
             (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-            b->box_done, b->recs, b->band);
+            b->box_done, b->recs, b->band, b->vband, 0);
 }
 
 template <typename T>
@@ -523,12 +661,12 @@ static void batch_launch_plane(cdi_batch *b, int parity, double vs, cudaStream_t
     if (b->sharpen == CDI_SHARPEN_FACE) {
         cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2, true><<<b->nblocks, dim3(cdi::PLANE_NT, 1), b->plane_bytes, s>>>(
             (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-            b->recs, b->band);
+            b->recs, b->band, b->vband, 0);
         return;
     }
     cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2><<<b->nblocks, dim3(cdi::PLANE_NT, 1), b->plane_bytes, s>>>(
         (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-        b->recs, b->band);
+        b->recs, b->band, b->vband, 0);
 }
 
 template <typename T>
@@ -536,11 +674,33 @@ static void batch_launch_band(cdi_batch *b, int parity, double vs, cudaStream_t 
 {
     cdi::batch_kernel<T, cdi::BAND_NT, 1, 3><<<b->nblocks, dim3(cdi::BAND_NT, 1), b->band_bytes, s>>>(
         (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-        b->recs, b->band);
+        b->recs, b->band, b->vband, 0);
 }
 
 template <typename T>
-static int batch_launch(cdi_batch *b, int parity, double vs, cudaStream_t s)
+static void batch_launch_vband(cdi_batch *b, int parity, double vs, cudaStream_t s, int final_write)
+{
+    cdi::batch_kernel<T, cdi::VBAND_NT, 1, 4><<<b->nblocks, dim3(cdi::VBAND_NT, 1), b->vband_bytes, s>>>(
+        (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
+        b->recs, b->band, b->vband, final_write);
+}
+
+// Tile 6: copy the current state (the caller's array of this parity) into the
+// padded copy of that parity; the steps of a call then read and write the padded
+// copies, the last of them the caller's array too.
+static int vband_pack_state(cdi_batch *b, int parity, cudaStream_t s)
+{
+    if (b->dtype == CDI_F64)
+        cdi::vband_pack<double><<<dim3(256, b->nbox), 256, 0, s>>>((const BoxDev<double> *)b->boxes_dev, parity);
+    else
+        cdi::vband_pack<float><<<dim3(256, b->nbox), 256, 0, s>>>((const BoxDev<float> *)b->boxes_dev, parity);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cdi::set_error(CDI_ERR_CUDA, "batch pack: %s", cudaGetErrorString(e));
+    return CDI_OK;
+}
+
+template <typename T>
+static int batch_launch(cdi_batch *b, int parity, double vs, cudaStream_t s, int final_write)
 {
     switch (b->tile) {
     case 0: batch_launch_one<T, 32, 8>(b, parity, vs, s); break;
@@ -549,6 +709,7 @@ static int batch_launch(cdi_batch *b, int parity, double vs, cudaStream_t s)
     case 3: batch_launch_one<T, 32, 4>(b, parity, vs, s); break;
     case cdi::BATCH_TILE_PLANE: batch_launch_plane<T>(b, parity, vs, s); break;
     case cdi::BATCH_TILE_BAND: batch_launch_band<T>(b, parity, vs, s); break;
+    case cdi::BATCH_TILE_VBAND: batch_launch_vband<T>(b, parity, vs, s, final_write); break;
     default: return cdi::set_error(CDI_ERR_STATE, "bad batch tile");
     }
     cudaError_t e = cudaGetLastError();
@@ -556,9 +717,12 @@ static int batch_launch(cdi_batch *b, int parity, double vs, cudaStream_t s)
     return CDI_OK;
 }
 
-static int launch_any(cdi_batch *b, int parity, double vs, cudaStream_t s)
+// One step of every box; final_write (tile 6): the step also writes the caller's
+// arrays (the last step of a call).
+static int launch_any(cdi_batch *b, int parity, double vs, cudaStream_t s, int final_write = 1)
 {
-    return b->dtype == CDI_F64 ? batch_launch<double>(b, parity, vs, s) : batch_launch<float>(b, parity, vs, s);
+    return b->dtype == CDI_F64 ? batch_launch<double>(b, parity, vs, s, final_write)
+                               : batch_launch<float>(b, parity, vs, s, final_write);
 }
 
 static void reset_recs(std::vector<StatsRec> &h)
@@ -591,6 +755,7 @@ int cdi_batch_create(cdi_batch **out, const cdi_box_desc *boxes, int nbox, int d
     for (int i = 0; i < nbox; ++i) b->flat = b->flat && boxes[i].nz == 1;
     b->plane_bytes = plane_bytes(b);
     b->band_bytes = band_bytes(b);
+    b->vband_bytes = vband_bytes(b);
     cudaError_t e;
     int dev = 0;
     std::vector<StatsRec> hrec(nbox);
@@ -633,7 +798,8 @@ int cdi_batch_step(cdi_batch *b, double vel_scale, void *stream)
     if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
     if (!isfinite(vel_scale)) return cdi::set_error(CDI_ERR_ARG, "vel_scale must be finite");
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = launch_any(b, b->parity, vel_scale, s);
+    int rc = b->tile == cdi::BATCH_TILE_VBAND ? vband_pack_state(b, b->parity, s) : CDI_OK;
+    if (rc == CDI_OK) rc = launch_any(b, b->parity, vel_scale, s);
     if (rc == CDI_OK) b->parity ^= 1;
     return rc;
 }
@@ -651,9 +817,9 @@ int cdi_batch_run(cdi_batch *b, int nsteps, void *stream)
         cudaGraph_t graph;
         if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return cdi::set_error(CDI_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
-        int rc = CDI_OK;
+        int rc = b->tile == cdi::BATCH_TILE_VBAND ? vband_pack_state(b, b->parity, b->cap) : CDI_OK;
         for (int i = 0; i < nsteps && rc == CDI_OK; ++i) {
-            rc = launch_any(b, b->parity ^ (i & 1), 1.0, b->cap);
+            rc = launch_any(b, b->parity ^ (i & 1), 1.0, b->cap, i == nsteps - 1);
         }
         e = cudaStreamEndCapture(b->cap, &graph);
         if (rc) return rc;
@@ -774,15 +940,18 @@ int cdi_batch_autotune(cdi_batch *b, int reps, float *best_ms, void *stream)
     for (int tile = 0; tile < cdi::BATCH_TILES && rc == CDI_OK; ++tile) {
         if (tile == cdi::BATCH_TILE_PLANE && b->plane_bytes == 0) continue;
         if (tile == cdi::BATCH_TILE_BAND && b->band_bytes == 0) continue;
+        if (tile == cdi::BATCH_TILE_VBAND && b->vband_bytes == 0) continue;
         if (b->sharpen == CDI_SHARPEN_FACE && tile != 0 && tile != cdi::BATCH_TILE_PLANE) continue;
         for (int zi = 0; zi < nz_opts && rc == CDI_OK; ++zi) {
             if ((rc = rebuild(b, tile, zopts[zi])) != CDI_OK) break;
-            if ((rc = launch_any(b, b->parity, 1.0, s)) != CDI_OK) break;  // warm-up
+            // tile 6: the state packed once, then steps between the padded copies as in a run
+            if (tile == cdi::BATCH_TILE_VBAND && (rc = vband_pack_state(b, b->parity, s)) != CDI_OK) break;
+            if ((rc = launch_any(b, b->parity, 1.0, s, 0)) != CDI_OK) break;  // warm-up
             if ((e = cudaEventRecord(e0, s)) != cudaSuccess) {
                 rc = cdi::set_error(CDI_ERR_CUDA, "event: %s", cudaGetErrorString(e));
                 break;
             }
-            for (int i = 0; i < reps && rc == CDI_OK; ++i) rc = launch_any(b, b->parity, 1.0, s);
+            for (int i = 0; i < reps && rc == CDI_OK; ++i) rc = launch_any(b, b->parity, 1.0, s, 0);
             if (rc != CDI_OK) break;
             if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess) {
                 rc = cdi::set_error(CDI_ERR_CUDA, "event: %s", cudaGetErrorString(e));

@@ -200,6 +200,18 @@ struct Acc<float> {
             }
         }
     }
+    // the first n (1 <= n <= N) of N values (a group cut by the end of a row)
+    template <int N>
+    __device__ __forceinline__ void add_group_n(const float *o, int n, float tol)
+    {
+        if (n == N) {
+            add_group<N>(o, tol);
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i < n) add(o[i], tol);
+    }
     __device__ __forceinline__ Partial partial() const
     {
         Partial r;
@@ -287,6 +299,17 @@ struct Acc<double> {
 #pragma unroll
             for (int i = 0; i < N; ++i) count(k[i], tol);
         }
+    }
+    template <int N>
+    __device__ __forceinline__ void add_group_n(const double *o, int n, double tol)
+    {
+        if (n == N) {
+            add_group<N>(o, tol);
+            return;
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i < n) add(o[i], tol);
     }
     __device__ __forceinline__ Partial partial() const
     {

@@ -69,7 +69,7 @@ def test_batch_graph_run_equals_steps():
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-@pytest.mark.parametrize("tile", [0, 1, 2, 3, 5])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 5, 6])
 @pytest.mark.parametrize("zdepth", [0, 5, 32])
 def test_batch_every_launch_configuration(dtype, tile, zdepth):
     """Each work-unit tile and z depth gives the oracle's steps (ragged tiles and chunks)."""
@@ -310,3 +310,51 @@ def test_band_tile_refusals():
         wide.set_launch(5, 0)
     wide.autotune(reps=1)
     assert wide.get_launch()["tile"] != 5
+
+
+def _twin_boxes(shapes, dtype, seed):
+    boxes = []
+    for i, s in enumerate(shapes):
+        nz, ny, nx = s
+        h = 1.0 / max(s)
+        phi = dev(I.random_phi(s, seed + i, smooth=True), dtype)
+        vel = [dev(x, dtype) for x in I.random_velocity(s, h, 8, 3, seed + 50 + i)]
+        eps, gamma = 1.1 * h, 1.0
+        boxes.append(dict(dx=h, dt=0.1 * h * h / (gamma * eps), eps=eps, gamma=gamma, u=vel[0], v=vel[1],
+                          w=vel[2], phi_a=phi, phi_b=torch.empty_like(phi)))
+    twins = [dict(x, phi_a=x["phi_a"].clone(), phi_b=torch.empty_like(x["phi_b"])) for x in boxes]
+    return boxes, twins
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_padded_band_tile_bit_for_bit(dtype):
+    """Tile 6 steps the batch's padded copies of the boxes (rows padded to 16 bytes, with
+    periodic ghost cells) and writes the caller's arrays on the last step of each call.  On
+    boxes of every row alignment, degenerate extents included, run() and step() give tile 0's
+    fields bit for bit, and a state the caller writes between calls is the one stepped."""
+    shapes = [(6, 9, 1), (5, 7, 2), (8, 11, 3), (9, 21, 68), (12, 33, 35), (1, 40, 61), (20, 1, 17),
+              (7, 3, 4), (16, 48, 128), (3, 2, 5)]
+    boxes, twins = _twin_boxes(shapes, dtype, 70)
+    b0, b6 = cdi.Batch(boxes), cdi.Batch(twins)
+    b0.set_launch(0, 0)
+    b6.set_launch(6, 4)
+    assert b6.get_launch()["tile"] == 6
+    for b in (b0, b6):
+        b.run(3)
+    for i in range(len(shapes)):
+        assert torch.equal(b0.current(i), b6.current(i)), ("run", i)
+    for b in (b0, b6):
+        b.step(1.0)
+        b.step(0.5)
+    for i in range(len(shapes)):
+        assert torch.equal(b0.current(i), b6.current(i)), ("step", i)
+    for b in (b0, b6):      # the caller changes the state between calls
+        for i in range(len(shapes)):
+            b.current(i).mul_(0.75)
+        b.run(2)
+    s0, s6 = b0.stats(), b6.stats()
+    for i in range(len(shapes)):
+        assert torch.equal(b0.current(i), b6.current(i)), ("written", i)
+        assert s0[i]["min"] == s6[i]["min"] and s0[i]["max"] == s6[i]["max"]
+        assert s0[i]["steps_run"] == s6[i]["steps_run"] == 7
+        assert s6[i]["sum"] == pytest.approx(s0[i]["sum"], rel=1e-12 if dtype == torch.float64 else 1e-6)
