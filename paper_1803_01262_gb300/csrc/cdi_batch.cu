@@ -1,11 +1,13 @@
 // Batched CDI step: many independent periodic boxes of uneven sizes, each
 // with its own face velocities, spacing, eps, gamma and dt, advanced by ONE
 // launch per step.  The launch is a persistent grid of resident blocks that
-// takes work units round-robin from one list covering every box: a unit is a
+// takes work units, in order, from one list covering every box (a counter hands
+// the next unit to the next block that is done with one): a unit is a
 // BX x BY tile of one box and a chunk of its planes, processed by the same
 // per-unit body as the single-box kernel (cdi_fwd_scalar.cuh).  Units of a box
 // are contiguous in the list (chunk-major), so blocks resident together share
-// halo planes through L2.  Each unit's outputs are reduced to one partial
+// halo planes through L2; the boxes come in order of decreasing unit size, so
+// the launch ends on the smallest units.  Each unit's outputs are reduced to one partial
 // slot; the block that completes a box's last unit folds that box's slots, in
 // unit order, into the box's statistics record (reproducible, and spread over
 // the launch instead of serialised at its end).  The tile shape and the number
@@ -138,12 +140,18 @@ __global__ void __launch_bounds__(BX * BY, BODY >= 3 ? 2 : 1)
 batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_box,
              const int total_units, const int parity, const T vs, Partial *partials,
              unsigned int *box_done, StatsRec *recs, const BandSlots bs, const VbandSlots vbs,
-             const int final_write)
+             const int final_write, unsigned int *queue)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int fold;
+    __shared__ int fold, next_u;
     const int tid = threadIdx.x + BX * threadIdx.y;
-    for (int u = blockIdx.x; u < total_units; u += gridDim.x) {
+    // Units are handed out in list order from a counter (queue[0]; every block
+    // starts with unit blockIdx.x): a block takes the next unit when it is done
+    // with one, so blocks that run faster take more.  The fields do not depend
+    // on which block steps a unit, and the statistics are folded per box in
+    // unit order, so the result does not either.
+    int u = blockIdx.x;
+    while (u < total_units) {
         const int bi = unit_box[u];
         FwdArgs<T> a = boxes[bi].a;
         if (parity) {
@@ -178,8 +186,11 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
             else
                 scalar_unit<T, BX, BY, false, SCALAR_PF, FACE>(a, un, acc, smem_raw);
         }
+        int claim = 0;  // the next unit, requested before this one's reduction
+        if (tid == 0) claim = (int)atomicAdd(queue, 1u) + (int)gridDim.x;
         const Partial p = block_partial(acc);
         if (tid == 0) {
+            next_u = claim;
             partials[u] = p;
             __threadfence();
             const unsigned done = atomicAdd(box_done + bi, 1u) + 1u;
@@ -208,6 +219,15 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
             }
         }
         __syncthreads();  // every thread has read `fold` before it is written again
+        u = next_u;
+    }
+    // the last block to run out of units resets the counters for the next launch
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+            queue[0] = 0u;
+            queue[1] = 0u;
+        }
     }
 }
 
@@ -262,6 +282,7 @@ struct cdi_batch {
     cdi::Partial *partials;    // [unit_cap]
     size_t unit_cap;
     unsigned int *box_done;    // [nbox] units completed in the current launch
+    unsigned int *queue;       // [2] next unit to hand out, blocks finished (self-resetting)
     StatsRec *recs;            // [nbox]
     unsigned int *status;      // status words (checked builds record out-of-range indices)
     long long cells;
@@ -488,6 +509,7 @@ static int batch_free(cdi_batch *b)
     cudaFree(b->unit_box);
     cudaFree(b->partials);
     cudaFree(b->box_done);
+    cudaFree(b->queue);
     cudaFree(b->recs);
     cudaFree(b->status);
     cudaFree(b->padbuf);
@@ -577,13 +599,28 @@ static int build_units(cdi_batch *b, int tile, int zdepth)
         int nch = zdepth > 0 && !plane ? (x.nz + zdepth / 2) / zdepth : 1;  // about zdepth planes per unit
         if (nch < 1) nch = 1;
         e.zc = (x.nz + nch - 1) / nch;
-        e.unit0 = unit;
         e.nunits = e.ntiles * ((x.nz + e.zc - 1) / e.zc);
         if ((long long)unit + e.nunits >= (1LL << 31)) return cdi::set_error(CDI_ERR_DIM, "too many work units");
-        for (int k = 0; k < e.nunits; ++k) ub.push_back(i);
         unit += e.nunits;
         cells += (long long)x.nx * x.ny * x.nz;
         tab.push_back(e);
+    }
+    // The boxes' unit ranges in the list by decreasing unit size (cells of a unit's
+    // plane times its planes plus a prologue of about four), so that the blocks
+    // taking units from the list end on the smallest ones.
+    std::vector<int> order(b->nbox);
+    std::vector<double> ucost(b->nbox);
+    for (int i = 0; i < b->nbox; ++i) {
+        const cdi_box_desc &x = b->desc[i];
+        order[i] = i;
+        ucost[i] = (double)x.nx * x.ny / tab[i].ntiles * (tab[i].zc + 4.0);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return ucost[p] > ucost[q]; });
+    unit = 0;
+    for (int i : order) {
+        tab[i].unit0 = unit;
+        for (int k = 0; k < tab[i].nunits; ++k) ub.push_back(i);
+        unit += tab[i].nunits;
     }
     int resident = 0;
     e = batch_occ<T>(b, tile, &resident);
@@ -638,21 +675,21 @@ static void batch_launch_one(cdi_batch *b, int parity, double vs, cudaStream_t s
         if (b->flat)
             cdi::batch_kernel<T, 32, 8, 1, true><<<b->nblocks, dim3(32, 8), cdi::FwdSmem<T, 32, 8>::bytes, s>>>(
                 (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-                b->box_done, b->recs, b->band, b->vband, 0);
+                b->box_done, b->recs, b->band, b->vband, 0, b->queue);
         else
             cdi::batch_kernel<T, 32, 8, 0, true><<<b->nblocks, dim3(32, 8), cdi::FwdSmem<T, 32, 8>::bytes, s>>>(
                 (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-                b->box_done, b->recs, b->band, b->vband, 0);
+                b->box_done, b->recs, b->band, b->vband, 0, b->queue);
         return;
     }
     if (b->flat)
         cdi::batch_kernel<T, BX, BY, 1><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
             (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-            b->box_done, b->recs, b->band, b->vband, 0);
+            b->box_done, b->recs, b->band, b->vband, 0, b->queue);
     else
         cdi::batch_kernel<T, BX, BY, 0><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
             (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-            b->box_done, b->recs, b->band, b->vband, 0);
+            b->box_done, b->recs, b->band, b->vband, 0, b->queue);
 }
 
 template <typename T>
@@ -661,12 +698,12 @@ static void batch_launch_plane(cdi_batch *b, int parity, double vs, cudaStream_t
     if (b->sharpen == CDI_SHARPEN_FACE) {
         cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2, true><<<b->nblocks, dim3(cdi::PLANE_NT, 1), b->plane_bytes, s>>>(
             (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-            b->recs, b->band, b->vband, 0);
+            b->recs, b->band, b->vband, 0, b->queue);
         return;
     }
     cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2><<<b->nblocks, dim3(cdi::PLANE_NT, 1), b->plane_bytes, s>>>(
         (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-        b->recs, b->band, b->vband, 0);
+        b->recs, b->band, b->vband, 0, b->queue);
 }
 
 template <typename T>
@@ -674,7 +711,7 @@ static void batch_launch_band(cdi_batch *b, int parity, double vs, cudaStream_t 
 {
     cdi::batch_kernel<T, cdi::BAND_NT, 1, 3><<<b->nblocks, dim3(cdi::BAND_NT, 1), b->band_bytes, s>>>(
         (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-        b->recs, b->band, b->vband, 0);
+        b->recs, b->band, b->vband, 0, b->queue);
 }
 
 template <typename T>
@@ -682,7 +719,7 @@ static void batch_launch_vband(cdi_batch *b, int parity, double vs, cudaStream_t
 {
     cdi::batch_kernel<T, cdi::VBAND_NT, 1, 4><<<b->nblocks, dim3(cdi::VBAND_NT, 1), b->vband_bytes, s>>>(
         (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-        b->recs, b->band, b->vband, final_write);
+        b->recs, b->band, b->vband, final_write, b->queue);
 }
 
 // Tile 6: copy the current state (the caller's array of this parity) into the
@@ -763,6 +800,8 @@ int cdi_batch_create(cdi_batch **out, const cdi_box_desc *boxes, int nbox, int d
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
         (e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
         (e = cudaMalloc(&b->box_done, sizeof(unsigned int) * nbox)) != cudaSuccess ||
+        (e = cudaMalloc(&b->queue, sizeof(unsigned int) * 2)) != cudaSuccess ||
+        (e = cudaMemset(b->queue, 0, sizeof(unsigned int) * 2)) != cudaSuccess ||
         (e = cudaMalloc(&b->recs, sizeof(StatsRec) * nbox)) != cudaSuccess ||
         (e = cudaMalloc(&b->status, sizeof(unsigned int) * cdi::kStatusWords)) != cudaSuccess ||
         (e = cudaMemset(b->status, 0, sizeof(unsigned int) * cdi::kStatusWords)) != cudaSuccess ||
