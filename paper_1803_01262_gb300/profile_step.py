@@ -36,6 +36,8 @@ def main():
     ap.add_argument("--nchunks", type=int, default=0)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--depth", type=int, default=1, help="forward: steps per launch (cdi_run)")
+    ap.add_argument("--run", action="store_true",
+                    help="forward, batch: the steps as one run (cdi_run / graph), as the bench times them")
     args = ap.parse_args()
     dtype = torch.float32 if args.dtype == "f32" else torch.float64
     if args.kernel == "batch":
@@ -58,6 +60,11 @@ def main():
         g.run(a, b, 2 * args.steps, dt, eps, gamma, period=3.0)
         torch.cuda.synchronize()
         print("run depth", g.get_run_depth())
+        return
+    if args.kernel == "forward" and args.run:
+        g.run(a, b, args.steps, dt, eps, gamma, period=3.0)
+        torch.cuda.synchronize()
+        print("launch", g.get_launch(which))
         return
     for i in range(args.steps):
         vs = math.cos(math.pi * i * dt / 3.0)
@@ -85,8 +92,11 @@ def run_batch(args, dtype):
         b.autotune(reps=2)
     else:
         b.set_launch(args.tile, args.zdepth)
-    for _ in range(args.steps):
-        b.step(1.0)
+    if args.run:
+        b.run(args.steps)
+    else:
+        for _ in range(args.steps):
+            b.step(1.0)
     torch.cuda.synchronize()
     print("launch", b.get_launch(), b.info())
 
