@@ -382,8 +382,13 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
 
     // gbar and the local term (1 - 2 phi)(sbar . n) of the VX cells of group
     // (gc, ly) at the plane of slot Pm (Pmm / Pmp: planes below / above; the
-    // same slots of the lam' ring).  n = g / m (0 where g = 0); the
-    // projection uses n x (sbar x n) + sbar tiny/m^2 (see the per-cell kernel above).
+    // same slots of the lam' ring).  n = g / m (0 where g = 0).  The projection
+    // is evaluated as sbar - n (n . sbar), which equals the per-cell kernel's
+    // n x (sbar x n) + sbar delta^2/m^2 since |n|^2 + delta^2/m^2 = 1: three FMAs
+    // on the already formed n . sbar instead of two cross products (112.0 ->
+    // 105.6 us per FP32 step at 256^3).  It rounds differently: where sbar is
+    // parallel to n (1D) the result is delta^2/m^2 sbar plus rounding of order
+    // eps |sbar|, where the cross form gives that term alone.
     auto gbar_group = [&](int sm, int smm, int smp, int gc, int ly, T *b0, T *b1, T *b2, T *tl) {
         const int off = (ly + 2) * PP + VX + gc * VX;
         const T *Pm = sphi + sm * C::PHI, *Pmm = sphi + smm * C::PHI, *Pmp = sphi + smp * C::PHI;
@@ -413,15 +418,13 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
             const T sb2 = c_sb * (lzp[i] - lzn[i]);
             const T n0 = g0 * inv, n1 = g1 * inv, n2 = g2 * inv;
             const T p = c[i];
-            tl[i] = (T(1) - T(2) * p) * (sb0 * n0 + sb1 * n1 + sb2 * n2);
-            const T x0_ = sb1 * n2 - sb2 * n1;
-            const T x1_ = sb2 * n0 - sb0 * n2;
-            const T x2_ = sb0 * n1 - sb1 * n0;
+            const T ns = sb0 * n0 + sb1 * n1 + sb2 * n2;
+            tl[i] = (T(1) - T(2) * p) * ns;
+            // the projection sbar - n (n . sbar) (|n|^2 + delta^2 / m^2 = 1), in three FMAs
             const T wgt = p * (T(1) - p) * inv;
-            const T fl = floor_part(inv);
-            b0[i] = wgt * fma(sb0, fl, n1 * x2_ - n2 * x1_);
-            b1[i] = wgt * fma(sb1, fl, n2 * x0_ - n0 * x2_);
-            b2[i] = wgt * fma(sb2, fl, n0 * x1_ - n1 * x0_);
+            b0[i] = wgt * fma(-n0, ns, sb0);
+            b1[i] = wgt * fma(-n1, ns, sb1);
+            b2[i] = wgt * fma(-n2, ns, sb2);
         }
     };
     // gbar_x only, of cell (lx, ly) (the x-ring).
@@ -438,9 +441,8 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
         const T sb1 = c_sb * (Lm[off + PP] - Lm[off - PP]);
         const T sb2 = c_sb * (Lmp[off] - Lmm[off]);
         const T n0 = g0 * inv, n1 = g1 * inv, n2 = g2 * inv;
-        const T x1_ = sb2 * n0 - sb0 * n2;
-        const T x2_ = sb0 * n1 - sb1 * n0;
-        return p * (T(1) - p) * inv * fma(sb0, floor_part(inv), n1 * x2_ - n2 * x1_);
+        const T ns = sb0 * n0 + sb1 * n1 + sb2 * n2;
+        return p * (T(1) - p) * inv * fma(-n0, ns, sb0);
     };
 
     bool dep_waited = false;  // the previous grid on the stream has completed
