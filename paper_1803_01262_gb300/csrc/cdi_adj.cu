@@ -348,7 +348,9 @@ struct AdjVecCfg {
 
 // Three FP32 blocks per SM (113 registers) measured 8% faster than two; FP64
 // keeps two (it would spill at three).
-template <typename T, int TX, int TY>
+// VEL: the velocity gradients are accumulated (a.gu, a.gv, a.gw not null); the
+// instantiation without them keeps no face differences live for them.
+template <typename T, int TX, int TY, bool VEL>
 __global__ void __launch_bounds__(AdjVecCfg<T, TX, TY>::NT, sizeof(T) == 4 ? 3 : 2)
 adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
 {
@@ -369,7 +371,7 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
     const int ntiles = tiles_x * ((ny + H - 1) / H);
     const T c_adv = a.c.c_adv, c_dif = a.c.c_dif, c_upd = a.c.c_upd, c_sb = a.c_shp_adj;
     const T c_vel = a.c_vel;
-    const bool want_vel = a.gu != nullptr;
+    constexpr bool want_vel = VEL;
 
     const bool is_own = tid < C::NOWN;
     const int tx = tid % TX, ty = tid / TX;
@@ -716,10 +718,12 @@ template <typename T>
 cudaError_t adj_vec_resident(int *resident)
 {
     using C = AdjVecCfg<T, 16, 8>;
-    cudaError_t e = cudaFuncSetAttribute(adj_vec_kernel<T, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(adj_vec_kernel<T, 16, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)C::bytes);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, adj_vec_kernel<T, 16, 8>, C::NT, C::bytes);
+    e = cudaFuncSetAttribute(adj_vec_kernel<T, 16, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(resident, adj_vec_kernel<T, 16, 8, false>, C::NT, C::bytes);
 }
 template cudaError_t adj_vec_resident<float>(int *);
 template cudaError_t adj_vec_resident<double>(int *);
@@ -762,7 +766,8 @@ static cudaError_t launch_adj_vec(const AdjArgs<T> &a, cudaStream_t s)
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, adj_vec_kernel<T, 16, 8>, a, nchunks);
+    if (a.gu) return cudaLaunchKernelEx(&cfg, adj_vec_kernel<T, 16, 8, true>, a, nchunks);
+    return cudaLaunchKernelEx(&cfg, adj_vec_kernel<T, 16, 8, false>, a, nchunks);
 }
 
 template <typename T, int BX, int BY>
