@@ -470,6 +470,7 @@ template <typename T>
 static size_t vband_bytes_t(cdi_batch *b)
 {
     const int vx = 16 / (int)sizeof(T);
+    if (b->nbox > 65535) return 0;  // the copy kernels take the box from blockIdx.y
     int phi = 0, ur = 0, vr = 0, sx = 0, sy = 0;
     for (const cdi_box_desc &x : b->desc) {
         if ((x.nx + vx - 1) / vx > cdi::VBAND_NT) return 0;  // a row has more groups than the block threads
