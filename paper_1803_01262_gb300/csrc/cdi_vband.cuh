@@ -260,88 +260,88 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
         // sharpening at plane k+1: the ring rows, then the own group (s_z kept)
         sharp_ring(Pk1, Pk, Pk2, syw);
         if (act) {
-        T szn[VX];
-        {
-            T s0[VX], s1[VX];
-            sharp_group(Pk1, Pk, Pk2, pos, s0, s1, szn);
-            VV::st(sxw + sxo, s0);
-            VV::st(syw + syo, s1);
-        }
-        // fluxes and update at plane k (s of plane k: buffer k & 1, written before the barrier)
-        const T *sx = ssx + (k & 1) * S.sx, *sy = ssy + (k & 1) * S.sy;
-        const T *vel = svel + vk * S.vel;
-        T c[VX], yn[VX], yp[VX], zp[VX];
-        VV::ld(c, Pk + pos);
-        VV::ld(yn, Pk + pos - P);
-        VV::ld(yp, Pk + pos + P);
-        VV::ld(zp, Pk1 + pos);
-        const T L = Pk[pos - 1], R = Pk[pos + VX];
-        T sxc[VX], syn[VX], syp[VX];
-        VV::ld(sxc, sx + sxo);
-        VV::ld(syn, sy + syo - P);
-        VV::ld(syp, sy + syo + P);
-        const T sxL = sx[sxo - 1 + dL], sxR = sx[sxo + VX + dR];
-        const T *ur = vel + r * P + GH + x0;
-        const T *vr = vel + S.vo + (r + 1) * P + GH + x0;
-        const T *wr = vel + S.wo + r * P + GH + x0;
-        T uc[VX], vc[VX], vn[VX], wc[VX];
-        VV::ld(uc, ur);
-        VV::ld(vc, vr);
-        VV::ld(vn, vr - P);
-        VV::ld(wc, wr);
-        const T uL = ur[-1];
-        T o[VX];
+            T szn[VX];
+            {
+                T s0[VX], s1[VX];
+                sharp_group(Pk1, Pk, Pk2, pos, s0, s1, szn);
+                VV::st(sxw + sxo, s0);
+                VV::st(syw + syo, s1);
+            }
+            // fluxes and update at plane k (s of plane k: buffer k & 1, written before the barrier)
+            const T *sx = ssx + (k & 1) * S.sx, *sy = ssy + (k & 1) * S.sy;
+            const T *vel = svel + vk * S.vel;
+            T c[VX], yn[VX], yp[VX], zp[VX];
+            VV::ld(c, Pk + pos);
+            VV::ld(yn, Pk + pos - P);
+            VV::ld(yp, Pk + pos + P);
+            VV::ld(zp, Pk1 + pos);
+            const T L = Pk[pos - 1], R = Pk[pos + VX];
+            T sxc[VX], syn[VX], syp[VX];
+            VV::ld(sxc, sx + sxo);
+            VV::ld(syn, sy + syo - P);
+            VV::ld(syp, sy + syo + P);
+            const T sxL = sx[sxo - 1 + dL], sxR = sx[sxo + VX + dR];
+            const T *ur = vel + r * P + GH + x0;
+            const T *vr = vel + S.vo + (r + 1) * P + GH + x0;
+            const T *wr = vel + S.wo + r * P + GH + x0;
+            T uc[VX], vc[VX], vn[VX], wc[VX];
+            VV::ld(uc, ur);
+            VV::ld(vc, vr);
+            VV::ld(vn, vr - P);
+            VV::ld(wc, wr);
+            const T uL = ur[-1];
+            T o[VX];
 #pragma unroll
-        for (int i = 0; i < VX; ++i) {
-            const T xl = i > 0 ? c[i - 1] : L, xr = i + 1 < VX ? c[i + 1] : R;
-            const T ul = i > 0 ? uc[i - 1] : uL;
-            const T sl = i > 0 ? sxc[i - 1] : sxL, sr = i + 1 < VX ? sxc[i + 1] : sxR;
-            T adv = uc[i] * (c[i] + xr);
-            adv = fma(-ul, xl + c[i], adv);
-            adv = fma(vc[i], c[i] + yp[i], adv);
-            adv = fma(-vn[i], yn[i] + c[i], adv);
-            const T dif = fma(T(-4), c[i], (xl + xr) + (yn[i] + yp[i]));
-            const T shp = (sr - sl) + (syp[i] - syn[i]);
-            const T Fzp = flux(c_adv * wc[i], c_dif, c_shp, c[i], zp[i], szc[i], szn[i]);
-            const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, Fzp - Fzm[i])));
-            o[i] = fma(-c_upd, div, c[i]);
-            Fzm[i] = Fzp;
-            szc[i] = szn[i];
-        }
-        // the padded copy of the next state: the group, and the ghost cells it feeds
-        T *const orow = pout + (long long)CDI_CHK(k, nz, st) * planeP + (long long)(y0 + r) * P + GH;
-        if (nown == VX) {
-            VV::st(orow + x0, o);
-        } else {
-#pragma unroll
-            for (int i = 0; i < VX; ++i)
-                if (i < nown) orow[x0 + i] = o[i];
-        }
-        acc.template add_group_n<VX>(o, nown, a.c.tol);
-        if (gmask) {  // cells within GH of a row end: their ghost copies
-            if (nx >= GH) {
-#pragma unroll
-                for (int i = 0; i < VX; ++i) {
-                    if ((gmask >> (2 * i)) & 1u) orow[x0 + i - nx] = o[i];
-                    if ((gmask >> (2 * i)) & 2u) orow[x0 + i + nx] = o[i];
-                }
+            for (int i = 0; i < VX; ++i) {
+                const T xl = i > 0 ? c[i - 1] : L, xr = i + 1 < VX ? c[i + 1] : R;
+                const T ul = i > 0 ? uc[i - 1] : uL;
+                const T sl = i > 0 ? sxc[i - 1] : sxL, sr = i + 1 < VX ? sxc[i + 1] : sxR;
+                T adv = uc[i] * (c[i] + xr);
+                adv = fma(-ul, xl + c[i], adv);
+                adv = fma(vc[i], c[i] + yp[i], adv);
+                adv = fma(-vn[i], yn[i] + c[i], adv);
+                const T dif = fma(T(-4), c[i], (xl + xr) + (yn[i] + yp[i]));
+                const T shp = (sr - sl) + (syp[i] - syn[i]);
+                const T Fzp = flux(c_adv * wc[i], c_dif, c_shp, c[i], zp[i], szc[i], szn[i]);
+                const T div = fma(c_adv, adv, fma(-c_dif, dif, fma(c_shp, shp, Fzp - Fzm[i])));
+                o[i] = fma(-c_upd, div, c[i]);
+                Fzm[i] = Fzp;
+                szc[i] = szn[i];
+            }
+            // the padded copy of the next state: the group, and the ghost cells it feeds
+            T *const orow = pout + (long long)CDI_CHK(k, nz, st) * planeP + (long long)(y0 + r) * P + GH;
+            if (nown == VX) {
+                VV::st(orow + x0, o);
             } else {
 #pragma unroll
-                for (int i = 0; i < VX; ++i) {
-                    if (i >= nown) continue;
-                    const int x = x0 + i;
-                    for (int g = x - nx; g >= -GH; g -= nx) orow[g] = o[i];
-                    for (int g = x + nx; g < nx + GH; g += nx) orow[g] = o[i];
+                for (int i = 0; i < VX; ++i)
+                    if (i < nown) orow[x0 + i] = o[i];
+            }
+            acc.template add_group_n<VX>(o, nown, a.c.tol);
+            if (gmask) {  // cells within GH of a row end: their ghost copies
+                if (nx >= GH) {
+#pragma unroll
+                    for (int i = 0; i < VX; ++i) {
+                        if ((gmask >> (2 * i)) & 1u) orow[x0 + i - nx] = o[i];
+                        if ((gmask >> (2 * i)) & 2u) orow[x0 + i + nx] = o[i];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < VX; ++i) {
+                        if (i >= nown) continue;
+                        const int x = x0 + i;
+                        for (int g = x - nx; g >= -GH; g -= nx) orow[g] = o[i];
+                        for (int g = x + nx; g < nx + GH; g += nx) orow[g] = o[i];
+                    }
                 }
             }
-        }
-        if (final_write) {  // the caller's array (rows at any 4-byte boundary: element stores)
-            T *const urow = a.out + (long long)k * plane + (long long)(y0 + r) * nx + x0;
+            if (final_write) {  // the caller's array (rows at any 4-byte boundary: element stores)
+                T *const urow = a.out + (long long)k * plane + (long long)(y0 + r) * nx + x0;
 #pragma unroll
-            for (int i = 0; i < VX; ++i)
-                if (i < nown) urow[i] = o[i];
+                for (int i = 0; i < VX; ++i)
+                    if (i < nown) urow[i] = o[i];
+            }
         }
-        }  // act
         pk = pk1;
         vk = vk == 2 ? 0 : vk + 1;
     }
