@@ -391,7 +391,11 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
     // 105.6 us per FP32 step at 256^3).  It rounds differently: where sbar is
     // parallel to n (1D) the result is delta^2/m^2 sbar plus rounding of order
     // eps |sbar|, where the cross form gives that term alone.
-    auto gbar_group = [&](int sm, int smm, int smp, int gc, int ly, T *b0, T *b1, T *b2, T *tl) {
+    // lzn_in (nullable): lam' of the group at the plane below, already loaded; lc_out
+    // (nullable): receives lam' of the group at this plane (an own thread's update
+    // reads both again)
+    auto gbar_group = [&](int sm, int smm, int smp, int gc, int ly, T *b0, T *b1, T *b2, T *tl,
+                          const T *lzn_in = nullptr, T *lc_out = nullptr) {
         const int off = (ly + 2) * PP + VX + gc * VX;
         const T *Pm = sphi + sm * C::PHI, *Pmm = sphi + smm * C::PHI, *Pmp = sphi + smp * C::PHI;
         const T *Lm = slam + sm * C::PHI, *Lmm = slam + smm * C::PHI, *Lmp = slam + smp * C::PHI;
@@ -406,9 +410,18 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
         VV::ld(lc, Lm + off);
         VV::ld(lyn, Lm + off - PP);
         VV::ld(lyp, Lm + off + PP);
-        VV::ld(lzn, Lmm + off);
+        if (lzn_in) {
+#pragma unroll
+            for (int i = 0; i < VX; ++i) lzn[i] = lzn_in[i];
+        } else {
+            VV::ld(lzn, Lmm + off);
+        }
         VV::ld(lzp, Lmp + off);
         const T lL = Lm[off - 1], lR = Lm[off + VX];
+        if (lc_out) {
+#pragma unroll
+            for (int i = 0; i < VX; ++i) lc_out[i] = lc[i];
+        }
 #pragma unroll
         for (int i = 0; i < VX; ++i) {
             const T g0 = (i + 1 < VX ? c[i + 1] : R) - (i > 0 ? c[i - 1] : L);
@@ -595,23 +608,22 @@ adj_vec_kernel(const AdjArgs<T> a, const int nchunks)
                 sgx[b1 * C::SXS + rx_row * SXP + VX + rx_col] = gbar_x_cell(pk1, pk, pk2, rx_col, rx_row);
             }
             if (is_own) {
-                T gzp[VX], tp[VX];
+                const int po = (ty + 2) * PP + VX + tx * VX;
+                T gzp[VX], tp[VX], lc[VX], lzp[VX];  // lam' of the own group at planes k, k+1
+                VV::ld(lc, slam + pk * C::PHI + po);
                 {
                     T b0[VX], bb1[VX];
-                    gbar_group(pk1, pk, pk2, tx, ty, b0, bb1, gzp, tp);
+                    gbar_group(pk1, pk, pk2, tx, ty, b0, bb1, gzp, tp, lc, lzp);
                     VV::st(sgx + b1 * C::SXS + ty * SXP + VX + tx * VX, b0);
                     VV::st(sgy + b1 * C::SYS + (ty + 1) * W + tx * VX, bb1);
                 }
 
                 // C: lam at plane k.
                 const int b = k & 1;
-                const int po = (ty + 2) * PP + VX + tx * VX;
-                const T *Lk = slam + pk * C::PHI, *Lk1 = slam + pk1 * C::PHI;
-                T lc[VX], lyn[VX], lyp[VX], lzp[VX];
-                VV::ld(lc, Lk + po);
+                const T *Lk = slam + pk * C::PHI;
+                T lyn[VX], lyp[VX];
                 VV::ld(lyn, Lk + po - PP);
                 VV::ld(lyp, Lk + po + PP);
-                VV::ld(lzp, Lk1 + po);
                 const T lL = Lk[po - 1], lR = Lk[po + VX];
                 const T *gxr = sgx + b * C::SXS + ty * SXP + VX + tx * VX;
                 const T *gyr = sgy + b * C::SYS + (ty + 1) * W + tx * VX;
