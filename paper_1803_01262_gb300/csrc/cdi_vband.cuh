@@ -143,14 +143,26 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
         if (i < nown) gmask |= ((x >= nx - GH ? 1u : 0u) | (x < GH ? 2u : 0u)) << (2 * i);
     }
 
-    // sharpening of the group at phi-slot offset off of plane Pm (below Pmm, above Pmp)
-    auto sharp_group = [&](const T *Pm, const T *Pmm, const T *Pmp, int off, T *s0, T *s1, T *s2) {
+    // sharpening of the group at phi-slot offset off of plane Pm (below Pmm, above Pmp);
+    // zn_in (nullable): the group at the plane below, already loaded; c_out (nullable):
+    // receives the group at this plane (an own group's update reads both again)
+    auto sharp_group = [&](const T *Pm, const T *Pmm, const T *Pmp, int off, T *s0, T *s1, T *s2,
+                           const T *zn_in = nullptr, T *c_out = nullptr) {
         T c[VX], yn[VX], yp[VX], zn[VX], zp[VX];
         VV::ld(c, Pm + off);
         VV::ld(yn, Pm + off - P);
         VV::ld(yp, Pm + off + P);
-        VV::ld(zn, Pmm + off);
+        if (zn_in) {
+#pragma unroll
+            for (int i = 0; i < VX; ++i) zn[i] = zn_in[i];
+        } else {
+            VV::ld(zn, Pmm + off);
+        }
         VV::ld(zp, Pmp + off);
+        if (c_out) {
+#pragma unroll
+            for (int i = 0; i < VX; ++i) c_out[i] = c[i];
+        }
         const T L = Pm[off - 1], R = Pm[off + VX];
 #pragma unroll
         for (int i = 0; i < VX; ++i) {
@@ -261,20 +273,20 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
         sharp_ring(Pk1, Pk, Pk2, syw);
         if (act) {
             T szn[VX];
+            T c[VX], zp[VX];  // the group at planes k and k+1, read once for both phases
+            VV::ld(c, Pk + pos);
             {
                 T s0[VX], s1[VX];
-                sharp_group(Pk1, Pk, Pk2, pos, s0, s1, szn);
+                sharp_group(Pk1, Pk, Pk2, pos, s0, s1, szn, c, zp);
                 VV::st(sxw + sxo, s0);
                 VV::st(syw + syo, s1);
             }
             // fluxes and update at plane k (s of plane k: buffer k & 1, written before the barrier)
             const T *sx = ssx + (k & 1) * S.sx, *sy = ssy + (k & 1) * S.sy;
             const T *vel = svel + vk * S.vel;
-            T c[VX], yn[VX], yp[VX], zp[VX];
-            VV::ld(c, Pk + pos);
+            T yn[VX], yp[VX];
             VV::ld(yn, Pk + pos - P);
             VV::ld(yp, Pk + pos + P);
-            VV::ld(zp, Pk1 + pos);
             const T L = Pk[pos - 1], R = Pk[pos + VX];
             T sxc[VX], syn[VX], syp[VX];
             VV::ld(sxc, sx + sxo);
