@@ -79,6 +79,15 @@ __host__ __device__ inline size_t vband_smem_bytes(const VbandSlots &s, size_t e
     return esize * (size_t)(5 * s.phi + 3 * s.vel + 2 * s.sx + 2 * s.sy);
 }
 
+// phi around a thread's group at one plane: the group, the groups above and below
+// it in y, and its x neighbours (carried from the sharpening at plane k+1 to the
+// update at plane k+1 in the next iteration).
+template <typename T, int VX>
+struct PhiNb {
+    T c[VX], yn[VX], yp[VX];
+    T L, R;
+};
+
 // Staging plan of one region -- `rows` padded rows from row yb (wrapped in y)
 // -- for this thread: the in-plane offsets of its (at most VBAND_CPY) 16-byte
 // vectors, chunk c = tid + i VBAND_NT of the region landing at c VX in the
@@ -144,10 +153,10 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
     }
 
     // sharpening of the group at phi-slot offset off of plane Pm (below Pmm, above Pmp);
-    // zn_in (nullable): the group at the plane below, already loaded; c_out (nullable):
-    // receives the group at this plane (an own group's update reads both again)
+    // zn_in (nullable): the group at the plane below, already loaded; nb_out (nullable):
+    // receives phi around the group at this plane (the own group's next update reads it)
     auto sharp_group = [&](const T *Pm, const T *Pmm, const T *Pmp, int off, T *s0, T *s1, T *s2,
-                           const T *zn_in = nullptr, T *c_out = nullptr) {
+                           const T *zn_in = nullptr, PhiNb<T, VX> *nb_out = nullptr) {
         T c[VX], yn[VX], yp[VX], zn[VX], zp[VX];
         VV::ld(c, Pm + off);
         VV::ld(yn, Pm + off - P);
@@ -159,11 +168,17 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
             VV::ld(zn, Pmm + off);
         }
         VV::ld(zp, Pmp + off);
-        if (c_out) {
-#pragma unroll
-            for (int i = 0; i < VX; ++i) c_out[i] = c[i];
-        }
         const T L = Pm[off - 1], R = Pm[off + VX];
+        if (nb_out) {
+#pragma unroll
+            for (int i = 0; i < VX; ++i) {
+                nb_out->c[i] = c[i];
+                nb_out->yn[i] = yn[i];
+                nb_out->yp[i] = yp[i];
+            }
+            nb_out->L = L;
+            nb_out->R = R;
+        }
 #pragma unroll
         for (int i = 0; i < VX; ++i) {
             const T g0 = (i + 1 < VX ? c[i + 1] : R) - (i > 0 ? c[i - 1] : L);
@@ -252,6 +267,15 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
     if (z0 + 1 < z1) issue_vel(z0 + 1, 1);
     cp_async_commit();
 
+    PhiNb<T, VX> cur;  // phi around the own group at plane z0 (slot 2)
+    if (act) {
+        const T *const P0 = sphi + 2 * S.phi + pos;
+        VV::ld(cur.c, P0);
+        VV::ld(cur.yn, P0 - P);
+        VV::ld(cur.yp, P0 + P);
+        cur.L = P0[-1];
+        cur.R = P0[VX];
+    }
     int pk = 2, vk = 0;  // ring slots of phi plane k and of the velocities of plane k
     for (int k = z0; k < z1; ++k) {
         const int pk1 = pk == 4 ? 0 : pk + 1, pk2 = pk1 == 4 ? 0 : pk1 + 1;
@@ -273,21 +297,19 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
         sharp_ring(Pk1, Pk, Pk2, syw);
         if (act) {
             T szn[VX];
-            T c[VX], zp[VX];  // the group at planes k and k+1, read once for both phases
-            VV::ld(c, Pk + pos);
+            PhiNb<T, VX> nxt;  // phi around the group at plane k+1
             {
                 T s0[VX], s1[VX];
-                sharp_group(Pk1, Pk, Pk2, pos, s0, s1, szn, c, zp);
+                sharp_group(Pk1, Pk, Pk2, pos, s0, s1, szn, cur.c, &nxt);
                 VV::st(sxw + sxo, s0);
                 VV::st(syw + syo, s1);
             }
             // fluxes and update at plane k (s of plane k: buffer k & 1, written before the barrier)
             const T *sx = ssx + (k & 1) * S.sx, *sy = ssy + (k & 1) * S.sy;
             const T *vel = svel + vk * S.vel;
-            T yn[VX], yp[VX];
-            VV::ld(yn, Pk + pos - P);
-            VV::ld(yp, Pk + pos + P);
-            const T L = Pk[pos - 1], R = Pk[pos + VX];
+            // phi around the group at plane k, carried from the previous iteration
+            const T *const c = cur.c, *const yn = cur.yn, *const yp = cur.yp, *const zp = nxt.c;
+            const T L = cur.L, R = cur.R;
             T sxc[VX], syn[VX], syp[VX];
             VV::ld(sxc, sx + sxo);
             VV::ld(syn, sy + syo - P);
@@ -353,6 +375,7 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
                 for (int i = 0; i < VX; ++i)
                     if (i < nown) urow[i] = o[i];
             }
+            cur = nxt;
         }
         pk = pk1;
         vk = vk == 2 ? 0 : vk + 1;
