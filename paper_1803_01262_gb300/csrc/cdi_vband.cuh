@@ -241,7 +241,7 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
     __syncthreads();
 
     // Prologue: s_z at plane z0-1 (own), s at plane z0 (own + ring), flux at z0-1/2.
-    T szc[VX], Fzm[VX];
+    T szc[VX], Fzm[VX], sxk[VX];  // sxk: the own group's s_x at plane k
     {
         const T *Pm2 = sphi, *Pm1 = sphi + S.phi, *P0 = sphi + 2 * S.phi, *P1 = sphi + 3 * S.phi;
         T *const sx = ssx + (z0 & 1) * S.sx;
@@ -251,6 +251,8 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
             sharp_group(Pm1, Pm2, P0, pos, a0, a1, szm);
             sharp_group(P0, Pm1, P1, pos, s0, s1, szc);
             VV::st(sx + sxo, s0);
+#pragma unroll
+            for (int i = 0; i < VX; ++i) sxk[i] = s0[i];
             VV::st(sy + syo, s1);
             T pm[VX], pc[VX];
             VV::ld(pm, Pm1 + pos);
@@ -298,10 +300,11 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
         if (act) {
             T szn[VX];
             PhiNb<T, VX> nxt;  // phi around the group at plane k+1
+            T sxn[VX];  // s_x of the group at plane k+1
             {
-                T s0[VX], s1[VX];
-                sharp_group(Pk1, Pk, Pk2, pos, s0, s1, szn, cur.c, &nxt);
-                VV::st(sxw + sxo, s0);
+                T s1[VX];
+                sharp_group(Pk1, Pk, Pk2, pos, sxn, s1, szn, cur.c, &nxt);
+                VV::st(sxw + sxo, sxn);
                 VV::st(syw + syo, s1);
             }
             // fluxes and update at plane k (s of plane k: buffer k & 1, written before the barrier)
@@ -310,8 +313,8 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
             // phi around the group at plane k, carried from the previous iteration
             const T *const c = cur.c, *const yn = cur.yn, *const yp = cur.yp, *const zp = nxt.c;
             const T L = cur.L, R = cur.R;
-            T sxc[VX], syn[VX], syp[VX];
-            VV::ld(sxc, sx + sxo);
+            const T *const sxc = sxk;
+            T syn[VX], syp[VX];
             VV::ld(syn, sy + syo - P);
             VV::ld(syp, sy + syo + P);
             const T sxL = sx[sxo - 1 + dL], sxR = sx[sxo + VX + dR];
@@ -376,6 +379,8 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
                     if (i < nown) urow[i] = o[i];
             }
             cur = nxt;
+#pragma unroll
+            for (int i = 0; i < VX; ++i) sxk[i] = sxn[i];
         }
         pk = pk1;
         vk = vk == 2 ? 0 : vk + 1;
