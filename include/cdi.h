@@ -291,13 +291,32 @@ CDI_API int cdi_batch_info(const cdi_batch *b, int *parity, int *total_units, in
 CDI_API int cdi_batch_step(cdi_batch *b, double vel_scale, void *stream);
 
 /* nsteps steps (vel_scale = 1) as one CUDA graph launch; the graph is
- * captured on first use for each (nsteps, parity) and replayed after. */
+ * captured on first use for each (nsteps, parity) and replayed after.  The
+ * launches of a run overlap: launch i + 1 starts on the SMs that launch i
+ * leaves, and each of its work units waits (on the device, for at most one
+ * second plus 2 ns per cell of the batch) only until its own box has completed
+ * step i.  The results are those
+ * of nsteps cdi_batch_step calls, bit for bit.  A wait that runs out is
+ * recorded in the status words (the units after it are skipped) and reported
+ * by the next cdi_batch_stats as CDI_ERR_TIMEOUT; the next run starts afresh.
+ * Allocates one pair of 32-bit counters per step on the first run of a new
+ * largest nsteps. */
 CDI_API int cdi_batch_run(cdi_batch *b, int nsteps, void *stream);
 
 /* Copy the nbox statistics records (last step + run accumulators) to out[];
- * synchronises.  CDI_ERR_NAN if a box's sum is not finite. */
+ * synchronises.  CDI_ERR_NAN if a box's sum is not finite; CDI_ERR_TIMEOUT if
+ * a run's device-side wait gave up since the last call (the status words are
+ * then cleared); CDI_ERR_BOUNDS from checked builds. */
 CDI_API int cdi_batch_stats(cdi_batch *b, cdi_stats *out, void *stream);
 CDI_API int cdi_batch_reset_run_stats(cdi_batch *b, void *stream);
+
+/* Test of the run's bounded wait: one launch whose work units wait for a step
+ * their boxes never reach, the first wait for limit_s seconds (0 < limit_s <=
+ * 2), the others giving up when they see it has.  No unit is stepped: fields,
+ * statistics and parity are unchanged.  Returns CDI_ERR_TIMEOUT (the expected
+ * result; the status words are cleared) or CDI_OK if no wait ran out (the
+ * time-out path is broken).  Synchronises. */
+CDI_API int cdi_batch_probe_box_wait(cdi_batch *b, double limit_s, void *stream);
 
 /* Sharpening form of every box of the batch (see cdi_set_sharpening):
  * CDI_SHARPEN_CENTRE (Section 2.2, the default) or CDI_SHARPEN_FACE, the

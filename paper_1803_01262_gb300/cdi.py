@@ -102,6 +102,7 @@ SIGNATURES = {
     "cdi_batch_run": [_V, _I, _V],
     "cdi_batch_stats": [_V, _V, _V],
     "cdi_batch_reset_run_stats": [_V, _V],
+    "cdi_batch_probe_box_wait": [_V, _Dbl, _V],
     "cdi_batch_set_launch": [_V, _I, _I],
     "cdi_batch_set_sharpening": [_V, _I],
     "cdi_batch_get_sharpening": [_V, _P(_I)],
@@ -513,3 +514,8 @@ class Batch:
     def reset_run_stats(self, stream=None):
         """Zero every box's run accumulators."""
         _ck(lib().cdi_batch_reset_run_stats(self._h, _stream(stream)))
+
+    def probe_box_wait(self, limit_s=0.05, stream=None):
+        """Make the run's per-box wait run out (see cdi_batch_probe_box_wait); raises CDIError
+        with code CDI_ERR_TIMEOUT, the expected result.  No box is stepped."""
+        _ck(lib().cdi_batch_probe_box_wait(self._h, limit_s, _stream(stream)))

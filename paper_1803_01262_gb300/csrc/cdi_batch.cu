@@ -135,16 +135,53 @@ __device__ __forceinline__ void plane_unit(const FwdArgs<T> &a, Acc<T> &acc, uns
 // BODY 4: bands of whole rows of the padded copies (vband_unit, cdi_vband.cuh),
 // slots of sizes vbs; final_write: the step also writes the caller's arrays.
 // FACE: the face-product sharpening (bodies 0, 1 and 2).
+// Work hand-out and ordering of one batch launch.  The steps of a run overlap:
+// launch i + 1 starts on the SMs that launch i leaves, and each of its units
+// waits only until its own box has completed step i (boxes are independent, so
+// the large boxes of the next step fill the tail of the current one).
+struct BatchSync {
+    unsigned int *queue;  // [2]: units handed out beyond the first grid's worth, blocks finished
+    unsigned int *epoch;  // [nbox]: steps of the current run each box has completed
+    int step;             // index of this launch in a run; its units wait for epoch >= step
+    int reset;            // the last block to finish zeroes queue (launches outside a run)
+    unsigned long long wait_ns;  // limit of one unit's wait
+};
+
+// Wait until *epoch >= target (acquire: the box's previous step is then visible),
+// for at most limit_ns; gives up at once if another wait has already given up
+// (status bit 0), else records that bit.  Returns whether the box is ready.
+__device__ __forceinline__ bool wait_epoch(const unsigned int *epoch, unsigned target, unsigned int *status,
+                                           unsigned long long limit_ns)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(epoch) : "memory");
+        if ((int)(v - target) >= 0) return true;
+        unsigned st;
+        asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(st) : "l"(status) : "memory");
+        if (st & 1u) return false;
+        if (global_ns() - t0 > limit_ns) break;
+        __nanosleep(256);
+    }
+    atomicOr(status, 1u);
+    return false;
+}
+
 template <typename T, int BX, int BY, int BODY = 0, bool FACE = false>
 __global__ void __launch_bounds__(BX * BY, BODY >= 3 ? 2 : 1)
 batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_box,
              const int total_units, const int parity, const T vs, Partial *partials,
              unsigned int *box_done, StatsRec *recs, const BandSlots bs, const VbandSlots vbs,
-             const int final_write, unsigned int *queue)
+             const int final_write, const BatchSync sync)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int fold, next_u;
+    __shared__ int fold, next_u, ready;
     const int tid = threadIdx.x + BX * threadIdx.y;
+    unsigned int *const status = boxes[0].a.red.status;
+    // The next launch of a run may start once every block of this one has
+    // started; it takes the SMs as this launch's blocks finish.
+    grid_dep_launch();
     // Units are handed out in list order from a counter (queue[0]; every block
     // starts with unit blockIdx.x): a block takes the next unit when it is done
     // with one, so blocks that run faster take more.  The fields do not depend
@@ -153,6 +190,14 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
     int u = blockIdx.x;
     while (u < total_units) {
         const int bi = unit_box[u];
+        if (sync.step > 0) {  // the box's previous step: complete and visible
+            if (tid == 0) {
+                ready = wait_epoch(sync.epoch + bi, (unsigned)sync.step, status, sync.wait_ns);
+                __threadfence();
+            }
+            __syncthreads();
+            if (!ready) break;  // a wait gave up (reported); the remaining units are skipped
+        }
         FwdArgs<T> a = boxes[bi].a;
         if (parity) {
             T *t = a.out;
@@ -187,7 +232,7 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
                 scalar_unit<T, BX, BY, false, SCALAR_PF, FACE>(a, un, acc, smem_raw);
         }
         int claim = 0;  // the next unit, requested before this one's reduction
-        if (tid == 0) claim = (int)atomicAdd(queue, 1u) + (int)gridDim.x;
+        if (tid == 0) claim = (int)atomicAdd(sync.queue, 1u) + (int)gridDim.x;
         const Partial p = block_partial(acc);
         if (tid == 0) {
             next_u = claim;
@@ -216,17 +261,21 @@ batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_b
                 r->nt_run += q.nt;
                 r->steps_run += 1;
                 box_done[fb] = 0u;  // every unit of the box has counted in this launch
+                __threadfence();
+                atomicAdd(sync.epoch + fb, 1u);  // release: the box's next step may start
             }
         }
         __syncthreads();  // every thread has read `fold` before it is written again
         u = next_u;
     }
-    // the last block to run out of units resets the counters for the next launch
-    if (tid == 0) {
+    // outside a run, the last block to run out of units resets the counters for
+    // the next launch (a run's launches each have counters of their own, zeroed
+    // before the run: an overlapping launch must not see a reset)
+    if (tid == 0 && sync.reset) {
         __threadfence();
-        if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
-            queue[0] = 0u;
-            queue[1] = 0u;
+        if (atomicAdd(sync.queue + 1, 1u) == gridDim.x - 1) {
+            atomicExch(sync.queue, 0u);
+            atomicExch(sync.queue + 1, 0u);
         }
     }
 }
@@ -283,6 +332,9 @@ struct cdi_batch {
     size_t unit_cap;
     unsigned int *box_done;    // [nbox] units completed in the current launch
     unsigned int *queue;       // [2] next unit to hand out, blocks finished (self-resetting)
+    unsigned int *epoch;       // [nbox] steps of the current run each box has completed
+    unsigned int *run_queue;   // [2 run_cap] the counters of a run's launches, zeroed before the run
+    int run_cap;
     StatsRec *recs;            // [nbox]
     unsigned int *status;      // status words (checked builds record out-of-range indices)
     long long cells;
@@ -511,6 +563,8 @@ static int batch_free(cdi_batch *b)
     cudaFree(b->partials);
     cudaFree(b->box_done);
     cudaFree(b->queue);
+    cudaFree(b->epoch);
+    cudaFree(b->run_queue);
     cudaFree(b->recs);
     cudaFree(b->status);
     cudaFree(b->padbuf);
@@ -669,58 +723,45 @@ static int rebuild(cdi_batch *b, int tile, int zdepth)
     return b->dtype == CDI_F64 ? build_units<double>(b, tile, zdepth) : build_units<float>(b, tile, zdepth);
 }
 
+// One launch of a batch kernel instantiation.  Launches after the first of a
+// run are made with programmatic stream serialisation: they start while the
+// launch before is finishing, ordered per box by the epochs (BatchSync).
+template <typename T, int BX, int BY, int BODY, bool FACE = false>
+static cudaError_t launch_batch_kernel(cdi_batch *b, size_t smem, int parity, double vs, cudaStream_t s,
+                                       int final_write, const cdi::BatchSync &y)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)b->nblocks);
+    cfg.blockDim = dim3(BX, BY);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = y.step > 0 && !y.reset ? 1 : 0;  // a run's launches after its first
+    return cudaLaunchKernelEx(&cfg, cdi::batch_kernel<T, BX, BY, BODY, FACE>, (const BoxDev<T> *)b->boxes_dev,
+                              (const int *)b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
+                              b->recs, b->band, b->vband, final_write, y);
+}
+
 template <typename T, int BX, int BY>
-static void batch_launch_one(cdi_batch *b, int parity, double vs, cudaStream_t s)
+static cudaError_t batch_launch_one(cdi_batch *b, int parity, double vs, cudaStream_t s, const cdi::BatchSync &y)
 {
-    if (BX == 32 && BY == 8 && b->sharpen == CDI_SHARPEN_FACE) {
-        if (b->flat)
-            cdi::batch_kernel<T, 32, 8, 1, true><<<b->nblocks, dim3(32, 8), cdi::FwdSmem<T, 32, 8>::bytes, s>>>(
-                (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-                b->box_done, b->recs, b->band, b->vband, 0, b->queue);
-        else
-            cdi::batch_kernel<T, 32, 8, 0, true><<<b->nblocks, dim3(32, 8), cdi::FwdSmem<T, 32, 8>::bytes, s>>>(
-                (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-                b->box_done, b->recs, b->band, b->vband, 0, b->queue);
-        return;
-    }
-    if (b->flat)
-        cdi::batch_kernel<T, BX, BY, 1><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
-            (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-            b->box_done, b->recs, b->band, b->vband, 0, b->queue);
-    else
-        cdi::batch_kernel<T, BX, BY, 0><<<b->nblocks, dim3(BX, BY), cdi::FwdSmem<T, BX, BY>::bytes, s>>>(
-            (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials,
-            b->box_done, b->recs, b->band, b->vband, 0, b->queue);
+    const size_t smem = cdi::FwdSmem<T, BX, BY>::bytes;
+    if (BX == 32 && BY == 8 && b->sharpen == CDI_SHARPEN_FACE)
+        return b->flat ? launch_batch_kernel<T, 32, 8, 1, true>(b, smem, parity, vs, s, 0, y)
+                       : launch_batch_kernel<T, 32, 8, 0, true>(b, smem, parity, vs, s, 0, y);
+    return b->flat ? launch_batch_kernel<T, BX, BY, 1>(b, smem, parity, vs, s, 0, y)
+                   : launch_batch_kernel<T, BX, BY, 0>(b, smem, parity, vs, s, 0, y);
 }
 
 template <typename T>
-static void batch_launch_plane(cdi_batch *b, int parity, double vs, cudaStream_t s)
+static cudaError_t batch_launch_plane(cdi_batch *b, int parity, double vs, cudaStream_t s, const cdi::BatchSync &y)
 {
-    if (b->sharpen == CDI_SHARPEN_FACE) {
-        cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2, true><<<b->nblocks, dim3(cdi::PLANE_NT, 1), b->plane_bytes, s>>>(
-            (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-            b->recs, b->band, b->vband, 0, b->queue);
-        return;
-    }
-    cdi::batch_kernel<T, cdi::PLANE_NT, 1, 2><<<b->nblocks, dim3(cdi::PLANE_NT, 1), b->plane_bytes, s>>>(
-        (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-        b->recs, b->band, b->vband, 0, b->queue);
-}
-
-template <typename T>
-static void batch_launch_band(cdi_batch *b, int parity, double vs, cudaStream_t s)
-{
-    cdi::batch_kernel<T, cdi::BAND_NT, 1, 3><<<b->nblocks, dim3(cdi::BAND_NT, 1), b->band_bytes, s>>>(
-        (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-        b->recs, b->band, b->vband, 0, b->queue);
-}
-
-template <typename T>
-static void batch_launch_vband(cdi_batch *b, int parity, double vs, cudaStream_t s, int final_write)
-{
-    cdi::batch_kernel<T, cdi::VBAND_NT, 1, 4><<<b->nblocks, dim3(cdi::VBAND_NT, 1), b->vband_bytes, s>>>(
-        (const BoxDev<T> *)b->boxes_dev, b->unit_box, b->total_units, parity, (T)vs, b->partials, b->box_done,
-        b->recs, b->band, b->vband, final_write, b->queue);
+    if (b->sharpen == CDI_SHARPEN_FACE)
+        return launch_batch_kernel<T, cdi::PLANE_NT, 1, 2, true>(b, b->plane_bytes, parity, vs, s, 0, y);
+    return launch_batch_kernel<T, cdi::PLANE_NT, 1, 2>(b, b->plane_bytes, parity, vs, s, 0, y);
 }
 
 // Tile 6: copy the current state (the caller's array of this parity) into the
@@ -738,29 +779,39 @@ static int vband_pack_state(cdi_batch *b, int parity, cudaStream_t s)
 }
 
 template <typename T>
-static int batch_launch(cdi_batch *b, int parity, double vs, cudaStream_t s, int final_write)
+static int batch_launch(cdi_batch *b, int parity, double vs, cudaStream_t s, int final_write,
+                        const cdi::BatchSync &y)
 {
+    cudaError_t e;
     switch (b->tile) {
-    case 0: batch_launch_one<T, 32, 8>(b, parity, vs, s); break;
-    case 1: batch_launch_one<T, 32, 16>(b, parity, vs, s); break;
-    case 2: batch_launch_one<T, 64, 8>(b, parity, vs, s); break;
-    case 3: batch_launch_one<T, 32, 4>(b, parity, vs, s); break;
-    case cdi::BATCH_TILE_PLANE: batch_launch_plane<T>(b, parity, vs, s); break;
-    case cdi::BATCH_TILE_BAND: batch_launch_band<T>(b, parity, vs, s); break;
-    case cdi::BATCH_TILE_VBAND: batch_launch_vband<T>(b, parity, vs, s, final_write); break;
+    case 0: e = batch_launch_one<T, 32, 8>(b, parity, vs, s, y); break;
+    case 1: e = batch_launch_one<T, 32, 16>(b, parity, vs, s, y); break;
+    case 2: e = batch_launch_one<T, 64, 8>(b, parity, vs, s, y); break;
+    case 3: e = batch_launch_one<T, 32, 4>(b, parity, vs, s, y); break;
+    case cdi::BATCH_TILE_PLANE: e = batch_launch_plane<T>(b, parity, vs, s, y); break;
+    case cdi::BATCH_TILE_BAND:
+        e = launch_batch_kernel<T, cdi::BAND_NT, 1, 3>(b, b->band_bytes, parity, vs, s, 0, y);
+        break;
+    case cdi::BATCH_TILE_VBAND:
+        e = launch_batch_kernel<T, cdi::VBAND_NT, 1, 4>(b, b->vband_bytes, parity, vs, s, final_write, y);
+        break;
     default: return cdi::set_error(CDI_ERR_STATE, "bad batch tile");
     }
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return cdi::set_error(CDI_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
     return CDI_OK;
 }
 
 // One step of every box; final_write (tile 6): the step also writes the caller's
-// arrays (the last step of a call).
-static int launch_any(cdi_batch *b, int parity, double vs, cudaStream_t s, int final_write = 1)
+// arrays (the last step of a call).  y: the step's place in a run (nullptr: a
+// launch on its own, after everything before it on the stream).
+static int launch_any(cdi_batch *b, int parity, double vs, cudaStream_t s, int final_write = 1,
+                      const cdi::BatchSync *y = nullptr)
 {
-    return b->dtype == CDI_F64 ? batch_launch<double>(b, parity, vs, s, final_write)
-                               : batch_launch<float>(b, parity, vs, s, final_write);
+    const cdi::BatchSync single = {b->queue, b->epoch, 0, 1, 0ull};
+    const cdi::BatchSync &sy = y ? *y : single;
+    return b->dtype == CDI_F64 ? batch_launch<double>(b, parity, vs, s, final_write, sy)
+                               : batch_launch<float>(b, parity, vs, s, final_write, sy);
 }
 
 static void reset_recs(std::vector<StatsRec> &h)
@@ -803,6 +854,8 @@ int cdi_batch_create(cdi_batch **out, const cdi_box_desc *boxes, int nbox, int d
         (e = cudaMalloc(&b->box_done, sizeof(unsigned int) * nbox)) != cudaSuccess ||
         (e = cudaMalloc(&b->queue, sizeof(unsigned int) * 2)) != cudaSuccess ||
         (e = cudaMemset(b->queue, 0, sizeof(unsigned int) * 2)) != cudaSuccess ||
+        (e = cudaMalloc(&b->epoch, sizeof(unsigned int) * nbox)) != cudaSuccess ||
+        (e = cudaMemset(b->epoch, 0, sizeof(unsigned int) * nbox)) != cudaSuccess ||
         (e = cudaMalloc(&b->recs, sizeof(StatsRec) * nbox)) != cudaSuccess ||
         (e = cudaMalloc(&b->status, sizeof(unsigned int) * cdi::kStatusWords)) != cudaSuccess ||
         (e = cudaMemset(b->status, 0, sizeof(unsigned int) * cdi::kStatusWords)) != cudaSuccess ||
@@ -853,13 +906,37 @@ int cdi_batch_run(cdi_batch *b, int nsteps, void *stream)
     auto it = b->graphs.find(key);
     cudaError_t e;
     if (it == b->graphs.end()) {
-        // Capture nsteps launches (parity alternating) once on the private stream.
+        if (nsteps > b->run_cap) {  // one counter pair per launch of the run
+            if ((e = cudaDeviceSynchronize()) != cudaSuccess)  // no graph in flight uses the old counters
+                return cdi::set_error(CDI_ERR_CUDA, "batch run: %s", cudaGetErrorString(e));
+            drop_graphs(b);
+            cudaFree(b->run_queue);
+            b->run_queue = nullptr;
+            b->run_cap = 0;
+            if ((e = cudaMalloc(&b->run_queue, sizeof(unsigned int) * 2 * (size_t)nsteps)) != cudaSuccess) {
+                b->run_queue = nullptr;
+                return cdi::set_error(CDI_ERR_CUDA, "batch run counters: %s", cudaGetErrorString(e));
+            }
+            b->run_cap = nsteps;
+        }
+        // Capture nsteps launches (parity alternating) once on the private stream:
+        // the run's counters and box epochs zeroed, then the steps, each after the
+        // first overlapping the one before (BatchSync).
         cudaGraph_t graph;
         if ((e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
             return cdi::set_error(CDI_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
-        int rc = b->tile == cdi::BATCH_TILE_VBAND ? vband_pack_state(b, b->parity, b->cap) : CDI_OK;
+        int rc = CDI_OK;
+        if ((e = cudaMemsetAsync(b->run_queue, 0, sizeof(unsigned int) * 2 * (size_t)nsteps, b->cap)) != cudaSuccess ||
+            (e = cudaMemsetAsync(b->epoch, 0, sizeof(unsigned int) * b->nbox, b->cap)) != cudaSuccess ||
+            (e = cudaMemsetAsync(b->box_done, 0, sizeof(unsigned int) * b->nbox, b->cap)) != cudaSuccess)
+            rc = cdi::set_error(CDI_ERR_CUDA, "batch run counters: %s", cudaGetErrorString(e));
+        if (rc == CDI_OK && b->tile == cdi::BATCH_TILE_VBAND) rc = vband_pack_state(b, b->parity, b->cap);
+        // a unit waits at most about one step: one second plus 2 ns per cell (a step
+        // of the slowest tile takes well under 1 ns per cell)
+        const unsigned long long wait_ns = 1000000000ull + 2ull * (unsigned long long)b->cells;
         for (int i = 0; i < nsteps && rc == CDI_OK; ++i) {
-            rc = launch_any(b, b->parity ^ (i & 1), 1.0, b->cap, i == nsteps - 1);
+            const cdi::BatchSync y = {b->run_queue + 2 * i, b->epoch, i, 0, wait_ns};
+            rc = launch_any(b, b->parity ^ (i & 1), 1.0, b->cap, i == nsteps - 1, &y);
         }
         e = cudaStreamEndCapture(b->cap, &graph);
         if (rc) return rc;
@@ -889,12 +966,38 @@ int cdi_batch_stats(cdi_batch *b, cdi_stats *out, void *stream)
         return cdi::set_error(CDI_ERR_CUDA, "batch statistics: %s", cudaGetErrorString(e));
     if (st[0]) {
         cudaMemsetAsync(b->status, 0, sizeof(st), s);
-        return cdi::set_error(CDI_ERR_BOUNDS, "checked build: %u index(es) out of range, the last %u against a limit of %u",
-                              st[1], st[2], st[3]);
+        if (st[0] & 2u)
+            return cdi::set_error(CDI_ERR_BOUNDS,
+                                  "checked build: %u index(es) out of range, the last %u against a limit of %u",
+                                  st[1], st[2], st[3]);
+        return cdi::set_error(CDI_ERR_TIMEOUT, "a bounded wait for a box's previous step gave up; "
+                                               "results are unreliable");
     }
     for (int i = 0; i < b->nbox; ++i)
         if (!isfinite(out[i].sum)) return cdi::set_error(CDI_ERR_NAN, "box %d: non-finite phi", i);
     return CDI_OK;
+}
+
+// One launch whose units wait for a step their boxes never reach: the first wait
+// runs out after limit_s, the others give up on seeing its status bit, and no
+// unit is stepped (fields, records and counters are left as they were).
+int cdi_batch_probe_box_wait(cdi_batch *b, double limit_s, void *stream)
+{
+    if (!b) return cdi::set_error(CDI_ERR_ARG, "batch is NULL");
+    if (!(limit_s > 0.0 && limit_s <= 2.0)) return cdi::set_error(CDI_ERR_ARG, "limit_s must be in (0, 2]");
+    cudaStream_t s = (cudaStream_t)stream;
+    const cdi::BatchSync y = {b->queue, b->epoch, 1 << 30, 1, (unsigned long long)(limit_s * 1e9)};
+    if (int rc = launch_any(b, b->parity, 1.0, s, 0, &y)) return rc;
+    unsigned int st = 0;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(&st, b->status, sizeof(st), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cdi::set_error(CDI_ERR_CUDA, "probe status readback: %s", cudaGetErrorString(e));
+    if (!(st & 1u)) return CDI_OK;  // the waits did not run out: the time-out path is broken
+    if ((e = cudaMemsetAsync(b->status, 0, sizeof(unsigned int) * cdi::kStatusWords, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cdi::set_error(CDI_ERR_CUDA, "probe status reset: %s", cudaGetErrorString(e));
+    return cdi::set_error(CDI_ERR_TIMEOUT, "bounded wait for a box's previous step ran out (probe)");
 }
 
 int cdi_batch_reset_run_stats(cdi_batch *b, void *stream)

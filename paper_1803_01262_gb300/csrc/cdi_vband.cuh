@@ -279,6 +279,9 @@ __device__ __forceinline__ void vband_unit(const FwdArgs<T> &a, const T *__restr
         cur.R = P0[VX];
     }
     int pk = 2, vk = 0;  // ring slots of phi plane k and of the velocities of plane k
+    // two planes per pass: the carried values (cur / nxt, s_x, s_z, the z flux)
+    // alternate between two register sets instead of being copied
+#pragma unroll 2
     for (int k = z0; k < z1; ++k) {
         const int pk1 = pk == 4 ? 0 : pk + 1, pk2 = pk1 == 4 ? 0 : pk1 + 1;
         const int pkm = pk == 0 ? 4 : pk - 1;  // also the slot of plane k+4

@@ -358,3 +358,70 @@ def test_padded_band_tile_bit_for_bit(dtype):
         assert s0[i]["min"] == s6[i]["min"] and s0[i]["max"] == s6[i]["max"]
         assert s0[i]["steps_run"] == s6[i]["steps_run"] == 7
         assert s6[i]["sum"] == pytest.approx(s0[i]["sum"], rel=1e-12 if dtype == torch.float64 else 1e-6)
+
+
+STAT_KEYS = ("mass", "sum", "min", "max", "n_strict", "n_tol", "min_run", "max_run", "n_strict_run",
+             "n_tol_run", "steps_run")
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("tile,zdepth", [(0, 0), (2, 8), (3, 0), (5, 0), (5, 16), (6, 0), (6, 8)])
+def test_overlapping_run_equals_single_steps(dtype, tile, zdepth):
+    """The launches of a run overlap: a unit of step i + 1 waits only for its own box to
+    finish step i.  Forty uneven boxes (more units than blocks, so blocks of two steps share
+    the SMs): fields and every statistic equal those of the same steps launched one at a
+    time, bit for bit, over runs of several lengths, a run after single steps, and a run
+    longer than any before (new counters)."""
+    boxes = make_boxes(dtype, nbox=40, nmin=4, nmax=48, seed=60 + tile)
+    twins = [dict(x, phi_a=x["phi_a"].clone(), phi_b=torch.empty_like(x["phi_b"])) for x in boxes]
+    b1, b2 = cdi.Batch(boxes), cdi.Batch(twins)
+    try:
+        b1.set_launch(tile, zdepth)
+    except cdi.CDIError:
+        pytest.skip("the tile does not apply to these boxes")
+    b2.set_launch(tile, zdepth)
+    for n, single_first in ((7, False), (2, False), (3, True), (12, False), (1, False)):
+        if single_first:
+            b1.step(1.0)
+            b2.step(1.0)
+        for _ in range(n):
+            b1.step(1.0)
+        b2.run(n)
+        torch.cuda.synchronize()
+        for i in range(len(boxes)):
+            assert torch.equal(b1.current(i), b2.current(i)), (n, i)
+        s1, s2 = b1.stats(), b2.stats()
+        for i, (a, c) in enumerate(zip(s1, s2)):
+            for k in STAT_KEYS:
+                assert a[k] == c[k], (n, i, k, a[k], c[k])
+
+
+def test_run_wait_times_out_and_the_batch_stays_usable():
+    """The run's per-box wait is bounded: a probe launch whose units wait for a step their
+    boxes never reach reports CDI_ERR_TIMEOUT within the limit, steps nothing, and the next
+    steps and runs are those of an untouched twin."""
+    import time
+    boxes = make_boxes(torch.float32, nbox=12, nmin=6, nmax=32, seed=71)
+    twins = [dict(x, phi_a=x["phi_a"].clone(), phi_b=torch.empty_like(x["phi_b"])) for x in boxes]
+    b1, b2 = cdi.Batch(boxes), cdi.Batch(twins)
+    b1.run(3)
+    b2.run(3)
+    t0 = time.perf_counter()
+    with pytest.raises(cdi.CDIError) as e:
+        b1.probe_box_wait(0.05)
+    assert e.value.code == cdi.CDI_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert b1.info()["parity"] == b2.info()["parity"]
+    b1.step(1.0)
+    b2.step(1.0)
+    b1.run(4)
+    b2.run(4)
+    torch.cuda.synchronize()
+    for i in range(len(boxes)):
+        assert torch.equal(b1.current(i), b2.current(i)), i
+    s1, s2 = b1.stats(), b2.stats()     # raises if the status word were still set
+    for a, c in zip(s1, s2):
+        for k in STAT_KEYS:
+            assert a[k] == c[k], k
+    with pytest.raises(cdi.CDIError):
+        b1.probe_box_wait(5.0)          # limit out of range
