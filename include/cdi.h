@@ -266,7 +266,9 @@ CDI_API int cdi_max_dt_mixed(double dx, double eps, double gamma, const double *
  * units -- a tile of one box and a chunk of its planes -- from one list), and
  * cdi_batch_run replays a captured CUDA graph of nsteps such launches.  Each
  * box evolves exactly as with cdi_step on its own grid.  Arrays follow the
- * conventions above and are borrowed for the batch's lifetime.
+ * conventions above and are borrowed for the batch's lifetime.  Like a grid,
+ * a batch (its counters, epochs and statistics scratch) must be used by one
+ * stream at a time.
  */
 typedef struct cdi_box_desc {
     int nx, ny, nz;
