@@ -986,17 +986,19 @@ static int step_host_pipelined(cdi_grid *g, const void *hin, void *hout, double 
         return cudaMemcpyAsync(si + (size_t)z0 * pb, src + (size_t)z0 * pb, (size_t)(z1 - z0) * pb,
                                cudaMemcpyHostToDevice, g->hs_in);
     };
+    // copy-in order: the two seam planes, then piece j = planes [b[j] + 2, b[j+1] + 2)
+    // (piece 0 from plane 0, the last up to nz - 2): piece j ends with the two halo
+    // planes above slab j, so slab j is stepped once piece j has landed (the halo
+    // below it came with piece j-1; the last slab's wrapped halo with the seam
+    // planes and piece 0).  For the smallest nz a piece may repeat seam planes.
     if ((e = h2d(nz - 2, nz)) != cudaSuccess) return cuda_fail(e, "host-to-device copy");
     for (int j = 0; j < S; ++j) {
-        if ((e = h2d(b[j], j == S - 1 ? nz - 2 : b[j + 1])) != cudaSuccess ||
-            (e = cudaEventRecord(g->ev_in[j], g->hs_in)) != cudaSuccess)
+        const int z0 = j == 0 ? 0 : b[j] + 2, z1 = j == S - 1 ? nz - 2 : b[j + 1] + 2;
+        if ((e = h2d(z0, z1)) != cudaSuccess || (e = cudaEventRecord(g->ev_in[j], g->hs_in)) != cudaSuccess)
             return cuda_fail(e, "host-to-device copy");
     }
     for (int j = 0; j < S; ++j) {
-        // the halo above slab j lies in piece j+1 (the last slab wraps onto slab 0
-        // and the seam planes, both landed before it)
-        const int need = j + 1 < S ? j + 1 : S - 1;
-        if ((e = cudaStreamWaitEvent(s, g->ev_in[need], 0)) != cudaSuccess) return cuda_fail(e, "wait");
+        if ((e = cudaStreamWaitEvent(s, g->ev_in[j], 0)) != cudaSuccess) return cuda_fail(e, "wait");
         int rc = g->dtype == CDI_F64
                      ? step_t<double>(g, si, so, dt, eps, gamma, vs, s, b[j], b[j + 1], j > 0, j == S - 1)
                      : step_t<float>(g, si, so, dt, eps, gamma, vs, s, b[j], b[j + 1], j > 0, j == S - 1);
