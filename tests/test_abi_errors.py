@@ -62,6 +62,15 @@ def test_batch_create_arguments(L):
     assert not b.value
 
 
+def test_null_batch_everywhere(L):
+    """A NULL batch is refused before any CUDA call, the run and its wait probe included."""
+    assert L.cdi_batch_step(None, 1.0, None) == cdi.CDI_ERR_ARG
+    assert L.cdi_batch_run(None, 4, None) == cdi.CDI_ERR_ARG
+    assert L.cdi_batch_probe_box_wait(None, 0.05, None) == cdi.CDI_ERR_ARG
+    assert L.cdi_batch_reset_run_stats(None, None) == cdi.CDI_ERR_ARG
+    assert "NULL" in msg(L)
+
+
 def test_step_noalloc_arguments(L):
     """Every rejection below happens before the first CUDA call, so the fake (never
     dereferenced) addresses are safe on any machine."""
