@@ -413,6 +413,14 @@ CDI_API int cdi_probe_bounds_check(cdi_grid *g, void *stream);
  * of the paper).  Synchronises the stream. */
 CDI_API int cdi_probe_fp64_rate(double *fma_per_s, void *stream);
 
+/* The slab plan cdi_step_host uses for nz >= 16 planes (host arithmetic only,
+ * no CUDA call): bounds[0..8] the 8 slabs [bounds[j], bounds[j+1]); after the
+ * two seam planes nz-2, nz-1, copy-in piece j is planes [copy_lo[j],
+ * copy_hi[j]) (8 entries each), which ends with the two halo planes above slab
+ * j, so slab j is stepped once piece j has landed.  CDI_ERR_DIM for nz < 16,
+ * CDI_ERR_ARG for a NULL array. */
+CDI_API int cdi_host_slab_plan(int nz, int *bounds, int *copy_lo, int *copy_hi);
+
 /* Kernels with a tunable launch configuration. */
 enum { CDI_KERNEL_FORWARD = 0, CDI_KERNEL_ADJOINT = 1 };
 

@@ -87,6 +87,7 @@ SIGNATURES = {
     "cdi_probe_bounded_wait": [_V, _Dbl, _V],
     "cdi_is_checked_build": [],
     "cdi_probe_fp64_rate": [_P(_Dbl), _V],
+    "cdi_host_slab_plan": [_I, _P(_I), _P(_I), _P(_I)],
     "cdi_probe_bounds_check": [_V, _V],
     "cdi_get_sharpening": [_V, _P(_I)],
     "cdi_set_launch": [_V, _I, _I, _I, _I],
@@ -157,6 +158,14 @@ def _dtype_code(dtype):
     if dtype == torch.float64:
         return CDI_F64
     raise ValueError("dtype must be torch.float32 or torch.float64")
+
+
+def host_slab_plan(nz):
+    """The slab plan of the host-buffer step (cdi_host_slab_plan): (bounds[9], copy_lo[8],
+    copy_hi[8]) as lists."""
+    b, lo, hi = (ctypes.c_int * 9)(), (ctypes.c_int * 8)(), (ctypes.c_int * 8)()
+    _ck(lib().cdi_host_slab_plan(int(nz), b, lo, hi))
+    return list(b), list(lo), list(hi)
 
 
 def probe_fp64_rate(stream=None):

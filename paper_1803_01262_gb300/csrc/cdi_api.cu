@@ -940,15 +940,42 @@ int cdi_step_planes(cdi_grid *g, const void *phi_in, void *phi_out, int z_lo, in
         : step_t<float>(g, phi_in, phi_out, dt, eps, gamma, vel_scale, s, z_lo, z_hi, 0, 1);
 }
 
-// cdi_step_host in S = 8 equal z slabs: the two planes of the periodic seam
-// (nz-2, nz-1) are copied in first, then slab j = [b_j, b_j+1) in order on
-// hs_in; slab j is stepped on the caller's stream as soon as the piece holding
-// its upper halo planes has landed, and copied out on hs_out once stepped, so
-// both copy directions and the kernel overlap.  The record is built by folding
-// the slabs' partial results (combine) and closed by the last slab.  (256^3
-// FP32: 2 slabs 0.78 ms per step, 4: 0.65, 8: 0.58, 16: 0.61, 32: 0.88 -- per-
-// slab copy and launch costs against overlap; slabs thinning towards the end
-// 0.62; the unpipelined step 0.80.)
+// The host-buffer step's slab plan for nz >= 16 planes: slab j is planes
+// [b[j], b[j+1]) (8 equal slabs); after the two seam planes nz-2, nz-1, copy-in
+// piece j is planes [c0[j], c1[j]) = [b[j] + 2, b[j+1] + 2) (piece 0 from plane 0,
+// the last up to nz - 2), so piece j ends with the two halo planes above slab j
+// and slab j is stepped once piece j has landed (the halo below it came with
+// piece j-1; the last slab's wrapped halo with the seam planes and piece 0).  For
+// the smallest nz a piece may repeat seam planes.
+constexpr int kHostSlabs = 8;
+static_assert(kHostSlabs == sizeof(cdi_grid::ev_in) / sizeof(cudaEvent_t), "one copy-in event per slab");
+static void host_slab_plan(int nz, int *b, int *c0, int *c1)
+{
+    constexpr int S = kHostSlabs;
+    for (int j = 0; j <= S; ++j) b[j] = (int)((long long)j * nz / S);
+    for (int j = 0; j < S; ++j) {
+        c0[j] = j == 0 ? 0 : b[j] + 2;
+        c1[j] = j == S - 1 ? nz - 2 : b[j + 1] + 2;
+    }
+}
+
+int cdi_host_slab_plan(int nz, int *bounds, int *copy_lo, int *copy_hi)
+{
+    if (nz < 16) return fail(CDI_ERR_DIM, "the slab pipeline needs nz >= 16");
+    if (!bounds || !copy_lo || !copy_hi) return fail(CDI_ERR_ARG, "NULL argument");
+    host_slab_plan(nz, bounds, copy_lo, copy_hi);
+    return CDI_OK;
+}
+
+// cdi_step_host in S = 8 equal z slabs (host_slab_plan): the two planes of the
+// periodic seam (nz-2, nz-1) are copied in first, then the pieces in order on
+// hs_in; slab j is stepped on the caller's stream as soon as piece j (which ends
+// with its upper halo planes) has landed, and copied out on hs_out once stepped,
+// so both copy directions and the kernel overlap.  The record is built by folding
+// the slabs' partial results (combine) and closed by the last slab.  (256^3 FP32:
+// 0.566 ms per step; with pieces ending at the slab bounds, each slab waiting for
+// the next piece, 2 slabs 0.78 ms, 4: 0.65, 8: 0.58, 16: 0.61, 32: 0.88 -- per-slab
+// copy and launch costs against overlap; the unpipelined step 0.80.)
 static int step_host_pipelined(cdi_grid *g, const void *hin, void *hout, double dt, double eps,
                                double gamma, double vs, cudaStream_t s)
 {
@@ -970,9 +997,10 @@ static int step_host_pipelined(cdi_grid *g, const void *hin, void *hout, double 
         g->pipe_ready = true;
     }
     if (int rc = ensure_slab_cfg(g)) return rc;
-    const int S = 8, nz = g->nz;  // nz >= 16: every slab holds the two halo planes
-    int b[S + 1];
-    for (int j = 0; j <= S; ++j) b[j] = (int)((long long)j * nz / S);
+    constexpr int S = kHostSlabs;
+    const int nz = g->nz;  // nz >= 16: every slab holds the two halo planes
+    int b[S + 1], c0[S], c1[S];
+    host_slab_plan(nz, b, c0, c1);
     const size_t pb = (size_t)g->nx * g->ny * esize(g);
     const char *src = (const char *)hin;
     char *dst = (char *)hout;
@@ -986,15 +1014,10 @@ static int step_host_pipelined(cdi_grid *g, const void *hin, void *hout, double 
         return cudaMemcpyAsync(si + (size_t)z0 * pb, src + (size_t)z0 * pb, (size_t)(z1 - z0) * pb,
                                cudaMemcpyHostToDevice, g->hs_in);
     };
-    // copy-in order: the two seam planes, then piece j = planes [b[j] + 2, b[j+1] + 2)
-    // (piece 0 from plane 0, the last up to nz - 2): piece j ends with the two halo
-    // planes above slab j, so slab j is stepped once piece j has landed (the halo
-    // below it came with piece j-1; the last slab's wrapped halo with the seam
-    // planes and piece 0).  For the smallest nz a piece may repeat seam planes.
+    // copy-in order: the two seam planes, then the pieces of host_slab_plan
     if ((e = h2d(nz - 2, nz)) != cudaSuccess) return cuda_fail(e, "host-to-device copy");
     for (int j = 0; j < S; ++j) {
-        const int z0 = j == 0 ? 0 : b[j] + 2, z1 = j == S - 1 ? nz - 2 : b[j + 1] + 2;
-        if ((e = h2d(z0, z1)) != cudaSuccess || (e = cudaEventRecord(g->ev_in[j], g->hs_in)) != cudaSuccess)
+        if ((e = h2d(c0[j], c1[j])) != cudaSuccess || (e = cudaEventRecord(g->ev_in[j], g->hs_in)) != cudaSuccess)
             return cuda_fail(e, "host-to-device copy");
     }
     for (int j = 0; j < S; ++j) {
