@@ -127,14 +127,6 @@ __device__ __forceinline__ void plane_unit(const FwdArgs<T> &a, Acc<T> &acc, uns
     }
 }
 
-// BODY 0: the 3D unit body (scalar_unit).  BODY 1: every box has nz == 1
-// (e.g. a phase-diagram sweep of 2D boxes): the single-plane unit body, which
-// stages the plane once (flat_unit).  BODY 2: every box has nz == 1 and fits
-// in shared memory: one unit per box, the whole-plane body (plane_unit).
-// BODY 3: bands of whole rows (band_unit, cdi_band.cuh), slots of sizes bs.
-// BODY 4: bands of whole rows of the padded copies (vband_unit, cdi_vband.cuh),
-// slots of sizes vbs; final_write: the step also writes the caller's arrays.
-// FACE: the face-product sharpening (bodies 0, 1 and 2).
 // Work hand-out and ordering of one batch launch.  The steps of a run overlap:
 // launch i + 1 starts on the SMs that launch i leaves, and each of its units
 // waits only until its own box has completed step i (boxes are independent, so
@@ -168,6 +160,15 @@ __device__ __forceinline__ bool wait_epoch(const unsigned int *epoch, unsigned t
     return false;
 }
 
+// BODY 0: the 3D unit body (scalar_unit).  BODY 1: every box has nz == 1
+// (e.g. a phase-diagram sweep of 2D boxes): the single-plane unit body, which
+// stages the plane once (flat_unit).  BODY 2: every box has nz == 1 and fits
+// in shared memory: one unit per box, the whole-plane body (plane_unit).
+// BODY 3: bands of whole rows (band_unit, cdi_band.cuh), slots of sizes bs.
+// BODY 4: bands of whole rows of the padded copies (vband_unit, cdi_vband.cuh),
+// slots of sizes vbs; final_write: the step also writes the caller's arrays.
+// FACE: the face-product sharpening (bodies 0, 1 and 2).  sync: the launch's
+// hand-out counters and its place in a run (BatchSync).
 template <typename T, int BX, int BY, int BODY = 0, bool FACE = false>
 __global__ void __launch_bounds__(BX * BY, BODY >= 3 ? 2 : 1)
 batch_kernel(const BoxDev<T> *__restrict__ boxes, const int *__restrict__ unit_box,
